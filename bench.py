@@ -1,0 +1,364 @@
+#!/usr/bin/env python3
+"""Benchmark: SCOUP sparse code uplift throughput on GB300.
+
+Workload: 1M Gaussians in 64 blobs, 200 sphere-band views at 988x731, 200
+Voronoi regions per view, C=256 atoms, s=8 nonzeros per region code, K=8
+(synthetic, seeded).  One step = one full uplift (all 200 views: projection,
+binning, per-tile sort + composite + sparse scatter) followed by the Top-K +
+L1 normalisation of every Gaussian, through the C ABI.
+
+Metric: accepted Gaussian-pixel contributions per second (alpha >= 1/255,
+before the transmittance stop), the count the library reports.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Under torchrun each rank runs its own replica of the workload on its GPU
+(independent problems, weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "uplift Gaussian-pixel contributions/s"
+UNIT = "contributions/s"
+WORKLOAD = "uplift_1M_gaussians_200views_988x731_C256_s8_K8"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--views", type=int, default=200, help="views of the workload (default: all 200)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU oracle sample budget")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# distributed plumbing (host-side barrier and max-over-ranks only)
+# ----------------------------------------------------------------------------
+
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+            if torch.cuda.is_available():
+                torch.cuda.set_device(self.local)
+            dist.init_process_group(backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, uuid: str | None):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            if uuid and uuid not in parts[1]:
+                continue
+            rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[6 + k].lower().startswith("active")})
+        busy = [s for s in sm if s > 0.5 * (max(mx) if mx else 1)] or sm
+        return {"sm_mhz": statistics.median(busy) if busy else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "sm_max_mhz": d.get("sm_max_mhz", 2070.0), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle sample (cpu_baseline and the reference arm)
+# ----------------------------------------------------------------------------
+
+def oracle_sample(budget_s: float, max_views: int = 16, device: str = "cpu"):
+    """Time the FP64 oracle on the first views of the same workload, one view
+    at a time, until the budget is spent.  Returns (contributions/s, views, threads)."""
+    import oracle
+    import synth
+    oracle.build()
+    threads = os.cpu_count() or 1
+    wl = synth.uplift_cfg2(device=device, V=max_views)
+    done_views, contrib, elapsed = 0, 0, 0.0
+    for v in range(max_views):
+        t0 = time.perf_counter()
+        _, _, cnt = oracle.uplift(wl, views=[v], nthreads=threads)
+        elapsed += time.perf_counter() - t0
+        contrib += cnt["contributions"]
+        done_views += 1
+        if elapsed >= budget_s:
+            break
+    return contrib / elapsed, done_views, threads, elapsed
+
+
+def run_reference(args, dist):
+    """The oracle, as it stands, on the host cores: each step one view of the
+    workload (a bounded sample); rank 0 only."""
+    if dist.rank != 0:
+        return
+    import oracle
+    import synth
+    oracle.build()
+    threads = os.cpu_count() or 1
+    nviews = args.warmup + args.steps
+    wl = synth.uplift_cfg2(device="cpu", V=nviews)
+    for v in range(args.warmup):
+        oracle.uplift(wl, views=[v], nthreads=threads)
+    contrib, t_total = 0, 0.0
+    for v in range(args.warmup, nviews):
+        t0 = time.perf_counter()
+        _, _, cnt = oracle.uplift(wl, views=[v], nthreads=threads)
+        t_total += time.perf_counter() - t0
+        contrib += cnt["contributions"]
+    value = contrib / t_total
+    sample = (f"one view per step (views {args.warmup}..{nviews - 1} of 200) of the 1M-Gaussian "
+              f"988x731 workload, FP64 oracle, OpenMP over tiles")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "1 view per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# GB300 arm
+# ----------------------------------------------------------------------------
+
+def run_gb300(args, dist):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2605_13600_gb300 import build as gbuild
+    gbuild.build()
+    import paper_2605_13600_gb300 as gb
+
+    dev = torch.device("cuda", dist.local if dist.world > 1 else 0)
+    torch.cuda.set_device(dev)
+    wl = synth.uplift_cfg2(device=str(dev), V=args.views)
+    up = gb.Uplift(wl, device=str(dev))
+    st0 = up.run(stats=True)
+    if st0["status"] != 0:
+        raise RuntimeError(f"uplift status {st0['status']}")
+    contrib = st0["contributions"]
+
+    for _ in range(args.warmup):
+        up.run(stats=False)
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    props = torch.cuda.get_device_properties(dev)
+    uuid = str(getattr(props, "uuid", "") or "")
+    clocks = ClockSampler()
+    l0 = gb.scoup_launch_count()
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        up.run(stats=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop(uuid)
+    launches = (gb.scoup_launch_count() - l0) // args.steps
+    st_end = gb.scoup_read_stats(up.workspace)
+    if st_end["status"] != 0:
+        raise RuntimeError(f"uplift status {st_end['status']} after the timed loop")
+    t_step = ev0.elapsed_time(ev1) / 1e3 / args.steps
+    t_max = dist.max(t_step)
+    value = dist.world * contrib / t_max
+
+    # per-phase kernel times (CUDA events on the launching stream)
+    gb.scoup_profile_enable(True)
+    for _ in range(2):
+        up.run(stats=False)
+    torch.cuda.synchronize()
+    prof = gb.scoup_profile_read()
+    gb.scoup_profile_enable(False)
+    step_ms = {k: v[0] / 2 for k, v in prof.items()}
+    tiles_ms, tiles_n = prof.get("uplift_tiles", (0.0, 1))
+    per_launch_s = tiles_ms / tiles_n / 1e3
+
+    # roofline of the dominant kernel (per-tile composite + scatter, one launch per view)
+    pk = peaks()
+    V = len(up.cams)
+    eval_per_launch = st0["evaluated_pairs"] / V
+    contrib_per_launch = contrib / V
+    # FP32-pipe work the compositing definition needs (Eq. 2): per evaluated pair
+    # 2 subtractions + 3 products + 2 fused sums (exponent) + 2 compares; per accepted
+    # pair 7 more (exp scale, alpha = o*exp, min, 1 - alpha, T(1 - alpha), stop compare, alpha*T)
+    ops = 9.0 * eval_per_launch + 7.0 * contrib_per_launch
+    alu_peak = 152 * 128 * pk["sm_max_mhz"] * 1e6  # FP32 lanes x max SM clock
+    achieved = ops / per_launch_s
+    npx = up.cams[0].width * up.cams[0].height
+    bytes_launch = 4.0 * npx + 8.0 * st0["atomics"] / V + 32.0 * st0["visible"] / V
+    roofline = {"kernel": "uplift_tile_kernel", "bound": "alu", "achieved": achieved / 1e12,
+                "peak": alu_peak / 1e12, "unit": "Tops/s (FP32 lane ops)",
+                "frac": achieved / alu_peak, "traffic": None,
+                "per_launch_ms": per_launch_s * 1e3,
+                "hbm_view": {"algorithmic_bytes_per_launch": bytes_launch,
+                             "achieved_gbs": bytes_launch / per_launch_s / 1e9,
+                             "peak_gbs": pk["hbm_gbs"],
+                             "frac": bytes_launch / per_launch_s / 1e9 / pk["hbm_gbs"]},
+                "peak_source": pk["source"]}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host = {
+            "means": torch.as_tensor(wl.scene.means).pin_memory(),
+            "scales": torch.as_tensor(wl.scene.scales).pin_memory(),
+            "quats": torch.as_tensor(wl.scene.quats).pin_memory(),
+            "opacity": torch.as_tensor(wl.scene.opacity).pin_memory(),
+            "region_maps": torch.as_tensor(wl.region_maps).pin_memory(),
+            "code_idx": torch.as_tensor(wl.code_idx).pin_memory(),
+            "code_val": torch.as_tensor(wl.code_val).pin_memory(),
+        }
+        out_i = torch.empty(up.topk_idx.shape, dtype=torch.int32).pin_memory()
+        out_v = torch.empty(up.topk_val.shape, dtype=torch.float32).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in host.values())
+        d2h = out_i.numel() * 4 + out_v.numel() * 4
+
+        def e2e_step():
+            for k, t in host.items():
+                getattr(up, k).copy_(t, non_blocking=True)
+            up.run(stats=False)
+            out_i.copy_(up.topk_idx, non_blocking=True)
+            out_v.copy_(up.topk_val, non_blocking=True)
+
+        for _ in range(args.warmup):
+            e2e_step()
+        torch.cuda.synchronize()
+        dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        t_e2e = dist.max((time.perf_counter() - t0) / args.steps)
+        e2e = {"value": dist.world * contrib / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": t_e2e * 1e3}
+
+    cpu = None
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        v, nv, threads, el = oracle_sample(args.cpu_seconds, device=str(dev))
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"views 0..{nv - 1} of 200 of the same workload (all 1M Gaussians, 988x731), "
+                         f"FP64 oracle, {el:.1f} s"}
+
+    if dist.rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded stand-in for pretrained 3DGS scenes with SAM/CLIP region codes)",
+            "config": {"workload": WORKLOAD, "n_gaussians": wl.scene.n, "views": len(up.cams),
+                       "width": 988, "height": 731, "regions_per_view": 200, "C": wl.C, "s": wl.s,
+                       "K": wl.K, "contributions_per_step": contrib,
+                       "evaluated_pairs_per_step": st0["evaluated_pairs"],
+                       "l2": "inputs larger than L2 (region maps 578 MB, accumulator 1.02 GB)",
+                       "parallelism": f"replica x{dist.world}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clk, "phase_ms_per_step": step_ms,
+            "stats": {k: st0[k] for k in ("visible", "duplicates", "flushes", "atomics")},
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    dist = Dist()
+    try:
+        if args.impl == "reference":
+            run_reference(args, dist)
+        else:
+            run_gb300(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,167 @@
+/*
+ * scoup.h -- C ABI of the GB300 (sm_103a) SCOUP sparse code uplift library.
+ *
+ * SCOUP (Sparse Code Uplifting) lifts per-region sparse codebook codes of
+ * 2D views onto the Gaussians of a pretrained 3D Gaussian Splatting scene,
+ * keeps a Top-K code per Gaussian, and renders those codes back to 2D.
+ *
+ * Conventions
+ *  - Every entry point returns an int status: SCOUP_OK (0) or a negative
+ *    SCOUP_ERR_* code; scoup_last_error() then holds a message for the
+ *    calling thread.  Nothing aborts or exits.
+ *  - Array pointers are DEVICE pointers owned by the caller (contiguous,
+ *    row-major, 16-byte aligned where noted); small descriptors (scene,
+ *    cameras, offsets) are HOST structs/arrays.  The library never frees
+ *    caller memory and allocates no device memory of its own on these
+ *    paths: scratch is the caller's `workspace`.
+ *  - Work is enqueued on `stream` (a cudaStream_t passed as void*; NULL is
+ *    the legacy default stream) and is complete when the stream is.  Calls
+ *    do not synchronise, except those that take a host `scoup_stats*`
+ *    (non-NULL) or read back sizes, as documented per function.
+ *  - Errors detected on the device (workspace capacity exceeded, invalid
+ *    region or atom ids) are recorded in the workspace status word and
+ *    returned by the next synchronising call (scoup_read_stats, or the call
+ *    itself when it was given `stats`).
+ */
+#ifndef SCOUP_H
+#define SCOUP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SCOUP_OK 0
+#define SCOUP_ERR_INVALID_ARG (-1)   /* host-side argument validation failed */
+#define SCOUP_ERR_CUDA (-2)          /* a CUDA runtime call failed */
+#define SCOUP_ERR_OOM (-3)           /* workspace smaller than required */
+#define SCOUP_ERR_CAPACITY (-4)      /* device: tile-list capacity exceeded */
+#define SCOUP_ERR_DEVICE_CHECK (-5)  /* device: region/atom id out of range */
+#define SCOUP_ERR_TIMEOUT (-6)       /* reserved: a bounded device wait gave up */
+
+/* Gaussians of a 3DGS scene (paper Sec. 3): means mu_i, linear scales s_i
+ * (exp of the stored log-scales), unit quaternions q_i in (w, x, y, z)
+ * order (normalised again inside), opacities o_i in (0, 1] after the
+ * sigmoid.  Device pointers, float32, row-major [n,3], [n,3], [n,4], [n]. */
+typedef struct scoup_scene {
+  int64_t n;
+  const float* means;
+  const float* scales;
+  const float* quats;
+  const float* opacity;
+} scoup_scene;
+
+/* Pinhole camera: world->camera 3x4 row-major [R | t] with camera x right,
+ * y down, z forward; focal lengths and principal point in pixels; pixel
+ * (x, y) is sampled at image point (x + 0.5, y + 0.5). */
+typedef struct scoup_camera {
+  float viewmat[12];
+  float fx, fy, cx, cy;
+  int32_t width, height;
+} scoup_camera;
+
+/* Counters of one uplift or render call (summed over its views). */
+typedef struct scoup_stats {
+  int64_t visible;          /* (Gaussian, view) pairs that survive culling */
+  int64_t duplicates;       /* (Gaussian, tile) pairs emitted by binning */
+  int64_t evaluated_pairs;  /* (pixel, Gaussian) pairs examined while the pixel was active */
+  int64_t contributions;    /* accepted pairs: alpha >= 1/255, before the transmittance stop */
+  int64_t flushes;          /* (Gaussian, tile, region) partial sums flushed to the accumulator */
+  int64_t atomics;          /* global accumulator atomics issued */
+  int32_t status;           /* SCOUP_OK or the first device-side error */
+  int32_t max_dups_view;    /* largest per-view duplicate count seen */
+} scoup_stats;
+
+const char* scoup_version(void);
+const char* scoup_last_error(void);
+
+/* ------------------------------------------------------------------ */
+/* Uplift (paper Sec. 4.2, Eq. 5 and Eq. 6, Algorithm 1)                */
+/* ------------------------------------------------------------------ */
+
+/* Bytes of workspace for scoup_uplift on scenes of up to n Gaussians, views
+ * of up to max_width x max_height pixels and up to dup_capacity
+ * (Gaussian, tile) pairs per view.  Returns 0 on invalid arguments. */
+size_t scoup_uplift_workspace_size(int64_t n, int32_t max_width, int32_t max_height,
+                                   int64_t dup_capacity);
+
+/* Exact per-view (Gaussian, tile) pair counts: projects every view and
+ * writes the largest count to *max_dups (host).  Synchronises `stream`.
+ * workspace may be sized with any dup_capacity >= 0. */
+int scoup_uplift_plan(const scoup_scene* scene, const scoup_camera* cams, int32_t V,
+                      void* workspace, size_t ws_bytes, int64_t* max_dups, void* stream);
+
+/* Sparse coefficient uplift.  For every view v (cams[v], host array of V),
+ * rasterizes the scene with standard 3DGS compositing (Sec. 3, Eq. 2) and
+ * adds, for every accepted (pixel p, Gaussian i) pair with weight
+ * e = alpha * T, c * e to accum[i][j] for every code entry (j, c) of the
+ * region of p (Eq. 5 without Z_i, which Eq. 6 makes redundant).  Then, if
+ * topk_idx != NULL, writes per Gaussian the K largest positive entries of
+ * its accumulator row (ties to the lower atom index) divided by their sum
+ * (Eq. 6), padded with (-1, 0).
+ *
+ *  region_maps  int32, views packed back to back; view v occupies
+ *               [map_offsets[v], map_offsets[v] + H_v*W_v), row-major; each
+ *               value is a row of the code table or -1 (unlabelled pixel:
+ *               occludes, contributes nothing).
+ *  map_offsets  HOST int64 [V] element offsets into region_maps.
+ *  R_total      number of code-table rows (region ids must be < R_total).
+ *  code_idx     int32 [R_total, s] atom ids (< C) or -1 padding.
+ *  code_val     float32 [R_total, s] nonnegative coefficients (Eq. 4).
+ *               If s > K, each code's K largest entries are used (Alg. 1).
+ *  accum        float32 [n, C] row-major accumulator (caller-owned).
+ *  accum_mode   0: zero accum first; 1: add to its current contents (resume
+ *               a chunked uplift).
+ *  topk_idx     int32 [n, K] or NULL (accumulate only); topk_val float32 [n, K].
+ *  workspace    device scratch of ws_bytes >= scoup_uplift_workspace_size().
+ *  stats        HOST scoup_stats* or NULL; when given, the call synchronises
+ *               `stream` and returns the device status.
+ * Limits: 1 <= K <= C <= 1024, 1 <= s <= 64, V >= 0, n >= 0 (n = 0 and V = 0
+ * are valid and produce empty / padded outputs). */
+int scoup_uplift(const scoup_scene* scene, const scoup_camera* cams, int32_t V,
+                 const int32_t* region_maps, const int64_t* map_offsets, int32_t R_total,
+                 const int32_t* code_idx, const float* code_val, int32_t s, int32_t C, int32_t K,
+                 float* accum, int32_t accum_mode, int32_t* topk_idx, float* topk_val,
+                 void* workspace, size_t ws_bytes, scoup_stats* stats, void* stream);
+
+/* Top-K + L1 normalisation (Eq. 6) of an accumulator accum[n, C] alone:
+ * positive entries only, ordered by (value desc, atom index asc), divided by
+ * the sum of the kept values; rows without positive entries give (-1, 0). */
+int scoup_topk(const float* accum, int64_t n, int32_t C, int32_t K, int32_t* topk_idx,
+               float* topk_val, void* stream);
+
+/* Synchronises `stream` and reads the counters and status of the last call
+ * that used this workspace. */
+int scoup_read_stats(const void* workspace, size_t ws_bytes, scoup_stats* stats, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* Profiling hooks                                                     */
+/* ------------------------------------------------------------------ */
+
+/* Phases timed by the profiling hooks. */
+#define SCOUP_PHASE_TAU 0          /* per-Gaussian alpha threshold */
+#define SCOUP_PHASE_PREPROCESS 1   /* projection of one view */
+#define SCOUP_PHASE_BINNING 2      /* tile binning of one view (3 kernels) */
+#define SCOUP_PHASE_UPLIFT_TILES 3 /* per-tile sort + composite + scatter of one view */
+#define SCOUP_PHASE_TOPK 4         /* Top-K + normalisation */
+#define SCOUP_PHASE_CODE_TOPK 5    /* per-code Top-K (s > K) */
+#define SCOUP_NUM_PHASES 16
+
+/* When enable != 0, each later launch group of a phase is bracketed by CUDA
+ * events recorded on its stream (process-wide switch). */
+int scoup_profile_enable(int32_t enable);
+
+/* Waits for the recorded events and returns, per phase, the summed elapsed
+ * milliseconds ms[phase] and the number of timed launch groups
+ * launches[phase] since the previous read (arrays of nphases, host). */
+int scoup_profile_read(double* ms, int64_t* launches, int32_t nphases);
+
+/* Total number of CUDA kernels this library has launched in the process. */
+int64_t scoup_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCOUP_H */

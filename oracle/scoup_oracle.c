@@ -255,9 +255,12 @@ static void view_free(view_ctx* v)
   memset(v, 0, sizeof(*v));
 }
 
-static int view_setup(view_ctx* v, const float* means, const float* scales,
-                      const float* quats, const float* opacity, int64_t n,
-                      const orc_camera* cam, orc_counts* cnt)
+/* Project every Gaussian for this view and build the depth-sorted candidate
+ * lists of the tiles flagged in `want` (all tiles when want == NULL). */
+static int view_setup_tiles(view_ctx* v, const float* means, const float* scales,
+                            const float* quats, const float* opacity, int64_t n,
+                            const orc_camera* cam, orc_counts* cnt,
+                            const int64_t* rows, int64_t nrows)
 {
   memset(v, 0, sizeof(*v));
   v->cam = cam;
@@ -268,35 +271,50 @@ static int view_setup(view_ctx* v, const float* means, const float* scales,
   v->ntiles = v->gx * v->gy;
   v->P = (orc_proj*)malloc(sizeof(orc_proj) * (size_t)(n > 0 ? n : 1));
   v->tile_start = (int64_t*)calloc((size_t)v->ntiles + 1, sizeof(int64_t));
-  if (!v->P || !v->tile_start) { view_free(v); return -1; }
+  uint8_t* want = (uint8_t*)calloc((size_t)v->ntiles, 1);
+  if (!v->P || !v->tile_start || !want) { free(want); view_free(v); return -1; }
 
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i)
     orc_project(means + 3 * i, scales + 3 * i, quats + 4 * i, cam, &v->P[i]);
 
-  /* count (Gaussian, tile) pairs per tile */
-  int64_t visible = 0;
+  if (rows) {
+    for (int64_t r = 0; r < nrows; ++r) {
+      const orc_proj* p = &v->P[rows[r]];
+      if (!p->visible) continue;
+      for (int ty = p->rect[1]; ty < p->rect[3]; ++ty)
+        for (int tx = p->rect[0]; tx < p->rect[2]; ++tx) want[ty * v->gx + tx] = 1;
+    }
+  } else {
+    memset(want, 1, (size_t)v->ntiles);
+  }
+
+  /* count (Gaussian, tile) pairs per wanted tile */
+  int64_t visible = 0, dups = 0;
   for (int64_t i = 0; i < n; ++i) {
     const orc_proj* p = &v->P[i];
     if (!p->visible) continue;
     ++visible;
+    dups += (int64_t)(p->rect[2] - p->rect[0]) * (p->rect[3] - p->rect[1]);
     for (int ty = p->rect[1]; ty < p->rect[3]; ++ty)
-      for (int tx = p->rect[0]; tx < p->rect[2]; ++tx) v->tile_start[ty * v->gx + tx + 1]++;
+      for (int tx = p->rect[0]; tx < p->rect[2]; ++tx)
+        if (want[ty * v->gx + tx]) v->tile_start[ty * v->gx + tx + 1]++;
   }
   for (int t = 0; t < v->ntiles; ++t) v->tile_start[t + 1] += v->tile_start[t];
-  int64_t dups = v->tile_start[v->ntiles];
-  v->tile_list = (int32_t*)malloc(sizeof(int32_t) * (size_t)(dups > 0 ? dups : 1));
+  int64_t listed = v->tile_start[v->ntiles];
+  v->tile_list = (int32_t*)malloc(sizeof(int32_t) * (size_t)(listed > 0 ? listed : 1));
   int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)v->ntiles);
-  if (!v->tile_list || !fill) { free(fill); view_free(v); return -1; }
+  if (!v->tile_list || !fill) { free(fill); free(want); view_free(v); return -1; }
   memcpy(fill, v->tile_start, sizeof(int64_t) * (size_t)v->ntiles);
   for (int64_t i = 0; i < n; ++i) {
     const orc_proj* p = &v->P[i];
     if (!p->visible) continue;
     for (int ty = p->rect[1]; ty < p->rect[3]; ++ty)
       for (int tx = p->rect[0]; tx < p->rect[2]; ++tx)
-        v->tile_list[fill[ty * v->gx + tx]++] = (int32_t)i;
+        if (want[ty * v->gx + tx]) v->tile_list[fill[ty * v->gx + tx]++] = (int32_t)i;
   }
   free(fill);
+  free(want);
 
   /* front-to-back order: (depth, gid) ascending */
 #pragma omp parallel
@@ -319,6 +337,13 @@ static int view_setup(view_ctx* v, const float* means, const float* scales,
   }
   if (cnt) { cnt->visible += visible; cnt->duplicates += dups; }
   return 0;
+}
+
+static int view_setup(view_ctx* v, const float* means, const float* scales,
+                      const float* quats, const float* opacity, int64_t n,
+                      const orc_camera* cam, orc_counts* cnt)
+{
+  return view_setup_tiles(v, means, scales, quats, opacity, n, cam, cnt, NULL, 0);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -545,7 +570,10 @@ int orc_uplift(const float* means, const float* scales, const float* quats,
     const orc_camera* cam = &cams[v];
     const int32_t* rmap = region_maps + map_offsets[v];
     view_ctx vc;
-    if (view_setup(&vc, means, scales, quats, opacity, n, cam, counts)) { free(row_of); return -1; }
+    if (view_setup_tiles(&vc, means, scales, quats, opacity, n, cam, counts, rows, nrows)) {
+      free(row_of);
+      return -1;
+    }
 
     /* tiles to composite: all, or those touched by the requested rows */
     uint8_t* want = (uint8_t*)calloc((size_t)vc.ntiles, 1);

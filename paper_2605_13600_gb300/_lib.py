@@ -1,0 +1,94 @@
+"""ctypes loader for libscoup.so (the C ABI declared in include/scoup.h).
+
+Raises immediately if the shared library is missing: there is no CPU or
+PyTorch fallback for any entry point.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libscoup.so")
+
+SCOUP_OK = 0
+SCOUP_ERR_INVALID_ARG = -1
+SCOUP_ERR_CUDA = -2
+SCOUP_ERR_OOM = -3
+SCOUP_ERR_CAPACITY = -4
+SCOUP_ERR_DEVICE_CHECK = -5
+SCOUP_ERR_TIMEOUT = -6
+
+
+class ScoupError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"scoup error {code}: {msg}")
+        self.code = code
+
+
+class Scene(ct.Structure):
+    _fields_ = [("n", ct.c_int64), ("means", ct.c_void_p), ("scales", ct.c_void_p),
+                ("quats", ct.c_void_p), ("opacity", ct.c_void_p)]
+
+
+class Camera(ct.Structure):
+    _fields_ = [("viewmat", ct.c_float * 12), ("fx", ct.c_float), ("fy", ct.c_float),
+                ("cx", ct.c_float), ("cy", ct.c_float), ("width", ct.c_int32),
+                ("height", ct.c_int32)]
+
+
+class Stats(ct.Structure):
+    _fields_ = [("visible", ct.c_int64), ("duplicates", ct.c_int64),
+                ("evaluated_pairs", ct.c_int64), ("contributions", ct.c_int64),
+                ("flushes", ct.c_int64), ("atomics", ct.c_int64), ("status", ct.c_int32),
+                ("max_dups_view", ct.c_int32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+_lib = None
+
+P = ct.c_void_p
+I32 = ct.c_int32
+I64 = ct.c_int64
+SZ = ct.c_size_t
+
+# name -> (restype, argtypes); every entry point of include/scoup.h
+PROTOS = {
+    "scoup_version": (ct.c_char_p, []),
+    "scoup_last_error": (ct.c_char_p, []),
+    "scoup_uplift_workspace_size": (SZ, [I64, I32, I32, I64]),
+    "scoup_uplift_plan": (ct.c_int, [ct.POINTER(Scene), P, I32, P, SZ, ct.POINTER(I64), P]),
+    "scoup_uplift": (ct.c_int, [ct.POINTER(Scene), P, I32, P, P, I32, P, P, I32, I32, I32, P, I32,
+                                P, P, P, SZ, ct.POINTER(Stats), P]),
+    "scoup_topk": (ct.c_int, [P, I64, I32, I32, P, P, P]),
+    "scoup_read_stats": (ct.c_int, [P, SZ, ct.POINTER(Stats), P]),
+    "scoup_profile_enable": (ct.c_int, [I32]),
+    "scoup_profile_read": (ct.c_int, [P, P, I32]),
+    "scoup_launch_count": (I64, []),
+}
+
+PHASES = ["tau", "preprocess", "binning", "uplift_tiles", "topk", "code_topk"]
+NUM_PHASES = 16
+
+
+def load():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_2605_13600_gb300.build.build() "
+                              "(nvcc, sm_103a); there is no fallback implementation")
+        lib = ct.CDLL(LIB_PATH)
+        for name, (res, args) in PROTOS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def check(rc: int) -> None:
+    if rc != SCOUP_OK:
+        msg = load().scoup_last_error()
+        raise ScoupError(rc, msg.decode() if msg else "")

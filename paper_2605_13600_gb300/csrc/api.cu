@@ -1,0 +1,363 @@
+// api.cu -- C ABI entry points: validation, workspace carve-up, launch order.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "scoup_internal.cuh"
+
+namespace scoup {
+
+std::atomic<long long> g_launches{0};
+
+namespace {
+
+// ---- optional per-phase CUDA-event timing -------------------------------
+struct EventPair {
+  int phase;
+  cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<EventPair> g_prof_pending;
+std::vector<cudaEvent_t> g_prof_pool;
+double g_prof_ms[SCOUP_NUM_PHASES];
+long long g_prof_n[SCOUP_NUM_PHASES];
+
+cudaEvent_t prof_event() {
+  if (!g_prof_pool.empty()) {
+    cudaEvent_t e = g_prof_pool.back();
+    g_prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets one launch (or launch group) of a phase with events on `st`.
+struct PhaseScope {
+  int phase;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  PhaseScope(int ph, cudaStream_t s) : phase(ph), st(s) {
+    if (!g_prof_on) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    a = prof_event();
+    cudaEventRecord(a, st);
+  }
+  ~PhaseScope() {
+    if (!a) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    cudaEvent_t b = prof_event();
+    cudaEventRecord(b, st);
+    g_prof_pending.push_back({phase, a, b});
+  }
+};
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(SCOUP_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+int tiles_of(int w, int h) { return ((w + kTile - 1) / kTile) * ((h + kTile - 1) / kTile); }
+
+// Fixed part of the uplift workspace (everything but the key lists).
+size_t uplift_fixed_bytes(int64_t n, int max_tiles, int64_t code_rows_k) {
+  size_t b = align_up(sizeof(WsHeader));
+  b += align_up(sizeof(float) * (size_t)n);               // tau
+  b += align_up(sizeof(ProjRec) * (size_t)n);             // proj
+  b += align_up(sizeof(uint32_t) * (size_t)n);            // depth
+  b += align_up(sizeof(ushort4) * (size_t)n);             // rect
+  b += 3 * align_up(sizeof(uint32_t) * ((size_t)max_tiles + 1));
+  b += 2 * align_up((size_t)code_rows_k * 4);             // filtered codes (s > K)
+  return b;
+}
+
+UpliftWs carve(void* ws, size_t bytes, int64_t n, int max_tiles, int64_t code_rows_k,
+               int32_t** codes_i, float** codes_v) {
+  UpliftWs w;
+  char* p = (char*)ws;
+  size_t off = 0;
+  auto take = [&](size_t sz) { char* q = p + off; off += align_up(sz); return (void*)q; };
+  w.hdr = (WsHeader*)take(sizeof(WsHeader));
+  w.tau = (float*)take(sizeof(float) * (size_t)n);
+  w.proj = (ProjRec*)take(sizeof(ProjRec) * (size_t)n);
+  w.depth = (uint32_t*)take(sizeof(uint32_t) * (size_t)n);
+  w.rect = (ushort4*)take(sizeof(ushort4) * (size_t)n);
+  w.tile_count = (uint32_t*)take(sizeof(uint32_t) * ((size_t)max_tiles + 1));
+  w.tile_start = (uint32_t*)take(sizeof(uint32_t) * ((size_t)max_tiles + 1));
+  w.tile_fill = (uint32_t*)take(sizeof(uint32_t) * ((size_t)max_tiles + 1));
+  *codes_i = (int32_t*)take((size_t)code_rows_k * 4);
+  *codes_v = (float*)take((size_t)code_rows_k * 4);
+  w.keys = (unsigned long long*)(p + off);
+  w.dup_capacity = bytes > off ? (int64_t)((bytes - off) / sizeof(unsigned long long)) : 0;
+  w.max_tiles = max_tiles;
+  return w;
+}
+
+CamArgs cam_args(const scoup_camera& c) {
+  CamArgs a;
+  memcpy(a.vm, c.viewmat, sizeof(a.vm));
+  a.fx = c.fx; a.fy = c.fy; a.cx = c.cx; a.cy = c.cy;
+  a.width = c.width; a.height = c.height;
+  a.gx = (c.width + kTile - 1) / kTile;
+  a.gy = (c.height + kTile - 1) / kTile;
+  return a;
+}
+
+int check_scene(const scoup_scene* sc) {
+  if (!sc) return fail(SCOUP_ERR_INVALID_ARG, "scene is NULL");
+  if (sc->n < 0 || sc->n > 0x7fffffffLL) return fail(SCOUP_ERR_INVALID_ARG, "scene n=%lld out of range", (long long)sc->n);
+  if (sc->n > 0 && (!sc->means || !sc->scales || !sc->quats || !sc->opacity))
+    return fail(SCOUP_ERR_INVALID_ARG, "scene arrays must be non-NULL when n > 0");
+  if (sc->n > 0 && ((uintptr_t)sc->quats & 15u))
+    return fail(SCOUP_ERR_INVALID_ARG, "scene quats must be 16-byte aligned");
+  return SCOUP_OK;
+}
+
+int check_cams(const scoup_camera* cams, int V, int* max_tiles) {
+  if (V < 0) return fail(SCOUP_ERR_INVALID_ARG, "V=%d < 0", V);
+  if (V > 0 && !cams) return fail(SCOUP_ERR_INVALID_ARG, "cams is NULL");
+  int mt = 1;
+  for (int v = 0; v < V; ++v) {
+    const scoup_camera& c = cams[v];
+    if (c.width <= 0 || c.height <= 0 || c.width > 65535 * kTile || c.height > 65535 * kTile)
+      return fail(SCOUP_ERR_INVALID_ARG, "camera %d: bad size %dx%d", v, c.width, c.height);
+    if (!(c.fx > 0.0f) || !(c.fy > 0.0f))
+      return fail(SCOUP_ERR_INVALID_ARG, "camera %d: focal lengths must be > 0", v);
+    const int t = tiles_of(c.width, c.height);
+    if (t > mt) mt = t;
+  }
+  *max_tiles = mt;
+  return SCOUP_OK;
+}
+
+void read_header(const WsHeader& h, scoup_stats* st) {
+  st->visible = (int64_t)h.visible;
+  st->duplicates = (int64_t)h.duplicates;
+  st->evaluated_pairs = (int64_t)h.evaluated;
+  st->contributions = (int64_t)h.contributions;
+  st->flushes = (int64_t)h.flushes;
+  st->atomics = (int64_t)h.atomics;
+  st->max_dups_view = h.max_dups_view;
+  st->status = SCOUP_OK;
+  if (h.status & kStatCapacity) st->status = SCOUP_ERR_CAPACITY;
+  else if (h.status & kStatDeviceCheck) st->status = SCOUP_ERR_DEVICE_CHECK;
+}
+
+int finish_with_stats(const WsHeader* dev_hdr, scoup_stats* stats, cudaStream_t st) {
+  WsHeader h;
+  cudaError_t e = cudaMemcpyAsync(&h, dev_hdr, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_fail(e, "read stats");
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+  read_header(h, stats);
+  if (stats->status == SCOUP_ERR_CAPACITY)
+    return fail(SCOUP_ERR_CAPACITY, "tile-list capacity exceeded (largest view needs %d pairs)", h.max_dups_view);
+  if (stats->status == SCOUP_ERR_DEVICE_CHECK)
+    return fail(SCOUP_ERR_DEVICE_CHECK, "region or atom id out of range");
+  return SCOUP_OK;
+}
+
+}  // namespace
+}  // namespace scoup
+
+using namespace scoup;
+
+extern "C" {
+
+const char* scoup_version(void) { return "scoup-gb300 0.1.0 (sm_103a)"; }
+
+const char* scoup_last_error(void) { return g_err.c_str(); }
+
+size_t scoup_uplift_workspace_size(int64_t n, int32_t max_width, int32_t max_height,
+                                   int64_t dup_capacity) {
+  if (n < 0 || max_width <= 0 || max_height <= 0 || dup_capacity < 0) return 0;
+  return uplift_fixed_bytes(n, tiles_of(max_width, max_height), 0) +
+         sizeof(unsigned long long) * (size_t)dup_capacity;
+}
+
+int scoup_uplift_plan(const scoup_scene* scene, const scoup_camera* cams, int32_t V,
+                      void* workspace, size_t ws_bytes, int64_t* max_dups, void* stream) {
+  int rc = check_scene(scene);
+  if (rc) return rc;
+  int max_tiles = 1;
+  if ((rc = check_cams(cams, V, &max_tiles))) return rc;
+  if (!max_dups) return fail(SCOUP_ERR_INVALID_ARG, "max_dups is NULL");
+  if (!workspace) return fail(SCOUP_ERR_INVALID_ARG, "workspace is NULL");
+  if (ws_bytes < uplift_fixed_bytes(scene->n, max_tiles, 0))
+    return fail(SCOUP_ERR_OOM, "workspace too small: %zu < %zu bytes", ws_bytes,
+                uplift_fixed_bytes(scene->n, max_tiles, 0));
+  cudaStream_t st = (cudaStream_t)stream;
+  int32_t* ci = nullptr;
+  float* cv = nullptr;
+  UpliftWs ws = carve(workspace, ws_bytes, scene->n, max_tiles, 0, &ci, &cv);
+  cudaError_t e = cudaMemsetAsync(ws.hdr, 0, sizeof(WsHeader), st);
+  if (e != cudaSuccess) return cuda_fail(e, "memset");
+  if ((e = launch_tau(scene->opacity, scene->n, ws.tau, st)) != cudaSuccess) return cuda_fail(e, "tau");
+  int64_t best = 0;
+  for (int v = 0; v < V; ++v) {
+    const CamArgs ca = cam_args(cams[v]);
+    if ((e = cudaMemsetAsync(&ws.hdr->duplicates, 0, sizeof(unsigned long long), st)) != cudaSuccess)
+      return cuda_fail(e, "memset");
+    if ((e = launch_preprocess(*scene, ca, ws, st)) != cudaSuccess) return cuda_fail(e, "preprocess");
+    unsigned long long d = 0;
+    if ((e = cudaMemcpyAsync(&d, &ws.hdr->duplicates, sizeof(d), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+      return cuda_fail(e, "read");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "synchronize");
+    if ((int64_t)d > best) best = (int64_t)d;
+  }
+  *max_dups = best;
+  return SCOUP_OK;
+}
+
+int scoup_uplift(const scoup_scene* scene, const scoup_camera* cams, int32_t V,
+                 const int32_t* region_maps, const int64_t* map_offsets, int32_t R_total,
+                 const int32_t* code_idx, const float* code_val, int32_t s, int32_t C, int32_t K,
+                 float* accum, int32_t accum_mode, int32_t* topk_idx, float* topk_val,
+                 void* workspace, size_t ws_bytes, scoup_stats* stats, void* stream) {
+  int rc = check_scene(scene);
+  if (rc) return rc;
+  int max_tiles = 1;
+  if ((rc = check_cams(cams, V, &max_tiles))) return rc;
+  if (C < 1 || C > 1024) return fail(SCOUP_ERR_INVALID_ARG, "C=%d outside [1, 1024]", C);
+  if (K < 1 || K > C) return fail(SCOUP_ERR_INVALID_ARG, "K=%d outside [1, C=%d]", K, C);
+  if (s < 1 || s > 64) return fail(SCOUP_ERR_INVALID_ARG, "s=%d outside [1, 64]", s);
+  if (R_total < 0) return fail(SCOUP_ERR_INVALID_ARG, "R_total=%d < 0", R_total);
+  if (accum_mode != 0 && accum_mode != 1) return fail(SCOUP_ERR_INVALID_ARG, "accum_mode must be 0 or 1");
+  if (scene->n > 0 && !accum) return fail(SCOUP_ERR_INVALID_ARG, "accum is NULL");
+  if ((topk_idx == nullptr) != (topk_val == nullptr))
+    return fail(SCOUP_ERR_INVALID_ARG, "topk_idx and topk_val must both be given or both be NULL");
+  if (V > 0 && (!region_maps || !map_offsets)) return fail(SCOUP_ERR_INVALID_ARG, "region maps are NULL");
+  if (V > 0 && R_total > 0 && (!code_idx || !code_val)) return fail(SCOUP_ERR_INVALID_ARG, "code table is NULL");
+  for (int v = 0; v < V; ++v)
+    if (map_offsets[v] < 0) return fail(SCOUP_ERR_INVALID_ARG, "map_offsets[%d] < 0", v);
+  if (!workspace) return fail(SCOUP_ERR_INVALID_ARG, "workspace is NULL");
+  const int64_t code_rows_k = s > K ? (int64_t)R_total * K : 0;
+  const size_t fixed = uplift_fixed_bytes(scene->n, max_tiles, code_rows_k);
+  if (ws_bytes < fixed)
+    return fail(SCOUP_ERR_OOM, "workspace too small: %zu < %zu bytes before tile lists", ws_bytes, fixed);
+
+  cudaStream_t st = (cudaStream_t)stream;
+  int32_t* fci = nullptr;
+  float* fcv = nullptr;
+  UpliftWs ws = carve(workspace, ws_bytes, scene->n, max_tiles, code_rows_k, &fci, &fcv);
+  const int64_t n = scene->n;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(ws.hdr, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
+  if (n > 0 && accum_mode == 0 &&
+      (e = cudaMemsetAsync(accum, 0, sizeof(float) * (size_t)n * (size_t)C, st)) != cudaSuccess)
+    return cuda_fail(e, "memset accum");
+  if ((e = cudaMemsetAsync(ws.tile_count, 0, sizeof(uint32_t) * ((size_t)max_tiles + 1), st)) != cudaSuccess)
+    return cuda_fail(e, "memset");
+  const int32_t* ci = code_idx;
+  const float* cv = code_val;
+  int s_eff = s;
+  if (s > K && R_total > 0) {
+    PhaseScope ps(SCOUP_PHASE_CODE_TOPK, st);
+    if ((e = launch_code_topk(code_idx, code_val, R_total, s, K, fci, fcv, st)) != cudaSuccess)
+      return cuda_fail(e, "code top-k");
+    ci = fci;
+    cv = fcv;
+    s_eff = K;
+  }
+  if (n > 0 && V > 0) {
+    {
+      PhaseScope ps(SCOUP_PHASE_TAU, st);
+      if ((e = launch_tau(scene->opacity, n, ws.tau, st)) != cudaSuccess) return cuda_fail(e, "tau");
+    }
+    for (int v = 0; v < V; ++v) {
+      const CamArgs ca = cam_args(cams[v]);
+      {
+        PhaseScope ps(SCOUP_PHASE_PREPROCESS, st);
+        if ((e = launch_preprocess(*scene, ca, ws, st)) != cudaSuccess) return cuda_fail(e, "preprocess");
+      }
+      {
+        PhaseScope ps(SCOUP_PHASE_BINNING, st);
+        if ((e = launch_binning(ca, n, ws, st)) != cudaSuccess) return cuda_fail(e, "binning");
+      }
+      {
+        PhaseScope ps(SCOUP_PHASE_UPLIFT_TILES, st);
+        if ((e = launch_uplift_tiles(ca, ws, region_maps + map_offsets[v], R_total, ci, cv, s_eff, C,
+                                     accum, st)) != cudaSuccess)
+          return cuda_fail(e, "uplift tiles");
+      }
+    }
+  }
+  if (topk_idx && n > 0) {
+    PhaseScope ps(SCOUP_PHASE_TOPK, st);
+    if ((e = launch_topk(accum, n, C, K, topk_idx, topk_val, st)) != cudaSuccess) return cuda_fail(e, "top-k");
+  }
+  if (stats) return finish_with_stats(ws.hdr, stats, st);
+  return SCOUP_OK;
+}
+
+int scoup_topk(const float* accum, int64_t n, int32_t C, int32_t K, int32_t* topk_idx,
+               float* topk_val, void* stream) {
+  if (n < 0) return fail(SCOUP_ERR_INVALID_ARG, "n < 0");
+  if (C < 1 || C > 1024) return fail(SCOUP_ERR_INVALID_ARG, "C=%d outside [1, 1024]", C);
+  if (K < 1 || K > C) return fail(SCOUP_ERR_INVALID_ARG, "K=%d outside [1, C=%d]", K, C);
+  if (n > 0 && (!accum || !topk_idx || !topk_val)) return fail(SCOUP_ERR_INVALID_ARG, "NULL array");
+  PhaseScope ps(SCOUP_PHASE_TOPK, (cudaStream_t)stream);
+  cudaError_t e = launch_topk(accum, n, C, K, topk_idx, topk_val, (cudaStream_t)stream);
+  return e == cudaSuccess ? SCOUP_OK : cuda_fail(e, "top-k");
+}
+
+int scoup_read_stats(const void* workspace, size_t ws_bytes, scoup_stats* stats, void* stream) {
+  if (!workspace || ws_bytes < sizeof(WsHeader)) return fail(SCOUP_ERR_INVALID_ARG, "bad workspace");
+  if (!stats) return fail(SCOUP_ERR_INVALID_ARG, "stats is NULL");
+  return finish_with_stats((const WsHeader*)workspace, stats, (cudaStream_t)stream);
+}
+
+int scoup_profile_enable(int32_t enable) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_on = enable != 0;
+  return SCOUP_OK;
+}
+
+int scoup_profile_read(double* ms, int64_t* launches, int32_t nphases) {
+  if (nphases < 0 || (nphases > 0 && (!ms || !launches)))
+    return fail(SCOUP_ERR_INVALID_ARG, "bad profile output arrays");
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (const EventPair& p : g_prof_pending) {
+    cudaError_t e = cudaEventSynchronize(p.b);
+    if (e != cudaSuccess) return cuda_fail(e, "profile event");
+    float t = 0.0f;
+    cudaEventElapsedTime(&t, p.a, p.b);
+    g_prof_ms[p.phase] += t;
+    g_prof_n[p.phase] += 1;
+    g_prof_pool.push_back(p.a);
+    g_prof_pool.push_back(p.b);
+  }
+  g_prof_pending.clear();
+  for (int i = 0; i < nphases && i < SCOUP_NUM_PHASES; ++i) {
+    ms[i] = g_prof_ms[i];
+    launches[i] = g_prof_n[i];
+    g_prof_ms[i] = 0.0;
+    g_prof_n[i] = 0;
+  }
+  return SCOUP_OK;
+}
+
+int64_t scoup_launch_count(void) { return (int64_t)g_launches.load(); }
+
+}  // extern "C"

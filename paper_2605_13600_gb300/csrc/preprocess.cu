@@ -1,0 +1,171 @@
+// preprocess.cu -- per-view projection of the Gaussians (paper Sec. 3).
+//
+// Standard 3DGS projection: camera-space mean, near-plane cull at z <= 0.2,
+// Sigma3 = (R S)(R S)^T from the normalised quaternion and scales, EWA 2D
+// covariance T Sigma3 T^T + 0.3 I with T = J Rv and the Jacobian J taken at
+// the tangent clamped to 1.3x the half field of view, inverse covariance,
+// radius ceil(3 sqrt(lambda_max)) with the 0.1 eigenvalue floor, and the
+// 16x16 tile rectangle.
+//
+// This translation unit is compiled with --fmad=false: every expression is
+// evaluated left to right in IEEE binary32 with each operation rounded, in the
+// operation order written here, so the discrete outcomes (cull, radius,
+// rectangle, depth) are reproducible on any IEEE binary32 machine.
+#include <math.h>
+
+#include "scoup_internal.cuh"
+
+namespace scoup {
+namespace {
+
+__device__ __forceinline__ int tile_clamp(float v, int g) {
+  if (!(v > 0.0f)) return 0;
+  if (v > (float)g) return g;
+  return (int)v;
+}
+
+// Smallest binary32 tau with o * exp(tau) >= 1/255, i.e. ceil_f(-log(255 o)).
+__global__ void tau_kernel(const float* __restrict__ opacity, int64_t n, float* __restrict__ tau) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double o = (double)opacity[i];
+    double t = o > 0.0 ? -log(255.0 * o) : INFINITY;
+    float th = (float)t;
+    if ((double)th < t) th = nextafterf(th, INFINITY);
+    tau[i] = th;
+  }
+}
+
+__global__ void __launch_bounds__(256) preprocess_kernel(
+    const float* __restrict__ means, const float* __restrict__ scales,
+    const float* __restrict__ quats, const float* __restrict__ opacity,
+    const float* __restrict__ tau, int64_t n, CamArgs cam, ProjRec* __restrict__ proj,
+    uint32_t* __restrict__ depth_bits, ushort4* __restrict__ rects, WsHeader* __restrict__ hdr) {
+  unsigned long long my_vis = 0, my_dups = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    ushort4 rect = make_ushort4(0, 0, 0, 0);
+    const float m0 = means[3 * i], m1 = means[3 * i + 1], m2 = means[3 * i + 2];
+    const float* W = cam.vm;
+    float t0 = W[0] * m0 + W[1] * m1 + W[2] * m2 + W[3];
+    float t1 = W[4] * m0 + W[5] * m1 + W[6] * m2 + W[7];
+    float t2 = W[8] * m0 + W[9] * m1 + W[10] * m2 + W[11];
+    depth_bits[i] = __float_as_uint(t2);
+    if (t2 > 0.2f) {
+      const float4 q = *reinterpret_cast<const float4*>(quats + 4 * i);
+      const float s0 = scales[3 * i], s1 = scales[3 * i + 1], s2 = scales[3 * i + 2];
+      float qn = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
+      float inv = 1.0f / sqrtf(qn);
+      float w = q.x * inv, x = q.y * inv, y = q.z * inv, z = q.w * inv;
+      float R00 = 1.0f - 2.0f * (y * y + z * z);
+      float R01 = 2.0f * (x * y - w * z);
+      float R02 = 2.0f * (x * z + w * y);
+      float R10 = 2.0f * (x * y + w * z);
+      float R11 = 1.0f - 2.0f * (x * x + z * z);
+      float R12 = 2.0f * (y * z - w * x);
+      float R20 = 2.0f * (x * z - w * y);
+      float R21 = 2.0f * (y * z + w * x);
+      float R22 = 1.0f - 2.0f * (x * x + y * y);
+      float M00 = R00 * s0, M01 = R01 * s1, M02 = R02 * s2;
+      float M10 = R10 * s0, M11 = R11 * s1, M12 = R12 * s2;
+      float M20 = R20 * s0, M21 = R21 * s1, M22 = R22 * s2;
+      float S00 = M00 * M00 + M01 * M01 + M02 * M02;
+      float S01 = M00 * M10 + M01 * M11 + M02 * M12;
+      float S02 = M00 * M20 + M01 * M21 + M02 * M22;
+      float S11 = M10 * M10 + M11 * M11 + M12 * M12;
+      float S12 = M10 * M20 + M11 * M21 + M12 * M22;
+      float S22 = M20 * M20 + M21 * M21 + M22 * M22;
+      // S10 = S01, S20 = S02, S21 = S12 (each is the same rounded expression)
+
+      float limx = 1.3f * (0.5f * (float)cam.width / cam.fx);
+      float limy = 1.3f * (0.5f * (float)cam.height / cam.fy);
+      float txz = t0 / t2, tyz = t1 / t2;
+      float txc = fminf(limx, fmaxf(-limx, txz)) * t2;
+      float tyc = fminf(limy, fmaxf(-limy, tyz)) * t2;
+      float tz2 = t2 * t2;
+      float j00 = cam.fx / t2;
+      float j02 = -(cam.fx * txc) / tz2;
+      float j11 = cam.fy / t2;
+      float j12 = -(cam.fy * tyc) / tz2;
+      float T00 = j00 * W[0] + j02 * W[8];
+      float T01 = j00 * W[1] + j02 * W[9];
+      float T02 = j00 * W[2] + j02 * W[10];
+      float T10 = j11 * W[4] + j12 * W[8];
+      float T11 = j11 * W[5] + j12 * W[9];
+      float T12 = j11 * W[6] + j12 * W[10];
+      float U00 = T00 * S00 + T01 * S01 + T02 * S02;
+      float U01 = T00 * S01 + T01 * S11 + T02 * S12;
+      float U02 = T00 * S02 + T01 * S12 + T02 * S22;
+      float U10 = T10 * S00 + T11 * S01 + T12 * S02;
+      float U11 = T10 * S01 + T11 * S11 + T12 * S12;
+      float U12 = T10 * S02 + T11 * S12 + T12 * S22;
+      float ca2 = U00 * T00 + U01 * T01 + U02 * T02 + 0.3f;
+      float cb2 = U00 * T10 + U01 * T11 + U02 * T12;
+      float cc2 = U10 * T10 + U11 * T11 + U12 * T12 + 0.3f;
+      float det = ca2 * cc2 - cb2 * cb2;
+      if (det > 0.0f) {
+        float idet = 1.0f / det;
+        float con_a = cc2 * idet, con_b = -cb2 * idet, con_c = ca2 * idet;
+        float mid = 0.5f * (ca2 + cc2);
+        float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - det));
+        float r = ceilf(3.0f * sqrtf(lam));
+        float mx = cam.fx * txz + cam.cx - 0.5f;
+        float my = cam.fy * tyz + cam.cy - 0.5f;
+        int xlo = tile_clamp(floorf((mx - r) / 16.0f), cam.gx);
+        int xhi = tile_clamp(floorf((mx + r + 15.0f) / 16.0f), cam.gx);
+        int ylo = tile_clamp(floorf((my - r) / 16.0f), cam.gy);
+        int yhi = tile_clamp(floorf((my + r + 15.0f) / 16.0f), cam.gy);
+        if (xhi > xlo && yhi > ylo) {
+          rect = make_ushort4((unsigned short)xlo, (unsigned short)ylo, (unsigned short)xhi,
+                              (unsigned short)yhi);
+          ProjRec pr;
+          pr.a = make_float4(mx, my, -0.5f * con_a, -con_b);
+          pr.b = make_float4(-0.5f * con_c, opacity[i], tau[i], 0.0f);
+          proj[i] = pr;
+          my_vis += 1;
+          my_dups += (unsigned long long)(xhi - xlo) * (unsigned long long)(yhi - ylo);
+        }
+      }
+    }
+    rects[i] = rect;
+  }
+  // block reduction of the counters
+  for (int off = 16; off > 0; off >>= 1) {
+    my_vis += __shfl_down_sync(0xffffffffu, my_vis, off);
+    my_dups += __shfl_down_sync(0xffffffffu, my_dups, off);
+  }
+  __shared__ unsigned long long s_vis[8], s_dups[8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { s_vis[warp] = my_vis; s_dups[warp] = my_dups; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long a = 0, b = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { a += s_vis[k]; b += s_dups[k]; }
+    if (a) atomicAdd(&hdr->visible, a);
+    if (b) atomicAdd(&hdr->duplicates, b);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_tau(const float* opacity, int64_t n, float* tau, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  tau_kernel<<<blocks, 256, 0, st>>>(opacity, n, tau);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_preprocess(const scoup_scene& sc, const CamArgs& cam, const UpliftWs& ws,
+                              cudaStream_t st) {
+  if (sc.n <= 0) return cudaSuccess;
+  int blocks = (int)((sc.n + 255) / 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  preprocess_kernel<<<blocks, 256, 0, st>>>(sc.means, sc.scales, sc.quats, sc.opacity, ws.tau,
+                                            sc.n, cam, ws.proj, ws.depth, ws.rect, ws.hdr);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace scoup

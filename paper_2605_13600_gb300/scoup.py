@@ -1,0 +1,196 @@
+"""Python binding of the C ABI: argument marshalling only.
+
+Functions carry the C names (``scoup_uplift`` ...) and take torch tensors
+already on the GPU; every step of the computation runs in libscoup.so.
+``Uplift`` is a convenience wrapper that sizes and allocates the workspace
+and outputs with torch and then calls the same entry points.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _lib
+from ._lib import Camera, Scene, ScoupError, Stats, check, load
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _need(t, dtype, name):
+    import torch
+    if t is None:
+        return
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() and not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+
+
+def scene_struct(means, scales, quats, opacity) -> Scene:
+    import torch
+    for t, nm in ((means, "means"), (scales, "scales"), (quats, "quats"), (opacity, "opacity")):
+        _need(t, torch.float32, nm)
+    sc = Scene()
+    sc.n = int(means.shape[0])
+    sc.means, sc.scales, sc.quats, sc.opacity = _ptr(means), _ptr(scales), _ptr(quats), _ptr(opacity)
+    sc._keep = (means, scales, quats, opacity)
+    return sc
+
+
+def camera_array(cams: Sequence) -> ct.Array:
+    arr = (Camera * max(1, len(cams)))()
+    for k, c in enumerate(cams):
+        vm = np.asarray(c.viewmat, np.float32).reshape(12)
+        for i in range(12):
+            arr[k].viewmat[i] = float(vm[i])
+        arr[k].fx, arr[k].fy, arr[k].cx, arr[k].cy = float(c.fx), float(c.fy), float(c.cx), float(c.cy)
+        arr[k].width, arr[k].height = int(c.width), int(c.height)
+    return arr
+
+
+def scoup_version() -> str:
+    return load().scoup_version().decode()
+
+
+def scoup_uplift_workspace_size(n: int, max_width: int, max_height: int, dup_capacity: int) -> int:
+    return int(load().scoup_uplift_workspace_size(n, max_width, max_height, dup_capacity))
+
+
+def scoup_uplift_plan(scene: Scene, cams: Sequence, workspace, stream=None) -> int:
+    import torch
+    _need(workspace, torch.uint8, "workspace")
+    out = ct.c_int64(0)
+    ca = camera_array(cams)
+    check(load().scoup_uplift_plan(ct.byref(scene), ct.cast(ca, ct.c_void_p), len(cams),
+                                   _ptr(workspace), workspace.numel(), ct.byref(out), _stream(stream)))
+    return int(out.value)
+
+
+def scoup_uplift(scene: Scene, cams: Sequence, region_maps, map_offsets, R_total: int, code_idx,
+                 code_val, s: int, C: int, K: int, accum, accum_mode: int, topk_idx, topk_val,
+                 workspace, stats: bool = True, stream=None):
+    """Returns the stats dict (synchronising) when stats=True, else None."""
+    import torch
+    _need(region_maps, torch.int32, "region_maps")
+    _need(code_idx, torch.int32, "code_idx")
+    _need(code_val, torch.float32, "code_val")
+    _need(accum, torch.float32, "accum")
+    _need(topk_idx, torch.int32, "topk_idx")
+    _need(topk_val, torch.float32, "topk_val")
+    _need(workspace, torch.uint8, "workspace")
+    offs = np.ascontiguousarray(np.asarray(map_offsets, np.int64)[:max(1, len(cams))])
+    ca = camera_array(cams)
+    st = Stats()
+    rc = load().scoup_uplift(ct.byref(scene), ct.cast(ca, ct.c_void_p), len(cams), _ptr(region_maps),
+                             offs.ctypes.data_as(ct.c_void_p), int(R_total), _ptr(code_idx),
+                             _ptr(code_val), int(s), int(C), int(K), _ptr(accum), int(accum_mode),
+                             _ptr(topk_idx), _ptr(topk_val), _ptr(workspace),
+                             0 if workspace is None else workspace.numel(),
+                             ct.byref(st) if stats else None, _stream(stream))
+    check(rc)
+    return st.as_dict() if stats else None
+
+
+def scoup_topk(accum, K: int, topk_idx, topk_val, stream=None) -> None:
+    import torch
+    _need(accum, torch.float32, "accum")
+    _need(topk_idx, torch.int32, "topk_idx")
+    _need(topk_val, torch.float32, "topk_val")
+    n, C = accum.shape
+    check(load().scoup_topk(_ptr(accum), n, C, K, _ptr(topk_idx), _ptr(topk_val), _stream(stream)))
+
+
+def scoup_read_stats(workspace, stream=None) -> dict:
+    st = Stats()
+    check(load().scoup_read_stats(_ptr(workspace), workspace.numel(), ct.byref(st), _stream(stream)))
+    return st.as_dict()
+
+
+def scoup_profile_enable(enable: bool) -> None:
+    check(load().scoup_profile_enable(1 if enable else 0))
+
+
+def scoup_profile_read() -> dict:
+    """{phase: (milliseconds, timed launch groups)} since the previous read."""
+    ms = np.zeros(_lib.NUM_PHASES, np.float64)
+    cnt = np.zeros(_lib.NUM_PHASES, np.int64)
+    check(load().scoup_profile_read(ms.ctypes.data_as(ct.c_void_p), cnt.ctypes.data_as(ct.c_void_p),
+                                    _lib.NUM_PHASES))
+    return {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(_lib.PHASES) if cnt[i]}
+
+
+def scoup_launch_count() -> int:
+    return int(load().scoup_launch_count())
+
+
+class Uplift:
+    """Holds device copies of one uplift workload and a planned workspace.
+
+    ``wl`` is any object with the fields of ``synth.UpliftWorkload`` (NumPy
+    arrays); they are copied to the GPU once.  ``run()`` enqueues one full
+    uplift (all views + Top-K) on the current stream.
+    """
+
+    def __init__(self, wl, device: str = "cuda", dup_capacity: Optional[int] = None,
+                 headroom: float = 1.0):
+        import torch
+        dev = torch.device(device)
+        sc = wl.scene
+        self.means = torch.as_tensor(sc.means, device=dev).contiguous()
+        self.scales = torch.as_tensor(sc.scales, device=dev).contiguous()
+        self.quats = torch.as_tensor(sc.quats, device=dev).contiguous()
+        self.opacity = torch.as_tensor(sc.opacity, device=dev).contiguous()
+        self.scene = scene_struct(self.means, self.scales, self.quats, self.opacity)
+        self.cams = list(wl.cams)
+        self.region_maps = torch.as_tensor(wl.region_maps, device=dev).contiguous()
+        self.map_offsets = np.asarray(wl.map_offsets, np.int64)
+        self.code_idx = torch.as_tensor(wl.code_idx, device=dev).contiguous()
+        self.code_val = torch.as_tensor(wl.code_val, device=dev).contiguous()
+        self.R_total = int(wl.code_idx.shape[0])
+        self.s, self.C, self.K = int(wl.s), int(wl.C), int(wl.K)
+        n = sc.n
+        self.n = n
+        maxw = max([c.width for c in self.cams] + [1])
+        maxh = max([c.height for c in self.cams] + [1])
+        extra = 8 * self.R_total * self.K + 1024 if self.s > self.K else 0
+        if dup_capacity is None:
+            probe = torch.empty(scoup_uplift_workspace_size(n, maxw, maxh, 0) + extra,
+                                dtype=torch.uint8, device=dev)
+            dup_capacity = int(scoup_uplift_plan(self.scene, self.cams, probe) * headroom) + 1
+            del probe
+        self.dup_capacity = dup_capacity
+        self.workspace = torch.empty(scoup_uplift_workspace_size(n, maxw, maxh, dup_capacity) + extra,
+                                     dtype=torch.uint8, device=dev)
+        self.accum = torch.empty((n, self.C), dtype=torch.float32, device=dev)
+        self.topk_idx = torch.empty((n, self.K), dtype=torch.int32, device=dev)
+        self.topk_val = torch.empty((n, self.K), dtype=torch.float32, device=dev)
+
+    def run(self, stats: bool = True, accum_mode: int = 0, views=None, stream=None):
+        cams = self.cams if views is None else [self.cams[v] for v in views]
+        offs = self.map_offsets if views is None else self.map_offsets[list(views)]
+        return scoup_uplift(self.scene, cams, self.region_maps, offs, self.R_total, self.code_idx,
+                            self.code_val, self.s, self.C, self.K, self.accum, accum_mode,
+                            self.topk_idx, self.topk_val, self.workspace, stats=stats, stream=stream)
+
+
+__all__ = ["ScoupError", "scene_struct", "camera_array", "scoup_version",
+           "scoup_uplift_workspace_size", "scoup_uplift_plan", "scoup_uplift", "scoup_topk",
+           "scoup_read_stats", "scoup_profile_enable", "scoup_profile_read", "scoup_launch_count",
+           "Uplift"]

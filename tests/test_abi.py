@@ -1,0 +1,88 @@
+"""The C-ABI library loads, exports every declared symbol, and validates
+arguments on the host (no GPU needed: every call here fails validation
+before any CUDA call)."""
+import ctypes as ct
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2605_13600_gb300 import build
+    build.build()
+    from paper_2605_13600_gb300 import _lib
+    return _lib
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(scoup_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert {"scoup_uplift", "scoup_topk", "scoup_version"} <= names
+    raw = ct.CDLL(lib.LIB_PATH)
+    for nm in sorted(names):
+        assert hasattr(raw, nm), nm
+        assert nm in lib.PROTOS, f"binding lacks {nm}"
+
+
+def test_version_and_sizes(lib):
+    L = lib.load()
+    assert b"sm_103a" in L.scoup_version()
+    assert L.scoup_uplift_workspace_size(-1, 10, 10, 0) == 0
+    assert L.scoup_uplift_workspace_size(10, 0, 10, 0) == 0
+    a = L.scoup_uplift_workspace_size(1000, 160, 120, 0)
+    b = L.scoup_uplift_workspace_size(1000, 160, 120, 100)
+    assert b - a == 800 and a > 1000 * 32
+
+
+def _call_uplift(lib, **kw):
+    L = lib.load()
+    sc = lib.Scene()
+    sc.n = kw.get("n", 4)
+    fake = ct.c_void_p(0x10000)  # never dereferenced: validation fails first
+    sc.means = sc.scales = sc.opacity = fake
+    sc.quats = kw.get("quats", fake)
+    cams = (lib.Camera * 1)()
+    cams[0].fx = cams[0].fy = kw.get("fx", 100.0)
+    cams[0].width, cams[0].height = kw.get("wh", (32, 32))
+    offs = (ct.c_int64 * 1)(0)
+    st = lib.Stats()
+    rc = L.scoup_uplift(ct.byref(sc), ct.cast(cams, ct.c_void_p), kw.get("V", 1), fake,
+                        ct.cast(offs, ct.c_void_p), 4, fake, fake, kw.get("s", 2), kw.get("C", 8),
+                        kw.get("K", 2), kw.get("accum", fake), kw.get("mode", 0), fake, fake,
+                        kw.get("ws", fake), kw.get("ws_bytes", 1 << 30), ct.byref(st), None)
+    return rc, L.scoup_last_error().decode()
+
+
+@pytest.mark.parametrize("kw,frag", [
+    ({"K": 0}, "K=0"), ({"K": 9}, "K=9"), ({"C": 2000, "K": 2}, "C=2000"), ({"s": 0}, "s=0"),
+    ({"s": 65}, "s=65"), ({"V": -1}, "V=-1"), ({"n": -5}, "n=-5"), ({"mode": 2}, "accum_mode"),
+    ({"wh": (0, 10)}, "bad size"), ({"fx": 0.0}, "focal"), ({"accum": None}, "accum"),
+    ({"ws": None}, "workspace"), ({"ws_bytes": 16}, "workspace too small"),
+    ({"quats": ct.c_void_p(0x10004)}, "aligned"),
+])
+def test_uplift_rejects_bad_arguments(lib, kw, frag):
+    rc, msg = _call_uplift(lib, **kw)
+    expect = lib.SCOUP_ERR_OOM if frag == "workspace too small" else lib.SCOUP_ERR_INVALID_ARG
+    assert rc == expect, msg
+    assert frag in msg
+
+
+def test_topk_rejects_bad_arguments(lib):
+    L = lib.load()
+    fake = ct.c_void_p(0x10000)
+    assert L.scoup_topk(fake, 10, 8, 9, fake, fake, None) == lib.SCOUP_ERR_INVALID_ARG
+    assert L.scoup_topk(None, 10, 8, 2, fake, fake, None) == lib.SCOUP_ERR_INVALID_ARG
+    assert L.scoup_topk(fake, -1, 8, 2, fake, fake, None) == lib.SCOUP_ERR_INVALID_ARG

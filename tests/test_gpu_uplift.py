@@ -1,0 +1,197 @@
+"""GPU uplift (scoup_uplift through the C ABI) vs the FP64 oracle.
+
+Element-by-element parity on seeded inputs small enough for the oracle
+(cfg1: 10k Gaussians x 8 views; random scenes with ragged image sizes), edge
+cases (empty scene, no views, all culled, unlabelled pixels, s > K, tiles
+longer than one sort window), device-side error reporting, chunked resume,
+and sampled rows of the full 1M-Gaussian x 200-view workload.
+"""
+import numpy as np
+import pytest
+
+import synth
+from parity import check_accum, check_topk
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_13600_gb300 import build
+    build.build()
+    import paper_2605_13600_gb300 as gb
+    return gb
+
+
+def _run(gb, wl, **kw):
+    up = gb.Uplift(wl, **kw)
+    st = up.run(stats=True)
+    return up, st
+
+
+def _parity(gb, oracle_lib, wl, tag=""):
+    up, st = _run(gb, wl)
+    acc, risk, cnt = oracle_lib.uplift(wl)
+    ga = up.accum.cpu().numpy()
+    info = check_accum(ga, acc, risk)
+    assert info["n_bad"] == 0, (tag, info)
+    tk = check_topk(up.topk_idx.cpu().numpy(), up.topk_val.cpu().numpy(), acc, risk, wl.K)
+    assert tk["n_problems"] == 0, (tag, tk)
+    # integer counters: equal except where a stop decision is at risk
+    assert st["visible"] == cnt["visible"], (tag, st, cnt)
+    assert st["duplicates"] == cnt["duplicates"], (tag, st, cnt)
+    assert abs(st["contributions"] - cnt["contributions"]) <= 2 * cnt["at_risk"], (tag, st, cnt)
+    assert abs(st["evaluated_pairs"] - cnt["evaluated"]) <= 64 * cnt["at_risk"], (tag, st, cnt)
+    return up, st, acc, risk, cnt, info, tk
+
+
+def test_cfg1_parity(gb, oracle_lib, cfg1):
+    up, st, acc, risk, cnt, info, tk = _parity(gb, oracle_lib, cfg1, "cfg1")
+    assert cnt["contributions"] > 1_000_000
+    assert info["max_rel_err"] < 1e-4
+    print("cfg1", st, info, {k: tk[k] for k in ("n_set_diff", "n_tie_ok", "max_val_rel_err")})
+
+
+@pytest.mark.parametrize("seed,W,H,n,V,R,C,s,K,lsm", [
+    (31, 50, 37, 300, 3, 7, 16, 3, 3, -2.6),      # ragged tail in x and y
+    (32, 33, 17, 500, 2, 5, 24, 4, 4, -2.2),
+    (33, 130, 70, 2000, 4, 20, 64, 4, 4, -3.0),
+    (34, 64, 48, 800, 2, 9, 32, 6, 3, -2.5),      # s > K: per-code Top-K first
+    (35, 16, 16, 100, 1, 2, 8, 2, 8, -2.0),       # single tile, K = C
+])
+def test_random_scene_parity(gb, oracle_lib, seed, W, H, n, V, R, C, s, K, lsm):
+    wl = synth.tiny_workload(seed, n=n, width=W, height=H, V=V, R=R, C=C, s=s, K=K,
+                             log_scale_mean=lsm)
+    _parity(gb, oracle_lib, wl, f"seed{seed}")
+
+
+def test_long_tile_lists_use_several_windows(gb, oracle_lib):
+    """Thousands of Gaussians over a 48x32 image: every tile list is longer
+    than one sort window, so the windowed radix select is exercised."""
+    wl = synth.tiny_workload(36, n=6000, width=48, height=32, V=2, R=4, C=16, s=3, K=3,
+                             log_scale_mean=-2.0)
+    wl.scene.opacity[:] = np.minimum(wl.scene.opacity, 0.08)  # keep pixels open for long
+    up, st, *_ = _parity(gb, oracle_lib, wl, "long")
+    assert st["duplicates"] / (2 * 6) > 3000
+
+
+def test_unlabelled_pixels(gb, oracle_lib):
+    wl = synth.tiny_workload(37, n=400, width=40, height=40, V=2, R=5, C=12, s=3, K=3,
+                             log_scale_mean=-2.5)
+    maps = wl.region_maps.copy()
+    maps[::3] = -1
+    wl.region_maps = maps
+    _parity(gb, oracle_lib, wl, "unlabelled")
+
+
+def test_empty_inputs(gb, oracle_lib):
+    import torch
+    wl = synth.tiny_workload(38, n=50, width=32, height=32, V=2)
+    # no views: accumulators stay zero, Top-K is all padding
+    wl0 = synth.UpliftWorkload("noviews", wl.scene, [], np.zeros(1, np.int32), np.zeros(1, np.int64),
+                               wl.code_idx, wl.code_val, wl.C, wl.s, wl.K)
+    up = gb.Uplift(wl0, dup_capacity=16)
+    st = up.run()
+    assert st["contributions"] == 0
+    assert (up.accum == 0).all() and (up.topk_idx == -1).all() and (up.topk_val == 0).all()
+    # no Gaussians
+    wln = synth.UpliftWorkload("empty", wl.scene.subset(np.arange(0)), wl.cams, wl.region_maps,
+                               wl.map_offsets, wl.code_idx, wl.code_val, wl.C, wl.s, wl.K)
+    up = gb.Uplift(wln, dup_capacity=16)
+    assert up.run()["contributions"] == 0
+    # everything behind the cameras
+    far = wl.scene.subset(np.arange(wl.scene.n))
+    far.means[:] = np.array([0.0, 0.0, 0.0], np.float32)
+    cams = [synth.camera_at([0.0, 0.0, 0.1], 32, 32, target=(0.0, 0.0, 1.0))]
+    wlb = synth.UpliftWorkload("culled", far, cams, wl.region_maps[:1024], wl.map_offsets[:2],
+                               wl.code_idx, wl.code_val, wl.C, wl.s, wl.K)
+    up = gb.Uplift(wlb, dup_capacity=16)
+    st = up.run()
+    assert st["visible"] == 0 and (up.topk_idx == -1).all()
+    torch.cuda.synchronize()
+
+
+def test_single_gaussian_closed_form(gb):
+    """Same closed form as the oracle pin: sum of alpha over pixels with alpha >= 1/255."""
+    import math
+    from conftest import axis_camera, make_scene, single_region_workload
+    f, s, z, o = 48.0, 0.125, 2.0, 0.3125
+    cam = axis_camera(64, 48, f=f, z=z)
+    scene = make_scene([0, 0, 0], [s, s, s], [1, 0, 0, 0], [o])
+    wl = single_region_workload(scene, [cam], C=8, code_pairs=[(5, 1.0)], K=4)
+    up, _ = _run(gb, wl)
+    sigma2 = (f * s / z) ** 2 + 0.3
+    ys, xs = np.mgrid[0:48, 0:64]
+    a = o * np.exp(-0.5 * ((xs - 31.5) ** 2 + (ys - 23.5) ** 2) / sigma2)
+    expect = a[a >= 1 / 255].sum()
+    got = float(up.accum[0, 5])
+    assert got == pytest.approx(expect, rel=1e-5)
+    assert up.topk_idx[0].tolist() == [5, -1, -1, -1] and float(up.topk_val[0, 0]) == 1.0
+
+
+def test_chunked_resume_matches_one_shot(gb, cfg1):
+    up = gb.Uplift(cfg1)
+    up.run()
+    one = up.accum.clone()
+    idx1 = up.topk_idx.clone()
+    up.run(views=range(0, 3))
+    up.run(views=range(3, 8), accum_mode=1)
+    np.testing.assert_allclose(up.accum.cpu().numpy(), one.cpu().numpy(), rtol=2e-6, atol=1e-7)
+    assert (up.topk_idx != idx1).sum().item() <= 4
+
+
+def test_capacity_overflow_is_reported(gb, cfg1):
+    up = gb.Uplift(cfg1, dup_capacity=1000)
+    with pytest.raises(gb.ScoupError) as ei:
+        up.run()
+    assert ei.value.code == -4
+
+
+def test_bad_region_id_is_reported(gb):
+    wl = synth.tiny_workload(39, n=100, width=32, height=32, V=1, R=3)
+    wl.region_maps = wl.region_maps.copy()
+    wl.region_maps[100] = 999
+    up = gb.Uplift(wl)
+    with pytest.raises(gb.ScoupError) as ei:
+        up.run()
+    assert ei.value.code == -5
+
+
+def test_topk_kernel_against_oracle(gb, oracle_lib):
+    import torch
+    rng = np.random.default_rng(5)
+    for C, K in ((64, 4), (256, 8), (100, 7), (1000, 16), (24, 24)):
+        acc = (rng.exponential(1.0, (3000, C)) * (rng.random((3000, C)) < 0.3)).astype(np.float32)
+        acc[7] = 0
+        acc[8, :5] = 2.0  # exact ties -> lower atom first
+        a = torch.as_tensor(acc, device="cuda")
+        ti = torch.empty((3000, K), dtype=torch.int32, device="cuda")
+        tv = torch.empty((3000, K), dtype=torch.float32, device="cuda")
+        gb.scoup_topk(a, K, ti, tv)
+        oi, ov = oracle_lib.topk(acc.astype(np.float64), K)
+        assert (ti.cpu().numpy() == oi).all()
+        np.testing.assert_allclose(tv.cpu().numpy(), ov, rtol=2e-6, atol=1e-7)
+
+
+@pytest.mark.slow
+def test_cfg2_full_size_sampled_rows(gb, oracle_lib):
+    """Full 1M-Gaussian x 200-view x 988x731 uplift in the benchmark's launch
+    configuration; rows of 12 sampled Gaussians checked against the oracle."""
+    import torch
+    wl = synth.uplift_cfg2(device="cuda")
+    up = gb.Uplift(wl)
+    st = up.run()
+    assert st["status"] == 0 and st["contributions"] > 1e9
+    acc_g = up.accum
+    hit = (acc_g.sum(1) > 0).nonzero().flatten().cpu().numpy()
+    rows = np.random.default_rng(0).choice(hit, 12, replace=False)
+    acc, risk, cnt = oracle_lib.uplift(wl, rows=rows)
+    ga = acc_g[torch.as_tensor(rows, device="cuda")].cpu().numpy()
+    info = check_accum(ga, acc, risk)
+    assert info["n_bad"] == 0, info
+    tk = check_topk(up.topk_idx.cpu().numpy()[rows], up.topk_val.cpu().numpy()[rows], acc, risk, wl.K)
+    assert tk["n_problems"] == 0, tk
+    print("cfg2 sampled", info, st)
