@@ -65,11 +65,12 @@ typedef struct scoup_camera {
 /* Counters of one uplift or render call (summed over its views). */
 typedef struct scoup_stats {
   int64_t visible;          /* (Gaussian, view) pairs that survive culling */
-  int64_t duplicates;       /* (Gaussian, tile) pairs emitted by binning */
+  int64_t duplicates;       /* (Gaussian, tile) pairs of the 3DGS tile rectangles */
   int64_t evaluated_pairs;  /* (pixel, Gaussian) pairs examined while the pixel was active */
   int64_t contributions;    /* accepted pairs: alpha >= 1/255, before the transmittance stop */
   int64_t flushes;          /* (Gaussian, tile, region) partial sums flushed to the accumulator */
   int64_t atomics;          /* global accumulator atomics issued */
+  int64_t listed;           /* (Gaussian, tile) pairs kept after the exact alpha-reach test */
   int32_t status;           /* SCOUP_OK or the first device-side error */
   int32_t max_dups_view;    /* largest per-view duplicate count seen */
 } scoup_stats;
@@ -141,7 +142,7 @@ int scoup_read_stats(const void* workspace, size_t ws_bytes, scoup_stats* stats,
 /* ------------------------------------------------------------------ */
 
 /* Phases timed by the profiling hooks. */
-#define SCOUP_PHASE_TAU 0          /* per-Gaussian alpha threshold */
+#define SCOUP_PHASE_TAU 0          /* spatial reorder of the scene + per-Gaussian alpha threshold */
 #define SCOUP_PHASE_PREPROCESS 1   /* projection of one view */
 #define SCOUP_PHASE_BINNING 2      /* tile binning of one view (3 kernels) */
 #define SCOUP_PHASE_UPLIFT_TILES 3 /* per-tile sort + composite + scatter of one view */

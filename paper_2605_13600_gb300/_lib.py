@@ -40,7 +40,8 @@ class Camera(ct.Structure):
 class Stats(ct.Structure):
     _fields_ = [("visible", ct.c_int64), ("duplicates", ct.c_int64),
                 ("evaluated_pairs", ct.c_int64), ("contributions", ct.c_int64),
-                ("flushes", ct.c_int64), ("atomics", ct.c_int64), ("status", ct.c_int32),
+                ("flushes", ct.c_int64), ("atomics", ct.c_int64), ("listed", ct.c_int64),
+                ("status", ct.c_int32),
                 ("max_dups_view", ct.c_int32)]
 
     def as_dict(self):
@@ -69,7 +70,7 @@ PROTOS = {
     "scoup_launch_count": (I64, []),
 }
 
-PHASES = ["tau", "preprocess", "binning", "uplift_tiles", "topk", "code_topk"]
+PHASES = ["reorder", "preprocess", "binning", "uplift_tiles", "topk", "code_topk"]
 NUM_PHASES = 16
 
 

@@ -82,11 +82,15 @@ int tiles_of(int w, int h) { return ((w + kTile - 1) / kTile) * ((h + kTile - 1)
 
 // Fixed part of the uplift workspace (everything but the key lists).
 size_t uplift_fixed_bytes(int64_t n, int max_tiles, int64_t code_rows_k) {
+  const size_t un = (size_t)n;
   size_t b = align_up(sizeof(WsHeader));
-  b += align_up(sizeof(float) * (size_t)n);               // tau
-  b += align_up(sizeof(ProjRec) * (size_t)n);             // proj
-  b += align_up(sizeof(uint32_t) * (size_t)n);            // depth
-  b += align_up(sizeof(ushort4) * (size_t)n);             // rect
+  b += 2 * align_up(sizeof(float) * 3 * un);              // spatially ordered means, scales
+  b += align_up(sizeof(float) * 4 * un);                  // quats
+  b += 4 * align_up(sizeof(float) * un);                  // opacity, tau, orig, cell
+  b += align_up(reorder_scratch_bytes());
+  b += align_up(sizeof(ProjRec) * un);                    // proj
+  b += align_up(sizeof(uint32_t) * un);                   // depth
+  b += align_up(sizeof(ushort4) * un);                    // rect
   b += 3 * align_up(sizeof(uint32_t) * ((size_t)max_tiles + 1));
   b += 2 * align_up((size_t)code_rows_k * 4);             // filtered codes (s > K)
   return b;
@@ -97,12 +101,20 @@ UpliftWs carve(void* ws, size_t bytes, int64_t n, int max_tiles, int64_t code_ro
   UpliftWs w;
   char* p = (char*)ws;
   size_t off = 0;
+  const size_t un = (size_t)n;
   auto take = [&](size_t sz) { char* q = p + off; off += align_up(sz); return (void*)q; };
   w.hdr = (WsHeader*)take(sizeof(WsHeader));
-  w.tau = (float*)take(sizeof(float) * (size_t)n);
-  w.proj = (ProjRec*)take(sizeof(ProjRec) * (size_t)n);
-  w.depth = (uint32_t*)take(sizeof(uint32_t) * (size_t)n);
-  w.rect = (ushort4*)take(sizeof(ushort4) * (size_t)n);
+  w.sp.means = (float*)take(sizeof(float) * 3 * un);
+  w.sp.scales = (float*)take(sizeof(float) * 3 * un);
+  w.sp.quats = (float*)take(sizeof(float) * 4 * un);
+  w.sp.opacity = (float*)take(sizeof(float) * un);
+  w.sp.tau = (float*)take(sizeof(float) * un);
+  w.sp.orig = (int32_t*)take(sizeof(int32_t) * un);
+  w.cell = (uint32_t*)take(sizeof(uint32_t) * un);
+  w.cells_scratch = (uint32_t*)take(reorder_scratch_bytes());
+  w.proj = (ProjRec*)take(sizeof(ProjRec) * un);
+  w.depth = (uint32_t*)take(sizeof(uint32_t) * un);
+  w.rect = (ushort4*)take(sizeof(ushort4) * un);
   w.tile_count = (uint32_t*)take(sizeof(uint32_t) * ((size_t)max_tiles + 1));
   w.tile_start = (uint32_t*)take(sizeof(uint32_t) * ((size_t)max_tiles + 1));
   w.tile_fill = (uint32_t*)take(sizeof(uint32_t) * ((size_t)max_tiles + 1));
@@ -158,6 +170,7 @@ void read_header(const WsHeader& h, scoup_stats* st) {
   st->contributions = (int64_t)h.contributions;
   st->flushes = (int64_t)h.flushes;
   st->atomics = (int64_t)h.atomics;
+  st->listed = (int64_t)h.listed;
   st->max_dups_view = h.max_dups_view;
   st->status = SCOUP_OK;
   if (h.status & kStatCapacity) st->status = SCOUP_ERR_CAPACITY;
@@ -213,13 +226,13 @@ int scoup_uplift_plan(const scoup_scene* scene, const scoup_camera* cams, int32_
   UpliftWs ws = carve(workspace, ws_bytes, scene->n, max_tiles, 0, &ci, &cv);
   cudaError_t e = cudaMemsetAsync(ws.hdr, 0, sizeof(WsHeader), st);
   if (e != cudaSuccess) return cuda_fail(e, "memset");
-  if ((e = launch_tau(scene->opacity, scene->n, ws.tau, st)) != cudaSuccess) return cuda_fail(e, "tau");
+  if ((e = launch_reorder(*scene, ws, st)) != cudaSuccess) return cuda_fail(e, "reorder");
   int64_t best = 0;
   for (int v = 0; v < V; ++v) {
     const CamArgs ca = cam_args(cams[v]);
     if ((e = cudaMemsetAsync(&ws.hdr->duplicates, 0, sizeof(unsigned long long), st)) != cudaSuccess)
       return cuda_fail(e, "memset");
-    if ((e = launch_preprocess(*scene, ca, ws, st)) != cudaSuccess) return cuda_fail(e, "preprocess");
+    if ((e = launch_preprocess(*scene, ca, ws, v & 1, st)) != cudaSuccess) return cuda_fail(e, "preprocess");
     unsigned long long d = 0;
     if ((e = cudaMemcpyAsync(&d, &ws.hdr->duplicates, sizeof(d), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
       return cuda_fail(e, "read");
@@ -283,22 +296,22 @@ int scoup_uplift(const scoup_scene* scene, const scoup_camera* cams, int32_t V,
   if (n > 0 && V > 0) {
     {
       PhaseScope ps(SCOUP_PHASE_TAU, st);
-      if ((e = launch_tau(scene->opacity, n, ws.tau, st)) != cudaSuccess) return cuda_fail(e, "tau");
+      if ((e = launch_reorder(*scene, ws, st)) != cudaSuccess) return cuda_fail(e, "reorder");
     }
     for (int v = 0; v < V; ++v) {
       const CamArgs ca = cam_args(cams[v]);
       {
         PhaseScope ps(SCOUP_PHASE_PREPROCESS, st);
-        if ((e = launch_preprocess(*scene, ca, ws, st)) != cudaSuccess) return cuda_fail(e, "preprocess");
+        if ((e = launch_preprocess(*scene, ca, ws, v & 1, st)) != cudaSuccess) return cuda_fail(e, "preprocess");
       }
       {
         PhaseScope ps(SCOUP_PHASE_BINNING, st);
-        if ((e = launch_binning(ca, n, ws, st)) != cudaSuccess) return cuda_fail(e, "binning");
+        if ((e = launch_binning(ca, n, ws, v & 1, st)) != cudaSuccess) return cuda_fail(e, "binning");
       }
       {
         PhaseScope ps(SCOUP_PHASE_UPLIFT_TILES, st);
-        if ((e = launch_uplift_tiles(ca, ws, region_maps + map_offsets[v], R_total, ci, cv, s_eff, C,
-                                     accum, st)) != cudaSuccess)
+        if ((e = launch_uplift_tiles(ca, ws, v & 1, region_maps + map_offsets[v], R_total, ci, cv, s_eff,
+                                     C, accum, st)) != cudaSuccess)
           return cuda_fail(e, "uplift tiles");
       }
     }

@@ -1,46 +1,131 @@
 // binning.cu -- tile binning of one view's projected Gaussians.
 //
-// Every visible Gaussian is listed in each 16x16 tile of its rectangle (the
-// 3DGS rule: membership is tile-granular).  The per-tile lists hold 64-bit
-// keys (depth bits << 32 | Gaussian id); they are left unordered here and
-// ordered front to back (depth, then id) inside the tile kernel.
+// Every visible Gaussian is listed in the 16x16 tiles of its rectangle (the
+// 3DGS rule: membership is tile-granular).  The rectangles here are the 3DGS
+// rectangles cut to the bounding box of each Gaussian's alpha >= 1/255
+// ellipse (by the projection): a dropped tile holds no pixel that passes the
+// alpha test, so the composite is unchanged.  The per-tile lists hold 64-bit
+// keys (depth bits << 32 | original Gaussian index); they are left unordered
+// here and ordered front to back (depth, then index) inside the tile kernel.
 //
-// Counting and filling are privatised per CTA in shared memory (one counter
-// per tile of the view) so that global atomics are one per (CTA, tile) rather
-// than one per (Gaussian, tile); views with more tiles than fit fall back to
-// global atomics.
+// The Gaussians arrive in spatial (Morton) order, so one CTA's chunk covers a
+// compact block of tiles.  Each warp expands the (Gaussian, tile) items of its
+// 32 Gaussians cooperatively, one item per lane per round.  Counting and
+// filling are privatised per CTA in shared memory over the chunk's tile
+// bounding box: global atomics are one per (CTA, tile), and the keys of a CTA
+// land in one contiguous run per tile.  Rectangles larger than kBigRect tiles
+// go straight to the global counters.
 #include "scoup_internal.cuh"
 
 namespace scoup {
 namespace {
 
-constexpr int kBinThreads = 512;
-constexpr int kSmemTilesMax = 24 * 1024;  // 2 x 96 KB of counters at most
+constexpr int kBinThreads = 256;
+constexpr int64_t kChunk = 2048;
+constexpr int kLocalMax = 4096;  // tiles of the per-CTA bounding box kept in shared memory
+constexpr int kBigRect = 256;
+constexpr unsigned kFull = 0xffffffffu;
 
-template <bool kSmem>
-__global__ void __launch_bounds__(kBinThreads) count_kernel(const ushort4* __restrict__ rects,
-                                                            int64_t n, int64_t chunk, int ntiles,
-                                                            int gx, uint32_t* __restrict__ tile_count) {
-  extern __shared__ uint32_t s_cnt[];
-  if (kSmem) {
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) s_cnt[t] = 0;
-    __syncthreads();
+struct LocalBox {
+  int x0, y0, w, h;
+  bool ok;
+  __device__ __forceinline__ int idx(int tx, int ty) const { return (ty - y0) * w + (tx - x0); }
+};
+
+__device__ __forceinline__ bool big(const ushort4& r) { return (r.z - r.x) * (r.w - r.y) > kBigRect; }
+
+// Warp-cooperative expansion of the (Gaussian, tile) items of the 32
+// Gaussians held by the lanes (lane l holds rectangle r): the items are
+// numbered by an exclusive scan of the rectangle areas and dealt out 32 at a
+// time, one per lane, so every lane works on one item per round whatever the
+// rectangle sizes.  f(src_lane, tx, ty) is called for each item.
+template <typename F>
+__device__ __forceinline__ void expand_items(const ushort4& r, F&& f) {
+  const int lane = threadIdx.x & 31;
+  const int w = r.z > r.x ? r.z - r.x : 0, h = r.w > r.y ? r.w - r.y : 0;
+  const int c = w * h;
+  int incl = c;
+  for (int off = 1; off < 32; off <<= 1) {
+    const int y = __shfl_up_sync(kFull, incl, off);
+    if (lane >= off) incl += y;
   }
-  const int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+  const int total = __shfl_sync(kFull, incl, 31);
+  const int excl = incl - c;
+  const int packed = (int)r.x | ((int)r.y << 16);
+  for (int k0 = 0; k0 < total; k0 += 32) {
+    const int item = k0 + lane;
+    int src = 0;  // largest lane whose first item is <= item (it owns the item)
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1) {
+      const int e = __shfl_sync(kFull, excl, src + step);
+      if (e <= item) src += step;
+    }
+    const int e_src = __shfl_sync(kFull, excl, src);
+    const int w_src = __shfl_sync(kFull, w, src);
+    const int p_src = __shfl_sync(kFull, packed, src);
+    if (item < total) {
+      const int local = item - e_src;
+      const int yy = local / w_src;
+      f(src, (p_src & 0xffff) + (local - yy * w_src), (p_src >> 16) + yy);
+    }
+  }
+}
+
+// Block-wide bounding box of the chunk's non-big rectangles.
+__device__ LocalBox chunk_box(const ushort4* __restrict__ rects, int64_t lo, int64_t hi) {
+  __shared__ int s_box[4];
+  if (threadIdx.x == 0) { s_box[0] = 1 << 30; s_box[1] = 1 << 30; s_box[2] = 0; s_box[3] = 0; }
+  __syncthreads();
+  int x0 = 1 << 30, y0 = 1 << 30, x1 = 0, y1 = 0;
   for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
     const ushort4 r = rects[i];
-    for (int ty = r.y; ty < r.w; ++ty)
-      for (int tx = r.x; tx < r.z; ++tx) {
-        const int t = ty * gx + tx;
-        if (kSmem) atomicAdd(&s_cnt[t], 1u);
-        else atomicAdd(&tile_count[t], 1u);
-      }
+    if (r.z <= r.x || big(r)) continue;
+    x0 = min(x0, (int)r.x); y0 = min(y0, (int)r.y); x1 = max(x1, (int)r.z); y1 = max(y1, (int)r.w);
   }
-  if (kSmem) {
-    __syncthreads();
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
-      if (s_cnt[t]) atomicAdd(&tile_count[t], s_cnt[t]);
+  for (int off = 16; off > 0; off >>= 1) {
+    x0 = min(x0, __shfl_xor_sync(0xffffffffu, x0, off));
+    y0 = min(y0, __shfl_xor_sync(0xffffffffu, y0, off));
+    x1 = max(x1, __shfl_xor_sync(0xffffffffu, x1, off));
+    y1 = max(y1, __shfl_xor_sync(0xffffffffu, y1, off));
   }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&s_box[0], x0); atomicMin(&s_box[1], y0); atomicMax(&s_box[2], x1); atomicMax(&s_box[3], y1);
+  }
+  __syncthreads();
+  LocalBox b;
+  b.x0 = s_box[0];
+  b.y0 = s_box[1];
+  b.w = max(0, s_box[2] - s_box[0]);
+  b.h = max(0, s_box[3] - s_box[1]);
+  b.ok = b.w * b.h <= kLocalMax;
+  __syncthreads();
+  return b;
+}
+
+__global__ void __launch_bounds__(kBinThreads) count_kernel(const ushort4* __restrict__ rects, int64_t n,
+                                                            int gx, uint32_t* __restrict__ tile_count) {
+  __shared__ uint32_t s_cnt[kLocalMax];
+  const int64_t lo = blockIdx.x * kChunk, hi = min(n, lo + kChunk);
+  const LocalBox box = chunk_box(rects, lo, hi);
+  const int area = box.w * box.h;
+  if (box.ok)
+    for (int t = threadIdx.x; t < area; t += blockDim.x) s_cnt[t] = 0u;
+  __syncthreads();
+  for (int k = 0; k < (int)(kChunk / kBinThreads); ++k) {
+    const int64_t i = lo + (int64_t)k * kBinThreads + threadIdx.x;
+    const ushort4 r = i < hi ? rects[i] : make_ushort4(0, 0, 0, 0);
+    const unsigned lmask = __ballot_sync(kFull, box.ok && !big(r));
+    expand_items(r, [&](int src, int tx, int ty) {
+      if ((lmask >> src) & 1u) atomicAdd(&s_cnt[box.idx(tx, ty)], 1u);
+      else atomicAdd(&tile_count[ty * gx + tx], 1u);
+    });
+  }
+  __syncthreads();
+  if (box.ok)
+    for (int t = threadIdx.x; t < area; t += blockDim.x) {
+      const uint32_t c = s_cnt[t];
+      if (c) atomicAdd(&tile_count[(box.y0 + t / box.w) * gx + box.x0 + t % box.w], c);
+    }
 }
 
 // Exclusive scan of the tile counts (one CTA), capacity check, and reset of
@@ -48,7 +133,8 @@ __global__ void __launch_bounds__(kBinThreads) count_kernel(const ushort4* __res
 __global__ void __launch_bounds__(1024) scan_kernel(uint32_t* __restrict__ tile_count,
                                                     uint32_t* __restrict__ tile_start,
                                                     uint32_t* __restrict__ tile_fill, int ntiles,
-                                                    int64_t capacity, WsHeader* __restrict__ hdr) {
+                                                    int64_t capacity, WsHeader* __restrict__ hdr,
+                                                    int slot) {
   __shared__ uint32_t s_warp[32];
   __shared__ unsigned long long s_carry;
   if (threadIdx.x == 0) s_carry = 0;
@@ -85,88 +171,107 @@ __global__ void __launch_bounds__(1024) scan_kernel(uint32_t* __restrict__ tile_
     __syncthreads();
   }
   if (threadIdx.x == 0) {
+    // the other depth-range slot is next written by the following view's projection
+    hdr->drange[slot ^ 1][0] = 0xffffffffu;
+    hdr->drange[slot ^ 1][1] = 0u;
     const unsigned long long total = s_carry;
     tile_start[ntiles] = (uint32_t)total;
     if ((long long)total > capacity || total > 0xffffffffull) atomicOr(&hdr->status, kStatCapacity);
+    atomicAdd(&hdr->listed, total);
     atomicMax(&hdr->max_dups_view, (int)min(total, 0x7fffffffull));
   }
 }
 
-template <bool kSmem>
 __global__ void __launch_bounds__(kBinThreads) fill_kernel(
-    const ushort4* __restrict__ rects, const uint32_t* __restrict__ depth, int64_t n, int64_t chunk,
-    int ntiles, int gx, const uint32_t* __restrict__ tile_start, uint32_t* __restrict__ tile_fill,
+    const ushort4* __restrict__ rects, const uint32_t* __restrict__ depth, const int32_t* __restrict__ orig,
+    int64_t n, int gx, const uint32_t* __restrict__ tile_start, uint32_t* __restrict__ tile_fill,
     unsigned long long* __restrict__ keys, const WsHeader* __restrict__ hdr) {
-  extern __shared__ uint32_t s_mem[];
-  uint32_t* s_cnt = s_mem;
-  uint32_t* s_base = s_mem + ntiles;
+  __shared__ uint32_t s_cnt[kLocalMax];
+  __shared__ uint32_t s_base[kLocalMax];
   if (hdr->status & kStatCapacity) return;
-  const int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
-  if (kSmem) {
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) s_cnt[t] = 0;
+  const int64_t lo = blockIdx.x * kChunk, hi = min(n, lo + kChunk);
+  const LocalBox box = chunk_box(rects, lo, hi);
+  const int area = box.w * box.h;
+  if (box.ok) {
+    for (int t = threadIdx.x; t < area; t += blockDim.x) s_cnt[t] = 0u;
     __syncthreads();
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-      const ushort4 r = rects[i];
-      for (int ty = r.y; ty < r.w; ++ty)
-        for (int tx = r.x; tx < r.z; ++tx) atomicAdd(&s_cnt[ty * gx + tx], 1u);
+    for (int k = 0; k < (int)(kChunk / kBinThreads); ++k) {
+      const int64_t i = lo + (int64_t)k * kBinThreads + threadIdx.x;
+      ushort4 r = i < hi ? rects[i] : make_ushort4(0, 0, 0, 0);
+      if (big(r)) r = make_ushort4(0, 0, 0, 0);
+      expand_items(r, [&](int, int tx, int ty) { atomicAdd(&s_cnt[box.idx(tx, ty)], 1u); });
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+    for (int t = threadIdx.x; t < area; t += blockDim.x) {
       const uint32_t c = s_cnt[t];
-      if (c) s_base[t] = tile_start[t] + atomicAdd(&tile_fill[t], c);
-      s_cnt[t] = 0;
+      if (c) {
+        const int tt = (box.y0 + t / box.w) * gx + box.x0 + t % box.w;
+        s_base[t] = tile_start[tt] + atomicAdd(&tile_fill[tt], c);
+      }
+      s_cnt[t] = 0u;
     }
     __syncthreads();
   }
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    const ushort4 r = rects[i];
-    if (r.z <= r.x) continue;
-    const unsigned long long key = ((unsigned long long)depth[i] << 32) | (unsigned long long)i;
-    for (int ty = r.y; ty < r.w; ++ty)
-      for (int tx = r.x; tx < r.z; ++tx) {
-        const int t = ty * gx + tx;
+  for (int k = 0; k < (int)(kChunk / kBinThreads); ++k) {
+    const int64_t i = lo + (int64_t)k * kBinThreads + threadIdx.x;
+    const ushort4 r = i < hi ? rects[i] : make_ushort4(0, 0, 0, 0);
+    const unsigned long long my_key =
+        i < hi ? (((unsigned long long)depth[i] << 32) | (uint32_t)orig[i]) : 0ull;
+    const unsigned lmask = __ballot_sync(kFull, box.ok && !big(r));
+    // the key of the owning lane is fetched for every round (all lanes shuffle)
+    const int lane = threadIdx.x & 31;
+    const int w = r.z > r.x ? r.z - r.x : 0, h = r.w > r.y ? r.w - r.y : 0;
+    const int c = w * h;
+    int incl = c;
+    for (int off = 1; off < 32; off <<= 1) {
+      const int y = __shfl_up_sync(kFull, incl, off);
+      if (lane >= off) incl += y;
+    }
+    const int total = __shfl_sync(kFull, incl, 31);
+    const int excl = incl - c;
+    const int packed = (int)r.x | ((int)r.y << 16);
+    for (int k0 = 0; k0 < total; k0 += 32) {
+      const int item = k0 + lane;
+      int src = 0;
+#pragma unroll
+      for (int step = 16; step >= 1; step >>= 1) {
+        const int e = __shfl_sync(kFull, excl, src + step);
+        if (e <= item) src += step;
+      }
+      const int e_src = __shfl_sync(kFull, excl, src);
+      const int w_src = __shfl_sync(kFull, w, src);
+      const int p_src = __shfl_sync(kFull, packed, src);
+      const unsigned long long key = __shfl_sync(kFull, my_key, src);
+      if (item < total) {
+        const int local = item - e_src;
+        const int yy = local / w_src;
+        const int tx = (p_src & 0xffff) + (local - yy * w_src), ty = (p_src >> 16) + yy;
         uint32_t pos;
-        if (kSmem) pos = s_base[t] + atomicAdd(&s_cnt[t], 1u);
-        else pos = tile_start[t] + atomicAdd(&tile_fill[t], 1u);
+        if ((lmask >> src) & 1u) {
+          const int t = box.idx(tx, ty);
+          pos = s_base[t] + atomicAdd(&s_cnt[t], 1u);
+        } else {
+          const int t = ty * gx + tx;
+          pos = tile_start[t] + atomicAdd(&tile_fill[t], 1u);
+        }
         keys[pos] = key;
       }
+    }
   }
 }
 
 }  // namespace
 
-cudaError_t launch_binning(const CamArgs& cam, int64_t n, const UpliftWs& ws, cudaStream_t st) {
+cudaError_t launch_binning(const CamArgs& cam, int64_t n, const UpliftWs& ws, int slot,
+                           cudaStream_t st) {
   const int ntiles = cam.gx * cam.gy;
-  if (n > 0) {
-    const int64_t chunk = 4096;
-    const int blocks = (int)((n + chunk - 1) / chunk);
-    if (ntiles <= kSmemTilesMax) {
-      const size_t smem = sizeof(uint32_t) * (size_t)ntiles;
-      cudaFuncSetAttribute(count_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      count_kernel<true><<<blocks, kBinThreads, smem, st>>>(ws.rect, n, chunk, ntiles, cam.gx,
-                                                           ws.tile_count);
-    } else {
-      count_kernel<false><<<blocks, kBinThreads, 0, st>>>(ws.rect, n, chunk, ntiles, cam.gx,
-                                                         ws.tile_count);
-    }
-  }
-  scan_kernel<<<1, 1024, 0, st>>>(ws.tile_count, ws.tile_start, ws.tile_fill, ntiles,
-                                  ws.dup_capacity, ws.hdr);
-  if (n > 0) {
-    const int64_t chunk = 4096;
-    const int blocks = (int)((n + chunk - 1) / chunk);
-    if (ntiles <= kSmemTilesMax) {
-      const size_t smem = 2 * sizeof(uint32_t) * (size_t)ntiles;
-      cudaFuncSetAttribute(fill_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      fill_kernel<true><<<blocks, kBinThreads, smem, st>>>(ws.rect, ws.depth, n, chunk, ntiles,
-                                                          cam.gx, ws.tile_start, ws.tile_fill,
-                                                          ws.keys, ws.hdr);
-    } else {
-      fill_kernel<false><<<blocks, kBinThreads, 0, st>>>(ws.rect, ws.depth, n, chunk, ntiles,
-                                                        cam.gx, ws.tile_start, ws.tile_fill,
-                                                        ws.keys, ws.hdr);
-    }
-  }
+  const int blocks = (int)((n + kChunk - 1) / kChunk);
+  if (n > 0) count_kernel<<<blocks, kBinThreads, 0, st>>>(ws.rect, n, cam.gx, ws.tile_count);
+  scan_kernel<<<1, 1024, 0, st>>>(ws.tile_count, ws.tile_start, ws.tile_fill, ntiles, ws.dup_capacity,
+                                  ws.hdr, slot);
+  if (n > 0)
+    fill_kernel<<<blocks, kBinThreads, 0, st>>>(ws.rect, ws.depth, ws.sp.orig, n, cam.gx, ws.tile_start,
+                                                ws.tile_fill, ws.keys, ws.hdr);
   g_launches += n > 0 ? 3 : 1;
   return cudaGetLastError();
 }

@@ -24,24 +24,17 @@ __device__ __forceinline__ int tile_clamp(float v, int g) {
   return (int)v;
 }
 
-// Smallest binary32 tau with o * exp(tau) >= 1/255, i.e. ceil_f(-log(255 o)).
-__global__ void tau_kernel(const float* __restrict__ opacity, int64_t n, float* __restrict__ tau) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    double o = (double)opacity[i];
-    double t = o > 0.0 ? -log(255.0 * o) : INFINITY;
-    float th = (float)t;
-    if ((double)th < t) th = nextafterf(th, INFINITY);
-    tau[i] = th;
-  }
-}
-
+// Thread p projects Gaussian p of the spatially ordered copy; the record is
+// stored at its original index, depth and rectangle in spatial order.
 __global__ void __launch_bounds__(256) preprocess_kernel(
     const float* __restrict__ means, const float* __restrict__ scales,
     const float* __restrict__ quats, const float* __restrict__ opacity,
-    const float* __restrict__ tau, int64_t n, CamArgs cam, ProjRec* __restrict__ proj,
-    uint32_t* __restrict__ depth_bits, ushort4* __restrict__ rects, WsHeader* __restrict__ hdr) {
+    const float* __restrict__ tau, const int32_t* __restrict__ orig, int64_t n, CamArgs cam,
+    ProjRec* __restrict__ proj,
+    uint32_t* __restrict__ depth_bits, ushort4* __restrict__ rects, WsHeader* __restrict__ hdr,
+    int slot) {
   unsigned long long my_vis = 0, my_dups = 0;
+  uint32_t my_dmin = 0xffffffffu, my_dmax = 0u;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     ushort4 rect = make_ushort4(0, 0, 0, 0);
@@ -116,14 +109,36 @@ __global__ void __launch_bounds__(256) preprocess_kernel(
         int ylo = tile_clamp(floorf((my - r) / 16.0f), cam.gy);
         int yhi = tile_clamp(floorf((my + r + 15.0f) / 16.0f), cam.gy);
         if (xhi > xlo && yhi > ylo) {
-          rect = make_ushort4((unsigned short)xlo, (unsigned short)ylo, (unsigned short)xhi,
-                              (unsigned short)yhi);
           ProjRec pr;
           pr.a = make_float4(mx, my, -0.5f * con_a, -con_b);
           pr.b = make_float4(-0.5f * con_c, opacity[i], tau[i], 0.0f);
-          proj[i] = pr;
+          proj[orig[i]] = pr;
+          // Binning lists only the tiles of the rectangle that also meet the
+          // bounding box of the alpha >= 1/255 ellipse {d : power(d) >= tau}:
+          // half-widths sqrt(-2 tau (A^-1)_xx), sqrt(-2 tau (A^-1)_yy) with
+          // A = [[-2qa, -qb], [-qb, -2qc]], widened by 0.1% + 0.5 px so no
+          // pixel centre that passes the alpha test is left out.
+          const float tau_i = tau[i];
+          int lx0 = xhi, lx1 = xlo, ly0 = yhi, ly1 = ylo;  // empty unless tau < 0
+          if (tau_i < 0.0f) {
+            const float A00 = con_a, A11 = con_c, A01 = con_b;  // = -2qa, -2qc, -qb
+            const float detA = A00 * A11 - A01 * A01;
+            const float ex = sqrtf(-2.0f * tau_i * A11 / detA) * 1.001f + 0.5f;
+            const float ey = sqrtf(-2.0f * tau_i * A00 / detA) * 1.001f + 0.5f;
+            lx0 = max(xlo, tile_clamp(floorf((mx - ex) / 16.0f), cam.gx));
+            lx1 = min(xhi, tile_clamp(floorf((mx + ex) / 16.0f) + 1.0f, cam.gx));
+            ly0 = max(ylo, tile_clamp(floorf((my - ey) / 16.0f), cam.gy));
+            ly1 = min(yhi, tile_clamp(floorf((my + ey) / 16.0f) + 1.0f, cam.gy));
+          }
+          if (lx1 > lx0 && ly1 > ly0)
+            rect = make_ushort4((unsigned short)lx0, (unsigned short)ly0, (unsigned short)lx1,
+                                (unsigned short)ly1);
+          else
+            rect = make_ushort4(0, 0, 0, 0);
           my_vis += 1;
           my_dups += (unsigned long long)(xhi - xlo) * (unsigned long long)(yhi - ylo);
+          my_dmin = min(my_dmin, __float_as_uint(t2));
+          my_dmax = max(my_dmax, __float_as_uint(t2));
         }
       }
     }
@@ -133,37 +148,39 @@ __global__ void __launch_bounds__(256) preprocess_kernel(
   for (int off = 16; off > 0; off >>= 1) {
     my_vis += __shfl_down_sync(0xffffffffu, my_vis, off);
     my_dups += __shfl_down_sync(0xffffffffu, my_dups, off);
+    my_dmin = min(my_dmin, __shfl_down_sync(0xffffffffu, my_dmin, off));
+    my_dmax = max(my_dmax, __shfl_down_sync(0xffffffffu, my_dmax, off));
   }
   __shared__ unsigned long long s_vis[8], s_dups[8];
+  __shared__ uint32_t s_dmin[8], s_dmax[8];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) { s_vis[warp] = my_vis; s_dups[warp] = my_dups; }
+  if (lane == 0) { s_vis[warp] = my_vis; s_dups[warp] = my_dups; s_dmin[warp] = my_dmin; s_dmax[warp] = my_dmax; }
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long a = 0, b = 0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { a += s_vis[k]; b += s_dups[k]; }
-    if (a) atomicAdd(&hdr->visible, a);
-    if (b) atomicAdd(&hdr->duplicates, b);
+    uint32_t lo = 0xffffffffu, hi = 0u;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      a += s_vis[k]; b += s_dups[k]; lo = min(lo, s_dmin[k]); hi = max(hi, s_dmax[k]);
+    }
+    if (a) {
+      atomicAdd(&hdr->visible, a);
+      atomicAdd(&hdr->duplicates, b);
+      atomicMin(&hdr->drange[slot][0], lo);
+      atomicMax(&hdr->drange[slot][1], hi);
+    }
   }
 }
 
 }  // namespace
 
-cudaError_t launch_tau(const float* opacity, int64_t n, float* tau, cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  int blocks = (int)((n + 255) / 256);
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  tau_kernel<<<blocks, 256, 0, st>>>(opacity, n, tau);
-  g_launches += 1;
-  return cudaGetLastError();
-}
-
 cudaError_t launch_preprocess(const scoup_scene& sc, const CamArgs& cam, const UpliftWs& ws,
-                              cudaStream_t st) {
+                              int slot, cudaStream_t st) {
   if (sc.n <= 0) return cudaSuccess;
   int blocks = (int)((sc.n + 255) / 256);
   if (blocks > 152 * 8) blocks = 152 * 8;
-  preprocess_kernel<<<blocks, 256, 0, st>>>(sc.means, sc.scales, sc.quats, sc.opacity, ws.tau,
-                                            sc.n, cam, ws.proj, ws.depth, ws.rect, ws.hdr);
+  preprocess_kernel<<<blocks, 256, 0, st>>>(ws.sp.means, ws.sp.scales, ws.sp.quats, ws.sp.opacity,
+                                            ws.sp.tau, ws.sp.orig, sc.n, cam, ws.proj, ws.depth, ws.rect,
+                                            ws.hdr, slot);
   g_launches += 1;
   return cudaGetLastError();
 }

@@ -20,18 +20,21 @@ constexpr int kTilePixels = kTile * kTile;
 constexpr int kStatCapacity = 1;
 constexpr int kStatDeviceCheck = 2;
 
-// Workspace header: status word + counters, 256 bytes.
+// Workspace header: status word, per-view depth range (double-buffered by
+// view parity), scene bounding box and counters, 256 bytes.
 struct WsHeader {
   int32_t status;
   int32_t max_dups_view;
-  int32_t pad[2];
+  uint32_t drange[2][2];  // [view & 1] = {min, max} float bits of visible depths
+  uint32_t bbox[3][2];    // order-preserving bits of the means' bounding box
   unsigned long long visible;
   unsigned long long duplicates;
   unsigned long long evaluated;
   unsigned long long contributions;
   unsigned long long flushes;
   unsigned long long atomics;
-  unsigned long long reserved[24];
+  unsigned long long listed;
+  unsigned long long reserved[19];
 };
 static_assert(sizeof(WsHeader) == 256, "header size");
 
@@ -45,6 +48,36 @@ struct __align__(16) ProjRec {
   float4 b;
 };
 
+// Conservative test: can any pixel centre of the box [x0, x0+w-1] x
+// [y0, y0+h-1] reach power >= tau for this record?  The maximum of the concave
+// exponent over the box is at the clamped centre or on one of the four edges
+// (each a 1D concave quadratic with its vertex clamped to the edge); the box
+// is rejected only if that maximum is below tau by a margin far above the
+// binary32 rounding of either evaluation, so a rejected box holds no pixel
+// that passes the per-pixel alpha test.
+__device__ __forceinline__ bool box_may_hit(const ProjRec& r, float x0, float y0, float w, float h) {
+  const float mx = r.a.x, my = r.a.y, qa = r.a.z, qb = r.a.w, qc = r.b.x, tau = r.b.z;
+  if (!(qa < 0.0f && qc < 0.0f)) return true;
+  const float x1 = x0 + (w - 1.0f), y1 = y0 + (h - 1.0f);
+  if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return true;
+  const float kx = -qb / (2.0f * qc);  // argmax over dy along an edge x = const: dy = kx * dx
+  const float ky = -qb / (2.0f * qa);  // argmax over dx along an edge y = const: dx = ky * dy
+  float best = -INFINITY;
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const float dx = mx - (e ? x1 : x0);
+    const float dy = my - fminf(y1, fmaxf(y0, my - kx * dx));
+    best = fmaxf(best, qa * dx * dx + qb * dx * dy + qc * dy * dy);
+  }
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const float dy = my - (e ? y1 : y0);
+    const float dx = mx - fminf(x1, fmaxf(x0, mx - ky * dy));
+    best = fmaxf(best, qa * dx * dx + qb * dx * dy + qc * dy * dy);
+  }
+  return best >= tau - (0.01f + 1e-3f * fabsf(best));
+}
+
 struct CamArgs {
   float vm[12];
   float fx, fy, cx, cy;
@@ -52,13 +85,26 @@ struct CamArgs {
   int gx, gy;  // tile grid
 };
 
+// Scene copy in spatial (Morton) order; orig[p] is the caller's index.
+struct SceneP {
+  float* means;    // [n,3]
+  float* scales;   // [n,3]
+  float* quats;    // [n,4], 16-byte aligned
+  float* opacity;  // [n]
+  float* tau;      // [n] alpha-threshold exponent
+  int32_t* orig;   // [n]
+};
+
 // Workspace carve-up for one uplift call.
 struct UpliftWs {
   WsHeader* hdr;
-  float* tau;               // [n] alpha-threshold exponent per Gaussian
-  ProjRec* proj;            // [n]
-  uint32_t* depth;          // [n] float bits of camera depth
-  ushort4* rect;            // [n] tile rect (x_lo, y_lo, x_hi, y_hi), empty if culled
+  SceneP sp;
+  uint32_t* cell;           // [n] Morton cell of each Gaussian
+  uint32_t* cells_scratch;  // counting-sort scratch (reorder_scratch_bytes())
+  ProjRec* proj;            // [n] by original index
+  uint32_t* depth;          // [n] float bits of camera depth, spatial order
+  ushort4* rect;            // [n] listed tiles (x_lo, y_lo, x_hi, y_hi), spatial order: the 3DGS
+                            //     rectangle cut to the alpha >= 1/255 ellipse's box; empty if culled
   uint32_t* tile_count;     // [max_tiles + 1]
   uint32_t* tile_start;     // [max_tiles + 1]
   uint32_t* tile_fill;      // [max_tiles]
@@ -68,11 +114,13 @@ struct UpliftWs {
 };
 
 // Launchers (each defined in its own translation unit).
-cudaError_t launch_tau(const float* opacity, int64_t n, float* tau, cudaStream_t st);
+size_t reorder_scratch_bytes();
+cudaError_t launch_reorder(const scoup_scene& sc, const UpliftWs& ws, cudaStream_t st);
 cudaError_t launch_preprocess(const scoup_scene& sc, const CamArgs& cam, const UpliftWs& ws,
-                              cudaStream_t st);
-cudaError_t launch_binning(const CamArgs& cam, int64_t n, const UpliftWs& ws, cudaStream_t st);
-cudaError_t launch_uplift_tiles(const CamArgs& cam, const UpliftWs& ws, const int32_t* rmap,
+                              int slot, cudaStream_t st);
+cudaError_t launch_binning(const CamArgs& cam, int64_t n, const UpliftWs& ws, int slot,
+                           cudaStream_t st);
+cudaError_t launch_uplift_tiles(const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* rmap,
                                 int32_t R_total, const int32_t* code_idx, const float* code_val,
                                 int s, int C, float* accum, cudaStream_t st);
 cudaError_t launch_topk(const float* accum, int64_t n, int C, int K, int32_t* idx, float* val,

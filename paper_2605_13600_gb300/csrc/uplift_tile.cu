@@ -1,20 +1,31 @@
 // uplift_tile.cu -- per-tile front-to-back compositing and sparse scatter
 // (paper Sec. 3 Eq. 2; Sec. 4.2 Eq. 5; Algorithm 1).
 //
-// One CTA per 16x16 tile, one pixel per thread.  The tile's unordered key list
-// (depth bits << 32 | Gaussian id) is consumed in windows of the kWin smallest
-// remaining keys: a block-wide MSD radix select finds the window boundary, the
-// window is gathered into shared memory and bitonic-sorted, and then composited
-// in batches of 256 Gaussians staged in shared memory.  The tile stops as soon
-// as every pixel has hit the transmittance cutoff, so the far part of a long
-// list is never ordered.
+// One CTA per 16x16 tile, one pixel per thread; each warp covers an 8x4 block.
 //
-// Scatter: codes are constant per region (Sec. 4.1), so for a Gaussian g the
-// contributions of all pixels of one region r inside the tile can be summed
-// first (distributivity) and flushed once as s atomics acc[g][j] += c_j * sum.
-// Per Gaussian, each warp reduces its pixels' weights with shuffles when the
-// warp lies in one region, and otherwise per lane; the per-(Gaussian, region)
-// tile partials live in shared memory and are flushed after every batch.
+// Ordering.  The tile's key list (depth bits << 32 | Gaussian id, unordered)
+// is read twice: a histogram pass over kNB depth buckets (a monotone map of
+// the depth bits onto the view's depth range), then, per window of whole
+// buckets holding at most kWin keys, a gather pass that places every key at
+// its bucket's slot (a counting sort by bucket).  Inside a bucket the keys are
+// ordered by rank (count of smaller keys in the same bucket, permuted in
+// place), which gives the exact (depth, id) order.  A bucket holding more than kWin keys is split by a
+// block-wide radix select.  Windows are composited front to back and the tile
+// stops once every pixel has reached the transmittance cutoff, so the far part
+// of a long list is never ordered.
+//
+// Scatter.  Codes are constant per region (Sec. 4.1), so the weights of all
+// pixels of one region inside the tile are summed per Gaussian before the
+// code is applied (distributivity): acc[g][j] += c_j * sum_p e_g(p).  A warp
+// whose 32 pixels share one region reduces 8 Gaussians at a time with a
+// transpose reduction (9 shuffles for 8 sums); other warps add per lane.  The
+// per-(region, Gaussian) tile partials live in shared memory and are flushed
+// as s global atomics once per window.
+//
+// Load balance.  After the block-wide ordering of a window, each warp walks
+// it independently (records staged per warp, no block barrier) and leaves as
+// soon as its 32 pixels are saturated; the block meets again only at the end
+// of the window.
 #include <math.h>
 
 #include "scoup_internal.cuh"
@@ -24,16 +35,21 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWin = 1024;
-constexpr int kMaxSlots = 8;
+constexpr int kLogNB = 11;
+constexpr int kNB = 1 << kLogNB;
+constexpr int kMaxSlots = 4;
 constexpr int kMaxS = 64;
+constexpr int kGroup = 8;
 constexpr unsigned kFull = 0xffffffffu;
 
 struct TileSmem {
+  uint32_t bstart[kNB + 1];
+  uint32_t bcur[kNB];
   unsigned long long win[kWin];
-  float4 rec_a[kThreads];
-  float4 rec_b[kThreads];
-  int gid[kThreads];
-  float part[kThreads][kMaxSlots];
+  float4 stage_a[kThreads / 32][32];
+  float4 stage_b[kThreads / 32][32];
+  int stage_g[kThreads / 32][32];
+  float part[kMaxSlots][kWin];
   int slot_region[kMaxSlots];
   int slot_idx[kMaxSlots][kMaxS];
   float slot_val[kMaxSlots][kMaxS];
@@ -45,25 +61,32 @@ struct TileSmem {
   int nslots;
   int sel_digit;
   int sel_rank;
+  int win_b1;
   unsigned long long cnt[4];
 };
 
-__device__ __forceinline__ float warp_sum(float v) {
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
-  return v;
-}
+struct Buckets {
+  uint32_t dmin;
+  int shift;
+  // monotone in the key and always inside [0, kNB)
+  __device__ __forceinline__ int operator()(unsigned long long key) const {
+    const uint32_t d = (uint32_t)(key >> 32);
+    return (int)min((d > dmin ? d - dmin : 0u) >> shift, (uint32_t)(kNB - 1));
+  }
+};
 
-// Block-wide: the rank-th smallest key (0-based) among keys[i] with
-// (first || keys[i] > last).  Keys are unique.  Requires rank < remaining.
-__device__ unsigned long long select_rank(TileSmem& sm, const unsigned long long* __restrict__ keys,
-                                          int n, unsigned long long last, bool first, int rank) {
+// Block-wide: the rank-th smallest (0-based) key among those in bucket b
+// with (first || key > last).  Keys are unique; requires rank < their count.
+__device__ unsigned long long select_in_bucket(TileSmem& sm, const unsigned long long* __restrict__ keys,
+                                               int n, const Buckets& bk, int b, unsigned long long last,
+                                               bool first, int rank) {
   const int tid = threadIdx.x;
   if (tid == 0) { sm.red_min = ~0ull; sm.red_max = 0ull; }
   __syncthreads();
   unsigned long long lmin = ~0ull, lmax = 0ull;
   for (int i = tid; i < n; i += kThreads) {
     const unsigned long long k = keys[i];
-    if (first || k > last) { lmin = min(lmin, k); lmax = max(lmax, k); }
+    if (bk(k) == b && (first || k > last)) { lmin = min(lmin, k); lmax = max(lmax, k); }
   }
   for (int off = 16; off > 0; off >>= 1) {
     lmin = min(lmin, __shfl_xor_sync(kFull, lmin, off));
@@ -79,24 +102,22 @@ __device__ unsigned long long select_rank(TileSmem& sm, const unsigned long long
     __syncthreads();
     for (int i = tid; i < n; i += kThreads) {
       const unsigned long long k = keys[i];
-      if (first || k > last) {
+      if (bk(k) == b && (first || k > last)) {
         const unsigned long long x = k - base;
         if ((x & pmask) == prefix) atomicAdd(&sm.hist[(x >> shift) & 255u], 1u);
       }
     }
     __syncthreads();
     if (tid < 32) {
-      // each lane owns 8 consecutive digits
-      uint32_t c[8], s = 0;
-      for (int d = 0; d < 8; ++d) { c[d] = sm.hist[tid * 8 + d]; s += c[d]; }
-      uint32_t incl = s;
+      uint32_t c[8], sum = 0;
+      for (int d = 0; d < 8; ++d) { c[d] = sm.hist[tid * 8 + d]; sum += c[d]; }
+      uint32_t incl = sum;
       for (int off = 1; off < 32; off <<= 1) {
-        uint32_t y = __shfl_up_sync(kFull, incl, off);
+        const uint32_t y = __shfl_up_sync(kFull, incl, off);
         if (tid >= off) incl += y;
       }
-      const uint32_t excl = incl - s;
-      const bool mine = (uint32_t)rank >= excl && (uint32_t)rank < incl;
-      if (mine) {
+      const uint32_t excl = incl - sum;
+      if ((uint32_t)rank >= excl && (uint32_t)rank < incl) {
         uint32_t cum = excl;
         for (int d = 0; d < 8; ++d) {
           if ((uint32_t)rank < cum + c[d]) { sm.sel_digit = tid * 8 + d; sm.sel_rank = rank - (int)cum; break; }
@@ -113,28 +134,35 @@ __device__ unsigned long long select_rank(TileSmem& sm, const unsigned long long
   return base + prefix;
 }
 
-// Ascending bitonic sort of sm.win[0..P), P a power of two <= kWin.
-__device__ void bitonic_sort(unsigned long long* win, int P) {
-  for (int k = 2; k <= P; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < P; i += kThreads) {
-        const int ixj = i ^ j;
-        if (ixj > i) {
-          const unsigned long long a = win[i], b = win[ixj];
-          const bool up = (i & k) == 0;
-          if ((a > b) == up) { win[i] = b; win[ixj] = a; }
-        }
-      }
-      __syncthreads();
-    }
+// Reduce 8 per-lane values across the warp: every lane ends up holding the
+// sum over all 32 lanes of v[lane >> 2].
+__device__ __forceinline__ float transpose_reduce8(const float (&v)[kGroup], int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+  float a[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float keep = b4 ? v[4 + i] : v[i];
+    const float send = b4 ? v[i] : v[4 + i];
+    a[i] = keep + __shfl_xor_sync(kFull, send, 16);
   }
+  float c[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float keep = b3 ? a[2 + i] : a[i];
+    const float send = b3 ? a[i] : a[2 + i];
+    c[i] = keep + __shfl_xor_sync(kFull, send, 8);
+  }
+  float d = (b2 ? c[1] : c[0]) + __shfl_xor_sync(kFull, b2 ? c[0] : c[1], 4);
+  d += __shfl_xor_sync(kFull, d, 2);
+  d += __shfl_xor_sync(kFull, d, 1);
+  return d;
 }
 
 __global__ void __launch_bounds__(kThreads, 4) uplift_tile_kernel(
     CamArgs cam, const ProjRec* __restrict__ proj, const unsigned long long* __restrict__ keys,
-    const uint32_t* __restrict__ tile_start, const int32_t* __restrict__ rmap, int32_t R_total,
-    const int32_t* __restrict__ code_idx, const float* __restrict__ code_val, int s, int C,
-    float* __restrict__ accum, WsHeader* __restrict__ hdr) {
+    const uint32_t* __restrict__ tile_start, int slot, const int32_t* __restrict__ rmap,
+    int32_t R_total, const int32_t* __restrict__ code_idx, const float* __restrict__ code_val, int s,
+    int C, float* __restrict__ accum, WsHeader* __restrict__ hdr) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TileSmem& sm = *reinterpret_cast<TileSmem*>(smem_raw);
   const int tile = blockIdx.x;
@@ -145,15 +173,25 @@ __global__ void __launch_bounds__(kThreads, 4) uplift_tile_kernel(
   if (hdr->status & kStatCapacity) return;
   const unsigned long long* tkeys = keys + begin;
 
+  Buckets bk;
+  {
+    const uint32_t dmin = hdr->drange[slot][0], dmax = hdr->drange[slot][1];
+    const uint32_t span = dmax >= dmin ? dmax - dmin : 0u;
+    const int nb = span ? 32 - __clz((int)span) : 0;
+    bk.dmin = dmin;
+    bk.shift = nb > kLogNB ? nb - kLogNB : 0;
+  }
+
   const int tx = tile % cam.gx, ty = tile / cam.gx;
-  const int px = tx * kTile + (tid & (kTile - 1));
-  const int py = ty * kTile + (tid >> 4);
+  const float bx0 = (float)(tx * kTile + (warp & 1) * 8), by0 = (float)(ty * kTile + (warp >> 1) * 4);
+  const int px = tx * kTile + (warp & 1) * 8 + (lane & 7);
+  const int py = ty * kTile + (warp >> 1) * 4 + (lane >> 3);
   const bool inside = px < cam.width && py < cam.height;
   int region = inside ? rmap[(int64_t)py * cam.width + px] : -1;
   if (region >= R_total) { atomicOr(&hdr->status, kStatDeviceCheck); region = -1; }
   const float fpx = (float)px, fpy = (float)py;
 
-  // ---- distinct regions of the tile -> slots ----
+  // ---- distinct regions of the tile -> slots; bucket histogram ----
   {
     const unsigned peers = __match_any_sync(kFull, region);
     const bool leader = region >= 0 && lane == __ffs(peers) - 1;
@@ -161,9 +199,11 @@ __global__ void __launch_bounds__(kThreads, 4) uplift_tile_kernel(
     if (leader) sm.warp_regions[warp][__popc(leaders & ((1u << lane) - 1u))] = region;
     if (lane == 0) sm.warp_nreg[warp] = __popc(leaders);
   }
-  for (int k = tid; k < kThreads * kMaxSlots; k += kThreads) (&sm.part[0][0])[k] = 0.0f;
+  for (int k = tid; k < kMaxSlots * kWin; k += kThreads) (&sm.part[0][0])[k] = 0.0f;
+  for (int b = tid; b < kNB; b += kThreads) sm.bcur[b] = 0u;
   if (tid < 4) sm.cnt[tid] = 0ull;
   __syncthreads();
+  for (int i = tid; i < n; i += kThreads) atomicAdd(&sm.bcur[bk(tkeys[i])], 1u);
   if (tid == 0) {
     int ns = 0;
     for (int w = 0; w < kThreads / 32; ++w)
@@ -176,6 +216,26 @@ __global__ void __launch_bounds__(kThreads, 4) uplift_tile_kernel(
     sm.nslots = ns;
   }
   __syncthreads();
+  // exclusive scan of the bucket counts (kNB / kThreads per thread, then across warps)
+  {
+    constexpr int kPer = kNB / kThreads;
+    uint32_t c[kPer], sum = 0;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) { c[q] = sm.bcur[tid * kPer + q]; sum += c[q]; }
+    uint32_t incl = sum;
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, incl, off);
+      if (lane >= off) incl += y;
+    }
+    if (lane == 31) sm.hist[warp] = incl;
+    __syncthreads();
+    uint32_t wbase = 0;
+    for (int w = 0; w < warp; ++w) wbase += sm.hist[w];
+    uint32_t run = wbase + incl - sum;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) { sm.bstart[tid * kPer + q] = run; run += c[q]; }
+    if (tid == kThreads - 1) sm.bstart[kNB] = run;
+  }
   const int nslots = sm.nslots;
   for (int k = tid; k < nslots * s; k += kThreads) {
     const int q = k / s, a = k - q * s;
@@ -188,120 +248,245 @@ __global__ void __launch_bounds__(kThreads, 4) uplift_tile_kernel(
   int my_slot = -1;
   for (int q = 0; q < nslots; ++q)
     if (sm.slot_region[q] == region) my_slot = q;
-  const bool warp_uniform = __all_sync(kFull, region == __shfl_sync(kFull, region, 0));
+  const bool uniform = __all_sync(kFull, region == __shfl_sync(kFull, region, 0));
+  const int wslot = uniform ? my_slot : -1;
   __syncthreads();
 
   float T = 1.0f;
   bool done = !inside;
-  unsigned long long n_eval = 0, n_contrib = 0, n_flush = 0, n_atom = 0;
+  unsigned n_eval = 0, n_contrib = 0, n_flush = 0, n_atom = 0;  // per thread and tile: fits 32 bits
 
-  unsigned long long last = 0ull;
-  bool first = true;
-  int remaining = n;
+  int b0 = 0;
   bool all_done = false;
-  while (!all_done && remaining > 0) {
-    // ---- window of the kWin smallest remaining keys ----
-    unsigned long long hi = ~0ull;
-    if (remaining > kWin) hi = select_rank(sm, tkeys, n, last, first, kWin - 1);
-    if (tid == 0) sm.cursor = 0u;
-    __syncthreads();
-    for (int i = tid; i < n; i += kThreads) {
-      const unsigned long long k = tkeys[i];
-      if ((first || k > last) && k <= hi) {
-        const unsigned pos = atomicAdd(&sm.cursor, 1u);
-        if (pos < (unsigned)kWin) sm.win[pos] = k;
+  // a bucket holding more than kWin keys is consumed in sub-windows
+  bool in_split = false, split_first = true;
+  unsigned long long split_last = 0ull;
+  int consumed = 0;
+  while (!all_done && b0 < kNB) {
+    const uint32_t base = sm.bstart[b0];
+    const int total_b0 = (int)(sm.bstart[b0 + 1] - base);
+    if (!in_split && total_b0 == 0) {
+      // skip empty buckets quickly: find the next non-empty one
+      if (tid == 0) {
+        int lo = b0 + 1, hi = kNB;  // smallest b with bstart[b + 1] > base, i.e. first b with keys
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (sm.bstart[mid + 1] > base) hi = mid; else lo = mid + 1;
+        }
+        sm.win_b1 = lo;
       }
+      __syncthreads();
+      b0 = sm.win_b1;
+      __syncthreads();
+      continue;
+    }
+    if (!in_split) {
+      if (tid == 0) {
+        // largest b1 in [b0 + 1, kNB] with bstart[b1] - base <= kWin (b0 itself if it is oversize)
+        int lo = b0 + 1, hi = kNB;
+        if (sm.bstart[lo] - base > (uint32_t)kWin) {
+          sm.win_b1 = b0;
+        } else {
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (sm.bstart[mid] - base <= (uint32_t)kWin) lo = mid; else hi = mid - 1;
+          }
+          sm.win_b1 = lo;
+        }
+      }
+      __syncthreads();
+    }
+    const int b1 = sm.win_b1;
+    int m;
+    if (!in_split && b1 > b0) {
+      // ---- gather whole buckets [b0, b1) at their slots, rank inside buckets ----
+      m = (int)(sm.bstart[b1] - base);
+      for (int b = b0 + tid; b < b1; b += kThreads) sm.bcur[b] = sm.bstart[b] - base;
+      __syncthreads();
+      for (int i = tid; i < n; i += kThreads) {
+        const unsigned long long k = tkeys[i];
+        const int b = bk(k);
+        if (b >= b0 && b < b1) {
+          const uint32_t pos = atomicAdd(&sm.bcur[b], 1u);
+          if (pos < (uint32_t)kWin) sm.win[pos] = k;
+        }
+      }
+      __syncthreads();
+      // rank inside the bucket, then permute in place (keys held in registers)
+      unsigned long long kk[kWin / kThreads];
+      int dst[kWin / kThreads];
+#pragma unroll
+      for (int u = 0; u < kWin / kThreads; ++u) {
+        const int p = tid + u * kThreads;
+        dst[u] = -1;
+        if (p < m) {
+          const unsigned long long k = sm.win[p];
+          const int b = bk(k);
+          const int lo = (int)(sm.bstart[b] - base), hi = (int)(sm.bstart[b + 1] - base);
+          int r = 0;
+          for (int q = lo; q < hi; ++q) r += sm.win[q] < k;
+          kk[u] = k;
+          dst[u] = lo + r;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < kWin / kThreads; ++u)
+        if (dst[u] >= 0) sm.win[dst[u]] = kk[u];
+    } else {
+      // ---- oversize bucket b0: the kWin smallest of its remaining keys ----
+      if (!in_split) { in_split = true; split_first = true; consumed = 0; }
+      const int left = total_b0 - consumed;
+      unsigned long long hi_key = ~0ull;
+      if (left > kWin) hi_key = select_in_bucket(sm, tkeys, n, bk, b0, split_last, split_first, kWin - 1);
+      if (tid == 0) sm.cursor = 0u;
+      __syncthreads();
+      for (int i = tid; i < n; i += kThreads) {
+        const unsigned long long k = tkeys[i];
+        if (bk(k) == b0 && (split_first || k > split_last) && k <= hi_key) {
+          const unsigned pos = atomicAdd(&sm.cursor, 1u);
+          if (pos < (unsigned)kWin) sm.win[pos] = k;
+        }
+      }
+      __syncthreads();
+      m = (int)min(sm.cursor, (unsigned)kWin);
+      unsigned long long kk[kWin / kThreads];
+      int dst[kWin / kThreads];
+#pragma unroll
+      for (int u = 0; u < kWin / kThreads; ++u) {
+        const int p = tid + u * kThreads;
+        dst[u] = -1;
+        if (p < m) {
+          const unsigned long long k = sm.win[p];
+          int r = 0;
+          for (int q = 0; q < m; ++q) r += sm.win[q] < k;
+          kk[u] = k;
+          dst[u] = r;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < kWin / kThreads; ++u)
+        if (dst[u] >= 0) sm.win[dst[u]] = kk[u];
     }
     __syncthreads();
-    const int m = (int)min(sm.cursor, (unsigned)kWin);
-    if (m == 0 || sm.cursor > (unsigned)kWin) {
-      // cannot happen for unique keys; stop this tile and report it
+    if (m <= 0) {
       if (tid == 0) atomicOr(&hdr->status, kStatDeviceCheck);
       break;
     }
-    int P = 1;
-    while (P < m) P <<= 1;
-    for (int i = m + tid; i < P; i += kThreads) sm.win[i] = ~0ull;
-    __syncthreads();
-    bitonic_sort(sm.win, P);
-    const unsigned long long wlast = sm.win[m - 1];
 
-    // ---- composite the window in batches ----
-    for (int b0 = 0; b0 < m && !all_done; b0 += kThreads) {
-      const int cnt = min(kThreads, m - b0);
-      if (tid < cnt) {
-        const int g = (int)(sm.win[b0 + tid] & 0xffffffffull);
+    // ---- composite the window: every warp walks it on its own ----
+    // Each lane stages one of the next 32 records and tests it against the
+    // warp's 8x4 pixel block (box_may_hit); the warp then composites only the
+    // Gaussians that can reach one of its pixels, in window order.
+    bool warp_done = __all_sync(kFull, done);
+    float4* st_a = sm.stage_a[warp];
+    float4* st_b = sm.stage_b[warp];
+    int* st_g = sm.stage_g[warp];
+    for (int j0 = 0; j0 < m && !warp_done; j0 += 32) {
+      bool rel = false;
+      if (j0 + lane < m) {
+        const int g = (int)(sm.win[j0 + lane] & 0xffffffffull);
         const ProjRec pr = proj[g];
-        sm.rec_a[tid] = pr.a;
-        sm.rec_b[tid] = pr.b;
-        sm.gid[tid] = g;
+        st_a[lane] = pr.a;
+        st_b[lane] = pr.b;
+        st_g[lane] = g;
+        rel = box_may_hit(pr, bx0, by0, 8.0f, 4.0f);
       }
-      __syncthreads();
-      for (int j = 0; j < cnt; ++j) {
-        float e = 0.0f;
-        if (!done) {
-          const float4 a = sm.rec_a[j];
-          const float4 b = sm.rec_b[j];
+      unsigned rmask = __ballot_sync(kFull, rel);
+      __syncwarp();
+      while (rmask != 0u && !warp_done) {
+        int idx[kGroup];
+#pragma unroll
+        for (int u = 0; u < kGroup; ++u) {
+          idx[u] = rmask ? __ffs(rmask) - 1 : -1;
+          rmask &= rmask ? rmask - 1u : 0u;
+        }
+        float e[kGroup];
+#pragma unroll
+        for (int u = 0; u < kGroup; ++u) {
+          // branch-free: every lane evaluates, inactive lanes discard the result
+          const int q = idx[u] < 0 ? 0 : idx[u];
+          const float4 a = st_a[q];
+          const float4 b = st_b[q];
+          const bool live = idx[u] >= 0 && !done;
           const float dx = a.x - fpx, dy = a.y - fpy;
-          // power = dx*(qa*dx + qb*dy) + (qc*dy)*dy, products rounded, two fused sums
+          // power = dx*(qa*dx + qb*dy) + (qc*dy)*dy: products rounded, two fused sums
           const float power = fmaf(dx, fmaf(a.z, dx, __fmul_rn(a.w, dy)), __fmul_rn(__fmul_rn(b.x, dy), dy));
-          ++n_eval;
-          if (power <= 0.0f && power >= b.z) {
-            const float alpha = fminf(0.99f, b.y * __expf(power));
-            const float test = T * (1.0f - alpha);
-            if (test < 1e-4f) {
-              done = true;
-            } else {
-              e = alpha * T;
-              T = test;
-              ++n_contrib;
-            }
-          }
+          const bool accept = live && power <= 0.0f && power >= b.z;
+          const float alpha = fminf(0.99f, b.y * __expf(power));
+          const float test = T * (1.0f - alpha);
+          const bool stop = accept && test < 1e-4f;
+          const bool take = accept && !stop;
+          e[u] = take ? alpha * T : 0.0f;
+          T = take ? test : T;
+          done = done || stop;
+          n_eval += live ? 1u : 0u;
+          n_contrib += take ? 1u : 0u;
         }
-        if (__any_sync(kFull, e > 0.0f)) {
-          if (warp_uniform && my_slot >= 0) {
-            const float ssum = warp_sum(e);
-            if (lane == 0) atomicAdd(&sm.part[j][my_slot], ssum);
-          } else if (e > 0.0f) {
-            if (my_slot >= 0) {
-              atomicAdd(&sm.part[j][my_slot], e);
-            } else if (region >= 0) {
-              // more regions in this tile than slots: scatter this pixel directly
-              const int g = sm.gid[j];
-              for (int a = 0; a < s; ++a) {
-                const int64_t row = (int64_t)region * s + a;
-                const int jj = code_idx[row];
-                if (jj >= 0 && jj < C) {
-                  atomicAdd(&accum[(int64_t)g * C + jj], code_val[row] * e);
-                  ++n_atom;
+        bool has = false;
+#pragma unroll
+        for (int u = 0; u < kGroup; ++u) has |= e[u] > 0.0f;
+        if (__any_sync(kFull, has)) {
+          if (wslot >= 0) {
+            const float S = transpose_reduce8(e, lane);
+            int jq = idx[0];
+#pragma unroll
+            for (int u = 1; u < kGroup; ++u) jq = (lane >> 2) == u ? idx[u] : jq;
+            if ((lane & 3) == 0 && S > 0.0f) atomicAdd(&sm.part[wslot][j0 + jq], S);
+          } else if (has) {
+#pragma unroll
+            for (int u = 0; u < kGroup; ++u) {
+              if (!(e[u] > 0.0f)) continue;
+              if (my_slot >= 0) {
+                atomicAdd(&sm.part[my_slot][j0 + idx[u]], e[u]);
+              } else if (region >= 0) {
+                // more regions in this tile than slots: scatter this pixel directly
+                const int64_t g = st_g[idx[u]];
+                for (int a = 0; a < s; ++a) {
+                  const int64_t row = (int64_t)region * s + a;
+                  const int jj = code_idx[row];
+                  if (jj >= 0 && jj < C) {
+                    atomicAdd(&accum[g * C + jj], code_val[row] * e[u]);
+                    ++n_atom;
+                  }
                 }
+                ++n_flush;
               }
-              ++n_flush;
             }
           }
         }
+        warp_done = __all_sync(kFull, done);
       }
-      __syncthreads();
-      // ---- flush the (Gaussian, region) tile partials of this batch ----
-      if (tid < cnt) {
-        const int64_t g = sm.gid[tid];
-        for (int q = 0; q < nslots; ++q) {
-          const float v = sm.part[tid][q];
-          if (v > 0.0f) {
-            for (int a = 0; a < s; ++a) {
-              const int jj = sm.slot_idx[q][a];
-              if (jj >= 0) { atomicAdd(&accum[g * C + jj], sm.slot_val[q][a] * v); ++n_atom; }
-            }
-            ++n_flush;
-            sm.part[tid][q] = 0.0f;
-          }
-        }
-      }
-      all_done = __syncthreads_and(done) != 0;
+      __syncwarp();
     }
-    remaining -= m;
-    last = wlast;
-    first = false;
+    __syncthreads();
+    // ---- flush the (region, Gaussian) tile partials of this window ----
+    for (int p = tid; p < m; p += kThreads) {
+      const int64_t g = (int64_t)(sm.win[p] & 0xffffffffull);
+      for (int q = 0; q < nslots; ++q) {
+        const float v = sm.part[q][p];
+        if (v > 0.0f) {
+          for (int a = 0; a < s; ++a) {
+            const int jj = sm.slot_idx[q][a];
+            if (jj >= 0) { atomicAdd(&accum[g * C + jj], sm.slot_val[q][a] * v); ++n_atom; }
+          }
+          ++n_flush;
+          sm.part[q][p] = 0.0f;
+        }
+      }
+    }
+    all_done = __syncthreads_and(done) != 0;
+
+    // ---- advance to the next window ----
+    if (in_split) {
+      consumed += m;
+      split_last = sm.win[m - 1];
+      split_first = false;
+      if (consumed >= total_b0) { in_split = false; b0 += 1; }
+    } else {
+      b0 = b1;
+    }
     __syncthreads();
   }
 
@@ -313,10 +498,10 @@ __global__ void __launch_bounds__(kThreads, 4) uplift_tile_kernel(
     n_atom += __shfl_xor_sync(kFull, n_atom, off);
   }
   if (lane == 0) {
-    atomicAdd(&sm.cnt[0], n_eval);
-    atomicAdd(&sm.cnt[1], n_contrib);
-    atomicAdd(&sm.cnt[2], n_flush);
-    atomicAdd(&sm.cnt[3], n_atom);
+    atomicAdd(&sm.cnt[0], (unsigned long long)n_eval);
+    atomicAdd(&sm.cnt[1], (unsigned long long)n_contrib);
+    atomicAdd(&sm.cnt[2], (unsigned long long)n_flush);
+    atomicAdd(&sm.cnt[3], (unsigned long long)n_atom);
   }
   __syncthreads();
   if (tid == 0) {
@@ -329,16 +514,17 @@ __global__ void __launch_bounds__(kThreads, 4) uplift_tile_kernel(
 
 }  // namespace
 
-cudaError_t launch_uplift_tiles(const CamArgs& cam, const UpliftWs& ws, const int32_t* rmap,
+cudaError_t launch_uplift_tiles(const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* rmap,
                                 int32_t R_total, const int32_t* code_idx, const float* code_val,
                                 int s, int C, float* accum, cudaStream_t st) {
   const int ntiles = cam.gx * cam.gy;
   if (ntiles <= 0) return cudaSuccess;
   const size_t smem = sizeof(TileSmem);
+  static_assert(sizeof(TileSmem) <= 55 * 1024, "4 CTAs per SM");
   cudaError_t err = cudaFuncSetAttribute(uplift_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
   if (err != cudaSuccess) return err;
-  uplift_tile_kernel<<<ntiles, kThreads, smem, st>>>(cam, ws.proj, ws.keys, ws.tile_start, rmap,
+  uplift_tile_kernel<<<ntiles, kThreads, smem, st>>>(cam, ws.proj, ws.keys, ws.tile_start, slot, rmap,
                                                      R_total, code_idx, code_val, s, C, accum, ws.hdr);
   g_launches += 1;
   return cudaGetLastError();

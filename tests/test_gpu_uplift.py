@@ -44,7 +44,10 @@ def _parity(gb, oracle_lib, wl, tag=""):
     assert st["visible"] == cnt["visible"], (tag, st, cnt)
     assert st["duplicates"] == cnt["duplicates"], (tag, st, cnt)
     assert abs(st["contributions"] - cnt["contributions"]) <= 2 * cnt["at_risk"], (tag, st, cnt)
-    assert abs(st["evaluated_pairs"] - cnt["evaluated"]) <= 64 * cnt["at_risk"], (tag, st, cnt)
+    # the GPU lists only (Gaussian, tile) pairs that can pass the alpha test somewhere in the
+    # tile, so it examines at most the pairs the oracle examines over the full rectangles
+    assert st["listed"] <= st["duplicates"], (tag, st)
+    assert st["evaluated_pairs"] <= cnt["evaluated"] + 64 * cnt["at_risk"], (tag, st, cnt)
     return up, st, acc, risk, cnt, info, tk
 
 
@@ -75,7 +78,7 @@ def test_long_tile_lists_use_several_windows(gb, oracle_lib):
                              log_scale_mean=-2.0)
     wl.scene.opacity[:] = np.minimum(wl.scene.opacity, 0.08)  # keep pixels open for long
     up, st, *_ = _parity(gb, oracle_lib, wl, "long")
-    assert st["duplicates"] / (2 * 6) > 3000
+    assert st["listed"] / (2 * 6) > 1500  # mean listed Gaussians per tile, above one 1024-key window
 
 
 def test_unlabelled_pixels(gb, oracle_lib):
