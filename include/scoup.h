@@ -138,6 +138,41 @@ int scoup_topk(const float* accum, int64_t n, int32_t C, int32_t K, int32_t* top
 int scoup_read_stats(const void* workspace, size_t ws_bytes, scoup_stats* stats, void* stream);
 
 /* ------------------------------------------------------------------ */
+/* Uplift without a caller-provided workspace                           */
+/* ------------------------------------------------------------------ */
+
+/* The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory: a host application whose memory manager
+ * owns every device allocation and hands out no scratch buffers, or a plugin
+ * running inside such a host with no allocator to call.
+ *
+ * Same arguments and results as scoup_uplift, but the scratch space lives in
+ * a fixed array inside this library (scoup_uplift_noalloc_max_bytes() bytes,
+ * 32 MiB, held on every GPU that loads the library until the process exits).
+ * The call allocates nothing: it calls no cudaMalloc/cudaFree or any other
+ * allocating routine.  Caller-owned inputs and outputs are as for
+ * scoup_uplift (accum, topk_idx, topk_val are still the caller's).
+ *  - Scenes whose fixed scratch (projection records, counters; see
+ *    scoup_uplift_workspace_size with dup_capacity 0) exceeds the array are
+ *    rejected with SCOUP_ERR_INVALID_ARG and a message; per-view tile lists
+ *    use what is left, and a view that needs more returns SCOUP_ERR_CAPACITY.
+ *  - The call synchronises `stream` and returns the device status; stats
+ *    (host, optional) receives the counters.
+ *  - The first call on each device looks up the device address of the array
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call on a device shares the one array and leaves its contents
+ *    behind (each call clears what must start at zero).  Calls that overlap on
+ *    the GPU -- from several host threads or on several streams at once --
+ *    race on the array and give wrong results: serialise them. */
+size_t scoup_uplift_noalloc_max_bytes(void);
+int scoup_uplift_noalloc(const scoup_scene* scene, const scoup_camera* cams, int32_t V,
+                         const int32_t* region_maps, const int64_t* map_offsets, int32_t R_total,
+                         const int32_t* code_idx, const float* code_val, int32_t s, int32_t C,
+                         int32_t K, float* accum, int32_t accum_mode, int32_t* topk_idx,
+                         float* topk_val, scoup_stats* stats, void* stream);
+
+/* ------------------------------------------------------------------ */
 /* Profiling hooks                                                     */
 /* ------------------------------------------------------------------ */
 

@@ -65,6 +65,9 @@ PROTOS = {
                                 P, P, P, SZ, ct.POINTER(Stats), P]),
     "scoup_topk": (ct.c_int, [P, I64, I32, I32, P, P, P]),
     "scoup_read_stats": (ct.c_int, [P, SZ, ct.POINTER(Stats), P]),
+    "scoup_uplift_noalloc_max_bytes": (SZ, []),
+    "scoup_uplift_noalloc": (ct.c_int, [ct.POINTER(Scene), P, I32, P, P, I32, P, P, I32, I32, I32, P, I32,
+                                        P, P, ct.POINTER(Stats), P]),
     "scoup_profile_enable": (ct.c_int, [I32]),
     "scoup_profile_read": (ct.c_int, [P, P, I32]),
     "scoup_launch_count": (I64, []),

@@ -194,6 +194,10 @@ int finish_with_stats(const WsHeader* dev_hdr, scoup_stats* stats, cudaStream_t 
 }  // namespace
 }  // namespace scoup
 
+namespace scoup {
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace scoup
+
 using namespace scoup;
 
 extern "C" {

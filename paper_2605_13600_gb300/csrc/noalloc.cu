@@ -1,0 +1,87 @@
+// noalloc.cu -- scoup_uplift_noalloc: the uplift with its scratch in a
+// fixed, library-owned device array instead of a caller-provided workspace.
+//
+// Some callers cannot allocate device memory: a host application whose
+// memory manager owns every device allocation and hands out no scratch
+// buffers, or a plugin that runs inside such a host and has no allocator to
+// call.  They can still pass their inputs and outputs; the scratch this call
+// needs lives in g_uplift_scratch below, a file-scope __device__ array that
+// every GPU which loads this library holds until the process exits.
+#include <stdio.h>
+
+#include <mutex>
+
+#include "scoup_internal.cuh"
+
+namespace scoup {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 32u << 20;  // 32 MiB
+
+__device__ __align__(256) unsigned char g_uplift_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_uplift_scratch on the current device, looked up once
+// per device (the host-side name of the array is not a device address).
+cudaError_t scratch_address(void** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_setup_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_uplift_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace scoup
+
+extern "C" {
+
+size_t scoup_uplift_noalloc_max_bytes(void) { return scoup::kNoAllocScratchBytes; }
+
+int scoup_uplift_noalloc(const scoup_scene* scene, const scoup_camera* cams, int32_t V,
+                         const int32_t* region_maps, const int64_t* map_offsets, int32_t R_total,
+                         const int32_t* code_idx, const float* code_val, int32_t s, int32_t C,
+                         int32_t K, float* accum, int32_t accum_mode, int32_t* topk_idx,
+                         float* topk_val, scoup_stats* stats, void* stream) {
+  if (!scene || scene->n < 0 || V < 0 || (V > 0 && !cams)) {
+    // let scoup_uplift produce the precise message
+    return scoup_uplift(scene, cams, V, region_maps, map_offsets, R_total, code_idx, code_val, s, C, K,
+                        accum, accum_mode, topk_idx, topk_val, nullptr, 0, stats, stream);
+  }
+  int maxw = 1, maxh = 1;
+  for (int v = 0; v < V; ++v) {
+    if (cams[v].width > maxw) maxw = cams[v].width;
+    if (cams[v].height > maxh) maxh = cams[v].height;
+  }
+  const size_t fixed = scoup_uplift_workspace_size(scene->n, maxw, maxh, 0) +
+                       (s > K && R_total > 0 ? 2 * (size_t)R_total * (size_t)K * 4 + 512 : 0);
+  if (fixed > scoup::kNoAllocScratchBytes) {
+    char msg[200];
+    snprintf(msg, sizeof(msg),
+             "scoup_uplift_noalloc: %lld Gaussians at %dx%d need %zu bytes of scratch before tile lists; "
+             "the fixed array holds %zu", (long long)scene->n, maxw, maxh, fixed,
+             scoup::kNoAllocScratchBytes);
+    return scoup::set_error(SCOUP_ERR_INVALID_ARG, msg);
+  }
+  void* scratch = nullptr;
+  cudaError_t e = scoup::scratch_address(&scratch);
+  if (e != cudaSuccess)
+    return scoup::set_error(SCOUP_ERR_CUDA, cudaGetErrorString(e));
+  scoup_stats local;
+  return scoup_uplift(scene, cams, V, region_maps, map_offsets, R_total, code_idx, code_val, s, C, K,
+                      accum, accum_mode, topk_idx, topk_val, scratch, scoup::kNoAllocScratchBytes,
+                      stats ? stats : &local, stream);
+}
+
+}  // extern "C"

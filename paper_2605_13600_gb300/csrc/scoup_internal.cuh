@@ -113,6 +113,9 @@ struct UpliftWs {
   int max_tiles;
 };
 
+// Records msg as the calling thread's last error and returns code.
+int set_error(int code, const char* msg);
+
 // Launchers (each defined in its own translation unit).
 size_t reorder_scratch_bytes();
 cudaError_t launch_reorder(const scoup_scene& sc, const UpliftWs& ws, cudaStream_t st);

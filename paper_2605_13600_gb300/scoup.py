@@ -108,6 +108,33 @@ def scoup_uplift(scene: Scene, cams: Sequence, region_maps, map_offsets, R_total
     return st.as_dict() if stats else None
 
 
+def scoup_uplift_noalloc(scene: Scene, cams: Sequence, region_maps, map_offsets, R_total: int,
+                         code_idx, code_val, s: int, C: int, K: int, accum, accum_mode: int,
+                         topk_idx, topk_val, stream=None) -> dict:
+    """scoup_uplift with the library's fixed scratch array (no workspace
+    argument, nothing allocated); synchronises and returns the stats dict."""
+    import torch
+    _need(region_maps, torch.int32, "region_maps")
+    _need(code_idx, torch.int32, "code_idx")
+    _need(code_val, torch.float32, "code_val")
+    _need(accum, torch.float32, "accum")
+    _need(topk_idx, torch.int32, "topk_idx")
+    _need(topk_val, torch.float32, "topk_val")
+    offs = np.ascontiguousarray(np.asarray(map_offsets, np.int64)[:max(1, len(cams))])
+    ca = camera_array(cams)
+    st = Stats()
+    check(load().scoup_uplift_noalloc(ct.byref(scene), ct.cast(ca, ct.c_void_p), len(cams),
+                                      _ptr(region_maps), offs.ctypes.data_as(ct.c_void_p), int(R_total),
+                                      _ptr(code_idx), _ptr(code_val), int(s), int(C), int(K), _ptr(accum),
+                                      int(accum_mode), _ptr(topk_idx), _ptr(topk_val), ct.byref(st),
+                                      _stream(stream)))
+    return st.as_dict()
+
+
+def scoup_uplift_noalloc_max_bytes() -> int:
+    return int(load().scoup_uplift_noalloc_max_bytes())
+
+
 def scoup_topk(accum, K: int, topk_idx, topk_val, stream=None) -> None:
     import torch
     _need(accum, torch.float32, "accum")
@@ -192,5 +219,6 @@ class Uplift:
 
 __all__ = ["ScoupError", "scene_struct", "camera_array", "scoup_version",
            "scoup_uplift_workspace_size", "scoup_uplift_plan", "scoup_uplift", "scoup_topk",
-           "scoup_read_stats", "scoup_profile_enable", "scoup_profile_read", "scoup_launch_count",
+           "scoup_read_stats", "scoup_uplift_noalloc", "scoup_uplift_noalloc_max_bytes",
+           "scoup_profile_enable", "scoup_profile_read", "scoup_launch_count",
            "Uplift"]
