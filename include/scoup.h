@@ -138,6 +138,26 @@ int scoup_topk(const float* accum, int64_t n, int32_t C, int32_t K, int32_t* top
 int scoup_read_stats(const void* workspace, size_t ws_bytes, scoup_stats* stats, void* stream);
 
 /* ------------------------------------------------------------------ */
+/* Sparse coefficient rendering (paper Sec. 4.3, Eq. 7)                 */
+/* ------------------------------------------------------------------ */
+
+/* Renders one view: What(p) = sum_i e_i(p) w^_i over the Gaussians in front
+ * to back order with the same compositing as scoup_uplift (Eq. 2), where
+ * w^_i is Gaussian i's K-sparse code (topk_idx[i][k] < C or -1 padding,
+ * topk_val[i][k]).  The result is the dense, unnormalised C-vector per pixel.
+ *  out_codes  float32 [H, W, C] row-major (every pixel written).
+ *  out_T      float32 [H, W] final transmittance, or NULL.
+ *  out_last   int32 [H, W]: number of front-to-back list entries up to and
+ *             including the last contributor of the pixel, or NULL.
+ *  workspace  as for scoup_uplift with one view (scoup_uplift_workspace_size
+ *             with the camera's size).
+ *  stats      HOST or NULL; when given, the call synchronises `stream`.
+ * Limits: 1 <= K <= C <= 1024. */
+int scoup_render(const scoup_scene* scene, const int32_t* topk_idx, const float* topk_val, int32_t K,
+                 int32_t C, const scoup_camera* cam, float* out_codes, float* out_T, int32_t* out_last,
+                 void* workspace, size_t ws_bytes, scoup_stats* stats, void* stream);
+
+/* ------------------------------------------------------------------ */
 /* Uplift without a caller-provided workspace                           */
 /* ------------------------------------------------------------------ */
 
@@ -183,6 +203,10 @@ int scoup_uplift_noalloc(const scoup_scene* scene, const scoup_camera* cams, int
 #define SCOUP_PHASE_UPLIFT_TILES 3 /* per-tile sort + composite + scatter of one view */
 #define SCOUP_PHASE_TOPK 4         /* Top-K + normalisation */
 #define SCOUP_PHASE_CODE_TOPK 5    /* per-code Top-K (s > K) */
+#define SCOUP_PHASE_RENDER 6       /* per-tile sparse-code rendering of one view */
+#define SCOUP_PHASE_RENDER_BWD 7   /* per-tile backward of the rendering */
+#define SCOUP_PHASE_DECODE 8       /* codebook decode GEMM */
+#define SCOUP_PHASE_SIMILARITY 9   /* cosine similarity to text vectors */
 #define SCOUP_NUM_PHASES 16
 
 /* When enable != 0, each later launch group of a phase is bracketed by CUDA

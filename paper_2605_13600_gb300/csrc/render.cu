@@ -1,0 +1,215 @@
+// render.cu -- sparse coefficient rendering (paper Sec. 4.3, Eq. 7):
+//   What(p) = sum_i e_i(p) w^_i,   e_i(p) = alpha_i(p) prod_{j<i} (1 - alpha_j(p)),
+// with the K-sparse Top-K codes w^_i of the uplift, into a dense C-vector per
+// pixel (unnormalised), plus the final transmittance and the list position of
+// the last contributor (for the backward pass).
+//
+// One CTA per 16x16 tile.  The tile's key list is ordered window by window
+// exactly as in the uplift (tile_order.cuh) and the window's records are
+// staged in shared memory.  Each warp then takes pixels one at a time from a
+// shared counter and walks the window 32 Gaussians per round: every lane
+// evaluates one Gaussian (the same binary32 exponent and alpha test as the
+// uplift), a warp product-scan of (1 - alpha) gives each lane its
+// transmittance, the first lane that would bring T below 1e-4 ends the pixel,
+// and the contributing lanes add e * val into the warp's dense C-vector in
+// shared memory (K shared atomics each).  A pixel's row is written once per
+// window (coalesced); a pixel still open at the end of a window keeps its
+// partial row in the output and resumes from it in the next window.
+#include <math.h>
+
+#include "tile_order.cuh"
+
+namespace scoup {
+namespace {
+
+constexpr int kRThreads = 256;
+constexpr int kRWarps = kRThreads / 32;
+using ROrder = OrderSmem<1024, 11>;
+
+struct RenderSmem {
+  ROrder ord;
+  float4 rec_a[ROrder::kWin];
+  float4 rec_b[ROrder::kWin];
+  float T[kTilePixels];
+  int last[kTilePixels];
+  int done[kTilePixels];
+  int next_pixel;
+  unsigned long long cnt[2];
+  // followed by kRWarps dense accumulators of C floats (dynamic)
+};
+
+__device__ __forceinline__ float* warp_acc(RenderSmem& sm, int warp, int C) {
+  return reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(&sm) + sizeof(RenderSmem)) + warp * C;
+}
+
+// Walk the sorted window win[0..m) for pixel (px, py).  T, last and the
+// accumulator carry the pixel's state; returns true once the pixel is done.
+__device__ __forceinline__ bool walk_pixel(RenderSmem& sm, int m, int wbase, float fpx, float fpy,
+                                           float& T, int& last, float* acc,
+                                           const int32_t* __restrict__ topk_idx,
+                                           const float* __restrict__ topk_val, int K, int C,
+                                           unsigned& n_eval, unsigned& n_contrib) {
+  const int lane = threadIdx.x & 31;
+  for (int w0 = 0; w0 < m; w0 += 32) {
+    const int j = w0 + lane;
+    const bool live = j < m;
+    const int jj = live ? j : 0;
+    const float4 a = sm.rec_a[jj];
+    const float4 b = sm.rec_b[jj];
+    const float dx = a.x - fpx, dy = a.y - fpy;
+    const float power = fmaf(dx, fmaf(a.z, dx, __fmul_rn(a.w, dy)), __fmul_rn(__fmul_rn(b.x, dy), dy));
+    const bool accept = live && power <= 0.0f && power >= b.z;
+    const float alpha = accept ? fminf(0.99f, b.y * __expf(power)) : 0.0f;
+    // inclusive product scan of (1 - alpha) over the lanes
+    float P = 1.0f - alpha;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const float y = __shfl_up_sync(0xffffffffu, P, off);
+      if (lane >= off) P *= y;
+    }
+    float Pex = __shfl_up_sync(0xffffffffu, P, 1);
+    if (lane == 0) Pex = 1.0f;
+    const float Tl = T * Pex;        // transmittance in front of this Gaussian
+    const float test = T * P;        // transmittance behind it
+    const unsigned stopmask = __ballot_sync(0xffffffffu, accept && test < 1e-4f);
+    const int first = stopmask ? __ffs(stopmask) - 1 : 32;
+    const bool take = accept && lane < first;
+    const unsigned livemask = __ballot_sync(0xffffffffu, live);
+    const unsigned evalmask = first < 32 ? livemask & ((2u << first) - 1u) : livemask;
+    n_eval += (lane == 0) ? __popc(evalmask) : 0u;
+    const unsigned takemask = __ballot_sync(0xffffffffu, take);
+    n_contrib += (lane == 0) ? __popc(takemask) : 0u;
+    if (take) {
+      const float e = alpha * Tl;
+      const int g = (int)(sm.ord.win[j] & 0xffffffffull);
+      const int32_t* ci = topk_idx + (int64_t)g * K;
+      const float* cv = topk_val + (int64_t)g * K;
+      for (int k = 0; k < K; ++k) {
+        const int atom = ci[k];
+        if (atom >= 0 && atom < C) atomicAdd(&acc[atom], e * cv[k]);
+      }
+    }
+    if (takemask) last = wbase + w0 + (31 - __clz((int)takemask)) + 1;
+    if (stopmask) {
+      T = __shfl_sync(0xffffffffu, Tl, first);
+      return true;
+    }
+    T = __shfl_sync(0xffffffffu, test, 31);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void write_row(float* __restrict__ out_row, const float* acc, int C) {
+  const int lane = threadIdx.x & 31;
+  for (int c = lane; c < C; c += 32) out_row[c] = acc[c];
+}
+
+__global__ void __launch_bounds__(kRThreads, 2) render_tile_kernel(
+    CamArgs cam, const ProjRec* __restrict__ proj, const unsigned long long* __restrict__ keys,
+    const uint32_t* __restrict__ tile_start, int slot, const int32_t* __restrict__ topk_idx,
+    const float* __restrict__ topk_val, int K, int C, float* __restrict__ out, float* __restrict__ out_T,
+    int32_t* __restrict__ out_last, WsHeader* __restrict__ hdr) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  RenderSmem& sm = *reinterpret_cast<RenderSmem*>(smem_raw);
+  const int tile = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tx = tile % cam.gx, ty = tile / cam.gx;
+  const uint32_t begin = tile_start[tile];
+  const int n = (int)(tile_start[tile + 1] - begin);
+  if (hdr->status & kStatCapacity) return;
+  const unsigned long long* tkeys = keys + begin;
+  float* acc = warp_acc(sm, warp, C);
+
+  for (int p = tid; p < kTilePixels; p += kRThreads) {
+    const int px = tx * kTile + (p & (kTile - 1)), py = ty * kTile + (p >> 4);
+    sm.T[p] = 1.0f;
+    sm.last[p] = 0;
+    sm.done[p] = !(px < cam.width && py < cam.height);
+  }
+  if (tid < 2) sm.cnt[tid] = 0ull;
+  const OrderBuckets bk = order_buckets<ROrder>(hdr, slot);
+  order_init(sm.ord, tkeys, n, bk);  // ends with a barrier
+  unsigned n_eval = 0, n_contrib = 0;
+
+  OrderState st;
+  int wbase = 0;
+  bool first_window = true;
+  while (true) {
+    const int m = n > 0 ? order_next_window(sm.ord, tkeys, n, bk, st, hdr) : 0;
+    if (m < 0) break;
+    if (m == 0 && !first_window) break;
+    for (int j = tid; j < m; j += kRThreads) {
+      const ProjRec pr = proj[(int)(sm.ord.win[j] & 0xffffffffull)];
+      sm.rec_a[j] = pr.a;
+      sm.rec_b[j] = pr.b;
+    }
+    if (tid == 0) sm.next_pixel = 0;
+    __syncthreads();
+    while (true) {
+      int p = 0;
+      if (lane == 0) p = atomicAdd(&sm.next_pixel, 1);
+      p = __shfl_sync(0xffffffffu, p, 0);
+      if (p >= kTilePixels) break;
+      if (sm.done[p]) continue;
+      const int px = tx * kTile + (p & (kTile - 1)), py = ty * kTile + (p >> 4);
+      float* row = out + ((int64_t)py * cam.width + px) * C;
+      if (first_window) {
+        for (int c = lane; c < C; c += 32) acc[c] = 0.0f;
+      } else {
+        for (int c = lane; c < C; c += 32) acc[c] = row[c];  // partial row of an earlier window
+      }
+      __syncwarp();
+      float T = sm.T[p];
+      int last = sm.last[p];
+      const bool fin = m > 0 && walk_pixel(sm, m, wbase, (float)px, (float)py, T, last, acc, topk_idx,
+                                           topk_val, K, C, n_eval, n_contrib);
+      __syncwarp();
+      write_row(row, acc, C);
+      if (lane == 0) {
+        sm.T[p] = T;
+        sm.last[p] = last;
+        sm.done[p] = fin;
+        if (out_T) out_T[(int64_t)py * cam.width + px] = T;
+        if (out_last) out_last[(int64_t)py * cam.width + px] = last;
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    first_window = false;
+    wbase += m;
+    if (m == 0) break;
+    int open = 0;
+    for (int p = tid; p < kTilePixels; p += kRThreads) open |= !sm.done[p];
+    if (!__syncthreads_or(open)) break;
+  }
+  if (lane == 0) {
+    atomicAdd(&sm.cnt[0], (unsigned long long)n_eval);
+    atomicAdd(&sm.cnt[1], (unsigned long long)n_contrib);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    atomicAdd(&hdr->evaluated, sm.cnt[0]);
+    atomicAdd(&hdr->contributions, sm.cnt[1]);
+  }
+}
+
+}  // namespace
+
+size_t render_smem_bytes(int C) { return sizeof(RenderSmem) + sizeof(float) * (size_t)kRWarps * (size_t)C; }
+
+cudaError_t launch_render_tiles(const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* topk_idx,
+                                const float* topk_val, int K, int C, float* out, float* out_T,
+                                int32_t* out_last, cudaStream_t st) {
+  const int ntiles = cam.gx * cam.gy;
+  if (ntiles <= 0) return cudaSuccess;
+  const size_t smem = render_smem_bytes(C);
+  cudaError_t err = cudaFuncSetAttribute(render_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+  if (err != cudaSuccess) return err;
+  render_tile_kernel<<<ntiles, kRThreads, smem, st>>>(cam, ws.proj, ws.keys, ws.tile_start, slot, topk_idx,
+                                                      topk_val, K, C, out, out_T, out_last, ws.hdr);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace scoup

@@ -144,6 +144,69 @@ def scoup_topk(accum, K: int, topk_idx, topk_val, stream=None) -> None:
     check(load().scoup_topk(_ptr(accum), n, C, K, _ptr(topk_idx), _ptr(topk_val), _stream(stream)))
 
 
+def scoup_render(scene: Scene, topk_idx, topk_val, K: int, C: int, cam, out_codes, out_T, out_last,
+                 workspace, stats: bool = True, stream=None):
+    """Eq. 7 for one view into out_codes [H, W, C] (float32); returns stats when stats=True."""
+    import torch
+    _need(topk_idx, torch.int32, "topk_idx")
+    _need(topk_val, torch.float32, "topk_val")
+    _need(out_codes, torch.float32, "out_codes")
+    _need(out_T, torch.float32, "out_T")
+    _need(out_last, torch.int32, "out_last")
+    _need(workspace, torch.uint8, "workspace")
+    ca = camera_array([cam])
+    st = Stats()
+    check(load().scoup_render(ct.byref(scene), _ptr(topk_idx), _ptr(topk_val), int(K), int(C),
+                              ct.cast(ca, ct.POINTER(Camera)), _ptr(out_codes), _ptr(out_T), _ptr(out_last),
+                              _ptr(workspace), workspace.numel(), ct.byref(st) if stats else None,
+                              _stream(stream)))
+    return st.as_dict() if stats else None
+
+
+class Render:
+    """Device copies of a scene and its K-sparse codes plus a planned workspace
+    for rendering views of up to max_width x max_height."""
+
+    def __init__(self, scene, topk_idx, topk_val, C: int, cams, device: str = "cuda",
+                 dup_capacity: Optional[int] = None):
+        import torch
+        dev = torch.device(device)
+        self.means = torch.as_tensor(scene.means, device=dev).contiguous()
+        self.scales = torch.as_tensor(scene.scales, device=dev).contiguous()
+        self.quats = torch.as_tensor(scene.quats, device=dev).contiguous()
+        self.opacity = torch.as_tensor(scene.opacity, device=dev).contiguous()
+        self.scene = scene_struct(self.means, self.scales, self.quats, self.opacity)
+        self.topk_idx = torch.as_tensor(np.asarray(topk_idx, np.int32), device=dev).contiguous()
+        self.topk_val = torch.as_tensor(np.asarray(topk_val, np.float32), device=dev).contiguous()
+        self.K = int(self.topk_idx.shape[1]) if self.topk_idx.ndim == 2 else 1
+        self.C = int(C)
+        self.cams = list(cams)
+        n = int(scene.means.shape[0])
+        maxw = max([c.width for c in self.cams] + [1])
+        maxh = max([c.height for c in self.cams] + [1])
+        if dup_capacity is None:
+            probe = torch.empty(scoup_uplift_workspace_size(n, maxw, maxh, 0), dtype=torch.uint8, device=dev)
+            dup_capacity = scoup_uplift_plan(self.scene, self.cams, probe) + 1
+            del probe
+        self.workspace = torch.empty(scoup_uplift_workspace_size(n, maxw, maxh, dup_capacity),
+                                     dtype=torch.uint8, device=dev)
+        self.device = dev
+
+    def outputs(self, cam):
+        import torch
+        H, W = cam.height, cam.width
+        return (torch.empty((H, W, self.C), dtype=torch.float32, device=self.device),
+                torch.empty((H, W), dtype=torch.float32, device=self.device),
+                torch.empty((H, W), dtype=torch.int32, device=self.device))
+
+    def run(self, v: int, out=None, stats: bool = True, stream=None):
+        cam = self.cams[v]
+        out = self.outputs(cam) if out is None else out
+        st = scoup_render(self.scene, self.topk_idx, self.topk_val, self.K, self.C, cam, out[0], out[1],
+                          out[2], self.workspace, stats=stats, stream=stream)
+        return out, st
+
+
 def scoup_read_stats(workspace, stream=None) -> dict:
     st = Stats()
     check(load().scoup_read_stats(_ptr(workspace), workspace.numel(), ct.byref(st), _stream(stream)))
@@ -221,4 +284,4 @@ __all__ = ["ScoupError", "scene_struct", "camera_array", "scoup_version",
            "scoup_uplift_workspace_size", "scoup_uplift_plan", "scoup_uplift", "scoup_topk",
            "scoup_read_stats", "scoup_uplift_noalloc", "scoup_uplift_noalloc_max_bytes",
            "scoup_profile_enable", "scoup_profile_read", "scoup_launch_count",
-           "Uplift"]
+           "scoup_render", "Render", "Uplift"]
