@@ -157,6 +157,22 @@ int scoup_render(const scoup_scene* scene, const int32_t* topk_idx, const float*
                  int32_t C, const scoup_camera* cam, float* out_codes, float* out_T, int32_t* out_last,
                  void* workspace, size_t ws_bytes, scoup_stats* stats, void* stream);
 
+/* Gradient through scoup_render (derived from Eq. 2 and Eq. 7) for a loss
+ * whose gradient with respect to the rendered codes is dL_dcodes (float32
+ * [H, W, C]).  ADDS into the caller's arrays (zero them first for a fresh
+ * gradient):
+ *   d_topk_val[i][k] += sum_p e_i(p) dL_dcodes[p][topk_idx[i][k]]
+ *   d_opacity[i]     += sum_p dalpha_i/do_i (T_i g.w^_i - S_after_i / (1 - alpha_i))
+ * with S_after_i the sum of e_j g.w^_j over the contributors behind i and
+ * dalpha/do = G_i(p) while o_i G_i(p) < 0.99, else 0.  Top-K indices and the
+ * discrete compositing decisions are held fixed.  Transmittance is recomputed
+ * (two front-to-back passes), nothing per pixel is stored between the calls.
+ * Workspace and stats as for scoup_render.  Limits: 1 <= K <= min(C, 64). */
+int scoup_render_backward(const scoup_scene* scene, const int32_t* topk_idx, const float* topk_val,
+                          int32_t K, int32_t C, const scoup_camera* cam, const float* dL_dcodes,
+                          float* d_topk_val, float* d_opacity, void* workspace, size_t ws_bytes,
+                          scoup_stats* stats, void* stream);
+
 /* ------------------------------------------------------------------ */
 /* Uplift without a caller-provided workspace                           */
 /* ------------------------------------------------------------------ */

@@ -66,6 +66,8 @@ PROTOS = {
     "scoup_topk": (ct.c_int, [P, I64, I32, I32, P, P, P]),
     "scoup_render": (ct.c_int, [ct.POINTER(Scene), P, P, I32, I32, ct.POINTER(Camera), P, P, P, P, SZ,
                                 ct.POINTER(Stats), P]),
+    "scoup_render_backward": (ct.c_int, [ct.POINTER(Scene), P, P, I32, I32, ct.POINTER(Camera), P, P, P, P,
+                                         SZ, ct.POINTER(Stats), P]),
     "scoup_read_stats": (ct.c_int, [P, SZ, ct.POINTER(Stats), P]),
     "scoup_uplift_noalloc_max_bytes": (SZ, []),
     "scoup_uplift_noalloc": (ct.c_int, [ct.POINTER(Scene), P, I32, P, P, I32, P, P, I32, I32, I32, P, I32,

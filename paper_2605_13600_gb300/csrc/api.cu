@@ -377,6 +377,57 @@ int scoup_render(const scoup_scene* scene, const int32_t* topk_idx, const float*
   return SCOUP_OK;
 }
 
+int scoup_render_backward(const scoup_scene* scene, const int32_t* topk_idx, const float* topk_val,
+                          int32_t K, int32_t C, const scoup_camera* cam, const float* dL_dcodes,
+                          float* d_topk_val, float* d_opacity, void* workspace, size_t ws_bytes,
+                          scoup_stats* stats, void* stream) {
+  int rc = check_scene(scene);
+  if (rc) return rc;
+  int max_tiles = 1;
+  if ((rc = check_cams(cam, 1, &max_tiles))) return rc;
+  if (C < 1 || C > 1024) return fail(SCOUP_ERR_INVALID_ARG, "C=%d outside [1, 1024]", C);
+  if (K < 1 || K > C || K > 64) return fail(SCOUP_ERR_INVALID_ARG, "K=%d outside [1, min(C, 64)]", K);
+  if (!dL_dcodes) return fail(SCOUP_ERR_INVALID_ARG, "dL_dcodes is NULL");
+  if (scene->n > 0 && (!topk_idx || !topk_val || !d_topk_val || !d_opacity))
+    return fail(SCOUP_ERR_INVALID_ARG, "Top-K or gradient arrays are NULL");
+  if (!workspace) return fail(SCOUP_ERR_INVALID_ARG, "workspace is NULL");
+  if (render_bwd_smem_bytes(C, K) > 227 * 1024)
+    return fail(SCOUP_ERR_INVALID_ARG, "C=%d, K=%d need more shared memory than a CTA has", C, K);
+  const size_t fixed = uplift_fixed_bytes(scene->n, max_tiles, 0);
+  if (ws_bytes < fixed)
+    return fail(SCOUP_ERR_OOM, "workspace too small: %zu < %zu bytes before tile lists", ws_bytes, fixed);
+  cudaStream_t st = (cudaStream_t)stream;
+  int32_t* fci = nullptr;
+  float* fcv = nullptr;
+  UpliftWs ws = carve(workspace, ws_bytes, scene->n, max_tiles, 0, &fci, &fcv);
+  const int64_t n = scene->n;
+  const CamArgs ca = cam_args(*cam);
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(ws.hdr, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
+  if ((e = cudaMemsetAsync(ws.tile_count, 0, sizeof(uint32_t) * ((size_t)max_tiles + 1), st)) != cudaSuccess)
+    return cuda_fail(e, "memset");
+  {
+    PhaseScope ps(SCOUP_PHASE_TAU, st);
+    if ((e = launch_reorder(*scene, ws, st)) != cudaSuccess) return cuda_fail(e, "reorder");
+  }
+  if (n > 0) {
+    PhaseScope ps(SCOUP_PHASE_PREPROCESS, st);
+    if ((e = launch_preprocess(*scene, ca, ws, 0, st)) != cudaSuccess) return cuda_fail(e, "preprocess");
+  }
+  {
+    PhaseScope ps(SCOUP_PHASE_BINNING, st);
+    if ((e = launch_binning(ca, n, ws, 0, st)) != cudaSuccess) return cuda_fail(e, "binning");
+  }
+  {
+    PhaseScope ps(SCOUP_PHASE_RENDER_BWD, st);
+    if ((e = launch_render_bwd(ca, ws, 0, topk_idx, topk_val, K, C, dL_dcodes, d_topk_val, d_opacity, st)) !=
+        cudaSuccess)
+      return cuda_fail(e, "render backward");
+  }
+  if (stats) return finish_with_stats(ws.hdr, stats, st);
+  return SCOUP_OK;
+}
+
 int scoup_topk(const float* accum, int64_t n, int32_t C, int32_t K, int32_t* topk_idx,
                float* topk_val, void* stream) {
   if (n < 0) return fail(SCOUP_ERR_INVALID_ARG, "n < 0");

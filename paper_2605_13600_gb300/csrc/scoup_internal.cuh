@@ -130,6 +130,10 @@ size_t render_smem_bytes(int C);
 cudaError_t launch_render_tiles(const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* topk_idx,
                                 const float* topk_val, int K, int C, float* out, float* out_T,
                                 int32_t* out_last, cudaStream_t st);
+size_t render_bwd_smem_bytes(int C, int K);
+cudaError_t launch_render_bwd(const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* topk_idx,
+                              const float* topk_val, int K, int C, const float* dL_dcodes, float* d_val,
+                              float* d_opacity, cudaStream_t st);
 cudaError_t launch_topk(const float* accum, int64_t n, int C, int K, int32_t* idx, float* val,
                         cudaStream_t st);
 cudaError_t launch_code_topk(const int32_t* ci, const float* cv, int64_t R, int s, int K,

@@ -163,6 +163,24 @@ def scoup_render(scene: Scene, topk_idx, topk_val, K: int, C: int, cam, out_code
     return st.as_dict() if stats else None
 
 
+def scoup_render_backward(scene: Scene, topk_idx, topk_val, K: int, C: int, cam, dL_dcodes, d_topk_val,
+                          d_opacity, workspace, stats: bool = False, stream=None):
+    """Adds dL/dval and dL/dopacity of one view into d_topk_val [n, K], d_opacity [n]."""
+    import torch
+    for t, nm in ((topk_val, "topk_val"), (dL_dcodes, "dL_dcodes"), (d_topk_val, "d_topk_val"),
+                  (d_opacity, "d_opacity")):
+        _need(t, torch.float32, nm)
+    _need(topk_idx, torch.int32, "topk_idx")
+    _need(workspace, torch.uint8, "workspace")
+    ca = camera_array([cam])
+    st = Stats()
+    check(load().scoup_render_backward(ct.byref(scene), _ptr(topk_idx), _ptr(topk_val), int(K), int(C),
+                                       ct.cast(ca, ct.POINTER(Camera)), _ptr(dL_dcodes), _ptr(d_topk_val),
+                                       _ptr(d_opacity), _ptr(workspace), workspace.numel(),
+                                       ct.byref(st) if stats else None, _stream(stream)))
+    return st.as_dict() if stats else None
+
+
 class Render:
     """Device copies of a scene and its K-sparse codes plus a planned workspace
     for rendering views of up to max_width x max_height."""
@@ -284,4 +302,4 @@ __all__ = ["ScoupError", "scene_struct", "camera_array", "scoup_version",
            "scoup_uplift_workspace_size", "scoup_uplift_plan", "scoup_uplift", "scoup_topk",
            "scoup_read_stats", "scoup_uplift_noalloc", "scoup_uplift_noalloc_max_bytes",
            "scoup_profile_enable", "scoup_profile_read", "scoup_launch_count",
-           "scoup_render", "Render", "Uplift"]
+           "scoup_render", "scoup_render_backward", "Render", "Uplift"]
