@@ -174,6 +174,53 @@ int scoup_render_backward(const scoup_scene* scene, const int32_t* topk_idx, con
                           scoup_stats* stats, void* stream);
 
 /* ------------------------------------------------------------------ */
+/* Codebook decode and text similarity (tensor cores, BF16 inputs)      */
+/* ------------------------------------------------------------------ */
+
+/* Workspace bytes for scoup_decode with P rows, C atoms of dimension D. */
+size_t scoup_decode_workspace_size(int64_t P, int32_t C, int32_t D);
+
+/* Codebook decode of rendered sparse codes into features (Sec. 4.3, Eq. 8):
+ *   features[p][d] = sum_c codes[p][c] codebook[c][d]
+ * computed on the tensor cores with BF16 operands and FP32 accumulation.
+ *  codes       DEVICE [P, C] row-major, float32 (codes_dtype 0; rounded to
+ *              bf16 in the workspace) or bf16 (codes_dtype 1), 16-byte aligned.
+ *  codebook    DEVICE float32 [C, D] row-major (rounded to bf16).
+ *  features    DEVICE [P, D] row-major, float32 (out_dtype 0) or bf16
+ *              (out_dtype 1, round to nearest even), 16-byte aligned.
+ *  feat_norm2  DEVICE float32 [P] or NULL: with out_dtype 1, receives the
+ *              squared norm of each stored (rounded) feature row, the input
+ *              scoup_similarity wants; ignored with out_dtype 0.
+ *  workspace   DEVICE, >= scoup_decode_workspace_size(P, C, D) bytes.
+ * Limits: C a multiple of 8 in [8, 4096]; D a multiple of 16, >= 16.
+ * Asynchronous on `stream`; a device-side timeout (a tensor-core pipeline
+ * wait that gave up) is reported by scoup_read_stats on the workspace as
+ * status SCOUP_ERR_TIMEOUT. */
+int scoup_decode(const void* codes, int32_t codes_dtype, int64_t P, int32_t C, const float* codebook,
+                 int32_t D, void* features, int32_t out_dtype, float* feat_norm2, void* workspace,
+                 size_t ws_bytes, void* stream);
+
+/* Workspace bytes for scoup_similarity with P feature rows of dimension D
+ * against Q text vectors. */
+size_t scoup_similarity_workspace_size(int64_t P, int32_t D, int32_t Q);
+
+/* Cosine similarity of decoded features to text embeddings (the open-
+ * vocabulary query of App. B):
+ *   out[p][q] = <f_p, t_q> / (|f_p| |t_q|),  0 where |f_p| < 1e-12 or |t_q| = 0
+ * with BF16 operands and FP32 accumulation on the tensor cores.
+ *  features    DEVICE bf16 [P, D] row-major, 16-byte aligned (scoup_decode
+ *              with out_dtype 1).
+ *  feat_norm2  DEVICE float32 [P] squared feature norms (as scoup_decode
+ *              writes them), or NULL to compute them here.
+ *  text        DEVICE float32 [Q, D] (rounded to bf16; |t_q| is the norm of
+ *              the rounded vector).
+ *  out         DEVICE float32 [P, Q].
+ * Limits: D a multiple of 8; Q a multiple of 16 in [16, 256] (pad the text
+ * set with zero rows).  Asynchronous; errors as for scoup_decode. */
+int scoup_similarity(const void* features, int64_t P, int32_t D, const float* feat_norm2, const float* text,
+                     int32_t Q, float* out, void* workspace, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------ */
 /* Uplift without a caller-provided workspace                           */
 /* ------------------------------------------------------------------ */
 

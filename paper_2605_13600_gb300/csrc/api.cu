@@ -175,6 +175,7 @@ void read_header(const WsHeader& h, scoup_stats* st) {
   st->status = SCOUP_OK;
   if (h.status & kStatCapacity) st->status = SCOUP_ERR_CAPACITY;
   else if (h.status & kStatDeviceCheck) st->status = SCOUP_ERR_DEVICE_CHECK;
+  else if (h.status & kStatTimeout) st->status = SCOUP_ERR_TIMEOUT;
 }
 
 int finish_with_stats(const WsHeader* dev_hdr, scoup_stats* stats, cudaStream_t st) {
@@ -188,6 +189,8 @@ int finish_with_stats(const WsHeader* dev_hdr, scoup_stats* stats, cudaStream_t 
     return fail(SCOUP_ERR_CAPACITY, "tile-list capacity exceeded (largest view needs %d pairs)", h.max_dups_view);
   if (stats->status == SCOUP_ERR_DEVICE_CHECK)
     return fail(SCOUP_ERR_DEVICE_CHECK, "region or atom id out of range");
+  if (stats->status == SCOUP_ERR_TIMEOUT)
+    return fail(SCOUP_ERR_TIMEOUT, "a bounded device wait gave up");
   return SCOUP_OK;
 }
 
@@ -425,6 +428,116 @@ int scoup_render_backward(const scoup_scene* scene, const int32_t* topk_idx, con
       return cuda_fail(e, "render backward");
   }
   if (stats) return finish_with_stats(ws.hdr, stats, st);
+  return SCOUP_OK;
+}
+
+// ---- decode (Eq. 8) and similarity ---------------------------------------
+static int64_t decode_chunk_rows(int64_t P) {
+  const int64_t cap = 262144;
+  const int64_t r = P < cap ? P : cap;
+  return (r + 127) / 128 * 128;
+}
+
+size_t scoup_decode_workspace_size(int64_t P, int32_t C, int32_t D) {
+  if (P < 0 || C <= 0 || D <= 0) return 0;
+  return align_up(sizeof(WsHeader)) + align_up((size_t)D * C * 2) + align_up((size_t)decode_chunk_rows(P) * C * 2);
+}
+
+int scoup_decode(const void* codes, int32_t codes_dtype, int64_t P, int32_t C, const float* codebook, int32_t D,
+                 void* features, int32_t out_dtype, float* feat_norm2, void* workspace, size_t ws_bytes,
+                 void* stream) {
+  if (P < 0) return fail(SCOUP_ERR_INVALID_ARG, "P < 0");
+  if (C < 8 || C % 8 || C > 4096) return fail(SCOUP_ERR_INVALID_ARG, "C=%d must be a multiple of 8 in [8, 4096]", C);
+  if (D < 16 || D % 16) return fail(SCOUP_ERR_INVALID_ARG, "D=%d must be a positive multiple of 16", D);
+  if (codes_dtype != 0 && codes_dtype != 1) return fail(SCOUP_ERR_INVALID_ARG, "codes_dtype must be 0 (f32) or 1 (bf16)");
+  if (out_dtype != 0 && out_dtype != 1) return fail(SCOUP_ERR_INVALID_ARG, "out_dtype must be 0 (f32) or 1 (bf16)");
+  if (P > 0 && (!codes || !codebook || !features)) return fail(SCOUP_ERR_INVALID_ARG, "NULL array");
+  if (((uintptr_t)codes & 15u) || ((uintptr_t)features & 15u))
+    return fail(SCOUP_ERR_INVALID_ARG, "codes and features must be 16-byte aligned");
+  if (!workspace || ws_bytes < scoup_decode_workspace_size(P, C, D))
+    return fail(SCOUP_ERR_OOM, "workspace too small: need %zu bytes", scoup_decode_workspace_size(P, C, D));
+  if (!gemm_tma_available()) return fail(SCOUP_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+  cudaStream_t st = (cudaStream_t)stream;
+  char* w = (char*)workspace;
+  WsHeader* hdr = (WsHeader*)w;
+  void* Bt = w + align_up(sizeof(WsHeader));
+  void* Abuf = (char*)Bt + align_up((size_t)D * C * 2);
+  cudaError_t e;
+  PhaseScope ps(SCOUP_PHASE_DECODE, st);
+  if ((e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
+  if (P == 0) return SCOUP_OK;
+  if (feat_norm2 && (e = cudaMemsetAsync(feat_norm2, 0, sizeof(float) * (size_t)P, st)) != cudaSuccess)
+    return cuda_fail(e, "memset");
+  if ((e = launch_transpose_bf16(codebook, Bt, C, D, st)) != cudaSuccess) return cuda_fail(e, "codebook");
+  const int64_t chunk = decode_chunk_rows(P);
+  for (int64_t r0 = 0; r0 < P; r0 += chunk) {
+    const int64_t rows = P - r0 < chunk ? P - r0 : chunk;
+    const void* A;
+    if (codes_dtype == 0) {
+      if ((e = launch_f32_to_bf16((const float*)codes + r0 * C, Abuf, rows * C, st)) != cudaSuccess)
+        return cuda_fail(e, "convert");
+      A = Abuf;
+    } else {
+      A = (const char*)codes + (size_t)r0 * C * 2;
+    }
+    GemmEpi ep;
+    ep.M = (int)rows;
+    ep.N = D;
+    ep.K = C;
+    ep.mode = out_dtype == 1 ? kOutBF16 : kOutF32;
+    ep.out = (char*)features + (size_t)r0 * D * (out_dtype == 1 ? 2 : 4);
+    ep.ldo = D;
+    ep.rownorm2 = (out_dtype == 1 && feat_norm2) ? feat_norm2 + r0 : nullptr;
+    ep.colnorm = nullptr;
+    ep.status = &hdr->status;
+    if ((e = launch_gemm_bf16(A, Bt, ep, st)) != cudaSuccess) return cuda_fail(e, "decode gemm");
+  }
+  return SCOUP_OK;
+}
+
+size_t scoup_similarity_workspace_size(int64_t P, int32_t D, int32_t Q) {
+  if (P < 0 || D <= 0 || Q <= 0) return 0;
+  return align_up(sizeof(WsHeader)) + align_up((size_t)Q * D * 2) + align_up((size_t)Q * 4) + align_up((size_t)P * 4);
+}
+
+int scoup_similarity(const void* features, int64_t P, int32_t D, const float* feat_norm2, const float* text,
+                     int32_t Q, float* out, void* workspace, size_t ws_bytes, void* stream) {
+  if (P < 0) return fail(SCOUP_ERR_INVALID_ARG, "P < 0");
+  if (D < 8 || D % 8) return fail(SCOUP_ERR_INVALID_ARG, "D=%d must be a positive multiple of 8", D);
+  if (Q < 16 || Q % 16 || Q > 256) return fail(SCOUP_ERR_INVALID_ARG, "Q=%d must be a multiple of 16 in [16, 256]", Q);
+  if (P > 0 && (!features || !text || !out)) return fail(SCOUP_ERR_INVALID_ARG, "NULL array");
+  if ((uintptr_t)features & 15u) return fail(SCOUP_ERR_INVALID_ARG, "features must be 16-byte aligned");
+  if (!workspace || ws_bytes < scoup_similarity_workspace_size(P, D, Q))
+    return fail(SCOUP_ERR_OOM, "workspace too small: need %zu bytes", scoup_similarity_workspace_size(P, D, Q));
+  if (!gemm_tma_available()) return fail(SCOUP_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+  cudaStream_t st = (cudaStream_t)stream;
+  char* w = (char*)workspace;
+  WsHeader* hdr = (WsHeader*)w;
+  void* tb = w + align_up(sizeof(WsHeader));
+  float* tnorm = (float*)((char*)tb + align_up((size_t)Q * D * 2));
+  float* fnorm2 = (float*)((char*)tnorm + align_up((size_t)Q * 4));
+  cudaError_t e;
+  PhaseScope ps(SCOUP_PHASE_SIMILARITY, st);
+  if ((e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
+  if (P == 0) return SCOUP_OK;
+  if ((e = launch_f32_to_bf16(text, tb, (int64_t)Q * D, st)) != cudaSuccess) return cuda_fail(e, "text");
+  if ((e = launch_row_norm_bf16(tb, Q, D, tnorm, 0, st)) != cudaSuccess) return cuda_fail(e, "text norms");
+  const float* rn2 = feat_norm2;
+  if (!rn2) {
+    if ((e = launch_row_norm_bf16(features, P, D, fnorm2, 1, st)) != cudaSuccess) return cuda_fail(e, "norms");
+    rn2 = fnorm2;
+  }
+  GemmEpi ep;
+  ep.M = (int)P;
+  ep.N = Q;
+  ep.K = D;
+  ep.mode = kOutCos;
+  ep.out = out;
+  ep.ldo = Q;
+  ep.rownorm2 = const_cast<float*>(rn2);
+  ep.colnorm = tnorm;
+  ep.status = &hdr->status;
+  if ((e = launch_gemm_bf16(features, tb, ep, st)) != cudaSuccess) return cuda_fail(e, "similarity gemm");
   return SCOUP_OK;
 }
 

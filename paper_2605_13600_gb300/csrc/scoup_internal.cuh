@@ -19,6 +19,7 @@ constexpr int kTilePixels = kTile * kTile;
 // Device status bits (workspace header).
 constexpr int kStatCapacity = 1;
 constexpr int kStatDeviceCheck = 2;
+constexpr int kStatTimeout = 4;
 
 // Workspace header: status word, per-view depth range (double-buffered by
 // view parity), scene bounding box and counters, 256 bytes.
@@ -134,6 +135,21 @@ size_t render_bwd_smem_bytes(int C, int K);
 cudaError_t launch_render_bwd(const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* topk_idx,
                               const float* topk_val, int K, int C, const float* dL_dcodes, float* d_val,
                               float* d_opacity, cudaStream_t st);
+constexpr int kOutBF16 = 0, kOutF32 = 1, kOutCos = 2;
+struct GemmEpi {
+  int M, N, K;
+  int mode;              // kOutBF16 / kOutF32 / kOutCos
+  void* out;
+  int64_t ldo;           // elements
+  float* rownorm2;       // kOutBF16: accumulated squared row norms (may be null); kOutCos: input
+  const float* colnorm;  // kOutCos: column norms
+  int* status;
+};
+cudaError_t launch_gemm_bf16(const void* A, const void* Bt, const GemmEpi& ep, cudaStream_t st);
+cudaError_t launch_f32_to_bf16(const float* x, void* y, int64_t n, cudaStream_t st);
+cudaError_t launch_transpose_bf16(const float* B, void* Bt, int Cdim, int D, cudaStream_t st);
+cudaError_t launch_row_norm_bf16(const void* X, int64_t R, int D, float* out, int squared, cudaStream_t st);
+bool gemm_tma_available();
 cudaError_t launch_topk(const float* accum, int64_t n, int C, int K, int32_t* idx, float* val,
                         cudaStream_t st);
 cudaError_t launch_code_topk(const int32_t* ci, const float* cv, int64_t R, int s, int K,

@@ -225,6 +225,63 @@ class Render:
         return out, st
 
 
+def scoup_decode_workspace_size(P: int, C: int, D: int) -> int:
+    return int(load().scoup_decode_workspace_size(P, C, D))
+
+
+def scoup_decode(codes, codebook, features, feat_norm2=None, workspace=None, stream=None):
+    """Eq. 8: features = codes @ codebook on the tensor cores (bf16 operands, f32 accumulate).
+
+    codes [P, C] float32 or bfloat16; codebook [C, D] float32; features [P, D]
+    float32 or bfloat16 (the output type); feat_norm2 [P] float32 (bf16 output
+    only) receives the squared norms of the stored rows.  Returns the workspace.
+    """
+    import torch
+    if codes.dtype not in (torch.float32, torch.bfloat16):
+        raise TypeError("codes must be float32 or bfloat16")
+    if features.dtype not in (torch.float32, torch.bfloat16):
+        raise TypeError("features must be float32 or bfloat16")
+    _need(codes, codes.dtype, "codes")
+    _need(codebook, torch.float32, "codebook")
+    _need(features, features.dtype, "features")
+    _need(feat_norm2, torch.float32, "feat_norm2")
+    P, C = codes.shape
+    D = codebook.shape[1]
+    if codebook.shape[0] != C or tuple(features.shape) != (P, D):
+        raise ValueError("shape mismatch")
+    if workspace is None:
+        workspace = torch.empty(scoup_decode_workspace_size(P, C, D), dtype=torch.uint8, device=codes.device)
+    _need(workspace, torch.uint8, "workspace")
+    check(load().scoup_decode(_ptr(codes), 1 if codes.dtype == torch.bfloat16 else 0, P, C, _ptr(codebook), D,
+                              _ptr(features), 1 if features.dtype == torch.bfloat16 else 0, _ptr(feat_norm2),
+                              _ptr(workspace), workspace.numel(), _stream(stream)))
+    return workspace
+
+
+def scoup_similarity_workspace_size(P: int, D: int, Q: int) -> int:
+    return int(load().scoup_similarity_workspace_size(P, D, Q))
+
+
+def scoup_similarity(features, text, out, feat_norm2=None, workspace=None, stream=None):
+    """Cosine similarity out [P, Q] of bf16 features [P, D] to float32 text vectors [Q, D]."""
+    import torch
+    _need(features, torch.bfloat16, "features")
+    _need(text, torch.float32, "text")
+    _need(out, torch.float32, "out")
+    _need(feat_norm2, torch.float32, "feat_norm2")
+    P, D = features.shape
+    Q = text.shape[0]
+    if text.shape[1] != D or tuple(out.shape) != (P, Q):
+        raise ValueError("shape mismatch")
+    if workspace is None:
+        workspace = torch.empty(scoup_similarity_workspace_size(P, D, Q), dtype=torch.uint8,
+                                device=features.device)
+    _need(workspace, torch.uint8, "workspace")
+    check(load().scoup_similarity(_ptr(features), P, D, _ptr(feat_norm2), _ptr(text), Q, _ptr(out),
+                                  _ptr(workspace), workspace.numel(), _stream(stream)))
+    return workspace
+
+
 def scoup_read_stats(workspace, stream=None) -> dict:
     st = Stats()
     check(load().scoup_read_stats(_ptr(workspace), workspace.numel(), ct.byref(st), _stream(stream)))
