@@ -45,6 +45,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU oracle sample budget")
+    ap.add_argument("--render-views", type=int, default=8,
+                    help="views of the 1920x1080 render + decode measurement (0 = skip)")
     return ap.parse_args()
 
 
@@ -353,6 +355,10 @@ def run_gb300(args, dist):
                "sample": f"views 0..{nv - 1} of 200 of the same workload (all 1M Gaussians, 988x731), "
                          f"FP64 oracle, {el:.1f} s"}
 
+    rd = None
+    if args.render_views > 0:
+        rd = render_decode_leg(args, dist, wl, up, dev, pk)
+
     if dist.rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
@@ -368,8 +374,103 @@ def run_gb300(args, dist):
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk, "phase_ms_per_step": step_ms,
             "stats": {k: st0[k] for k in ("visible", "duplicates", "flushes", "atomics")},
+            "render_decode": rd,
         }
         print(json.dumps(line), flush=True)
+
+
+def render_decode_leg(args, dist, wl, up, dev, pk):
+    """Secondary measurement: sparse-code rendering (Eq. 7) of 1920x1080 views of
+    the same 1M Gaussians with the Top-K codes the uplift just produced, codebook
+    decode (Eq. 8) to bf16 features and cosine similarity to 32 text vectors.
+    Returns the MPix/s figure with its phase split and the decode GEMM roofline."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2605_13600_gb300 as gb
+
+    rw = synth.render_cfg4(n_views=args.render_views)
+    cams = rw.cams
+    ren = gb.Render(wl.scene, up.topk_idx.cpu().numpy(), up.topk_val.cpu().numpy(), wl.C, cams,
+                    device=str(dev))
+    H, W = cams[0].height, cams[0].width
+    P = H * W
+    D, Q = rw.codebook.shape[1], rw.text.shape[0]
+    out = ren.outputs(cams[0])
+    codebook = torch.from_numpy(rw.codebook).to(dev)
+    text = torch.from_numpy(rw.text).to(dev)
+    feats = torch.empty((P, D), dtype=torch.bfloat16, device=dev)
+    n2 = torch.empty((P,), dtype=torch.float32, device=dev)
+    sim = torch.empty((P, Q), dtype=torch.float32, device=dev)
+    dws = torch.empty(gb.scoup_decode_workspace_size(P, wl.C, D), dtype=torch.uint8, device=dev)
+    sws = torch.empty(gb.scoup_similarity_workspace_size(P, D, Q), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def view(v):
+        ren.run(v, out=out, stats=False)
+        gb.scoup_decode(out[0].view(P, wl.C), codebook, feats, n2, workspace=dws)
+        gb.scoup_similarity(feats, text, sim, feat_norm2=n2, workspace=sws)
+
+    stats = [ren.run(v, out=out, stats=True)[1] for v in range(len(cams))]
+    for st in stats:
+        if st["status"] != 0:
+            raise RuntimeError(f"render status {st['status']}")
+    for _ in range(max(3, args.warmup)):
+        view(0)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dist.barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for v in range(len(cams)):
+        view(v)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    t = dist.max(ev0.elapsed_time(ev1) / 1e3)
+    mpix = dist.world * len(cams) * P / t / 1e6
+
+    gb.scoup_profile_enable(True)
+    for v in range(len(cams)):
+        view(v)
+    torch.cuda.synchronize()
+    prof = gb.scoup_profile_read()
+    gb.scoup_profile_enable(False)
+    phase_ms = {k: prof[k][0] / len(cams) for k in ("render", "decode", "similarity") if k in prof}
+    if gb.scoup_read_stats(dws)["status"] != 0 or gb.scoup_read_stats(sws)["status"] != 0:
+        raise RuntimeError("decode/similarity device status")
+
+    # the decode GEMM alone: bf16 codes in, bf16 features out (one launch + a 256x512 transpose)
+    codes_bf16 = out[0].view(P, wl.C).to(torch.bfloat16)
+    for _ in range(3):
+        gb.scoup_decode(codes_bf16, codebook, feats, n2, workspace=dws)
+    torch.cuda.synchronize()
+    reps = 10
+    ev0.record(stream)
+    for _ in range(reps):
+        gb.scoup_decode(codes_bf16, codebook, feats, n2, workspace=dws)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_gemm = ev0.elapsed_time(ev1) / 1e3 / reps
+    flops = 2.0 * P * wl.C * D
+    del codes_bf16
+    evaluated = sum(s["evaluated_pairs"] for s in stats) / len(stats)
+    contrib = sum(s["contributions"] for s in stats) / len(stats)
+    return {
+        "metric": "render+decode+similarity pixels/s", "value": mpix, "unit": "MPix/s",
+        "workload": rw.name, "views_timed": len(cams), "pixels_per_view": P,
+        "C": wl.C, "D": D, "Q": Q, "K": wl.K,
+        "codes": "Top-K of the uplift measured above",
+        "ms_per_view": t * 1e3 / len(cams), "phase_ms_per_view": phase_ms,
+        "render_evaluated_pairs_per_view": evaluated, "render_contributions_per_view": contrib,
+        "decode_roofline": {"kernel": "gemm_bf16_kernel", "bound": "tensor",
+                            "achieved": flops / t_gemm / 1e12, "peak": pk["bf16_tflops"],
+                            "unit": "TFLOP/s", "frac": flops / t_gemm / 1e12 / pk["bf16_tflops"],
+                            "per_launch_ms": t_gemm * 1e3,
+                            "hbm_gbs": (2.0 * P * wl.C + 2.0 * P * D) / t_gemm / 1e9,
+                            "peak_source": pk["source"] + " bf16 burst"},
+    }
 
 
 def main():

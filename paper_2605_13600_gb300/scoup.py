@@ -359,4 +359,6 @@ __all__ = ["ScoupError", "scene_struct", "camera_array", "scoup_version",
            "scoup_uplift_workspace_size", "scoup_uplift_plan", "scoup_uplift", "scoup_topk",
            "scoup_read_stats", "scoup_uplift_noalloc", "scoup_uplift_noalloc_max_bytes",
            "scoup_profile_enable", "scoup_profile_read", "scoup_launch_count",
-           "scoup_render", "scoup_render_backward", "Render", "Uplift"]
+           "scoup_render", "scoup_render_backward", "Render", "Uplift",
+           "scoup_decode_workspace_size", "scoup_decode", "scoup_similarity_workspace_size",
+           "scoup_similarity"]
