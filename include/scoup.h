@@ -39,7 +39,7 @@ extern "C" {
 #define SCOUP_ERR_OOM (-3)           /* workspace smaller than required */
 #define SCOUP_ERR_CAPACITY (-4)      /* device: tile-list capacity exceeded */
 #define SCOUP_ERR_DEVICE_CHECK (-5)  /* device: region/atom id out of range */
-#define SCOUP_ERR_TIMEOUT (-6)       /* reserved: a bounded device wait gave up */
+#define SCOUP_ERR_TIMEOUT (-6)       /* device: a bounded wait in a tensor-core pipeline gave up */
 
 /* Gaussians of a 3DGS scene (paper Sec. 3): means mu_i, linear scales s_i
  * (exp of the stored log-scales), unit quaternions q_i in (w, x, y, z)
@@ -94,6 +94,9 @@ size_t scoup_uplift_workspace_size(int64_t n, int32_t max_width, int32_t max_hei
 int scoup_uplift_plan(const scoup_scene* scene, const scoup_camera* cams, int32_t V,
                       void* workspace, size_t ws_bytes, int64_t* max_dups, void* stream);
 
+#define SCOUP_ACCUM_CONTINUE 1    /* accum_mode: add to the accumulator instead of zeroing it */
+#define SCOUP_ACCUM_COMPENSATED 2 /* accum_mode: compensated (TwoSum) FP32 accumulation */
+
 /* Sparse coefficient uplift.  For every view v (cams[v], host array of V),
  * rasterizes the scene with standard 3DGS compositing (Sec. 3, Eq. 2) and
  * adds, for every accepted (pixel p, Gaussian i) pair with weight
@@ -112,9 +115,16 @@ int scoup_uplift_plan(const scoup_scene* scene, const scoup_camera* cams, int32_
  *  code_idx     int32 [R_total, s] atom ids (< C) or -1 padding.
  *  code_val     float32 [R_total, s] nonnegative coefficients (Eq. 4).
  *               If s > K, each code's K largest entries are used (Alg. 1).
- *  accum        float32 [n, C] row-major accumulator (caller-owned).
- *  accum_mode   0: zero accum first; 1: add to its current contents (resume
- *               a chunked uplift).
+ *  accum        float32 [n, C] row-major accumulator (caller-owned); with
+ *               SCOUP_ACCUM_COMPENSATED, float32 [2, n, C]: the running sums
+ *               followed by their compensation terms (value = sum + term).
+ *  accum_mode   bit flags.  Without SCOUP_ACCUM_CONTINUE accum is zeroed
+ *               first; with it the call adds to the current contents (resume
+ *               a chunked uplift).  SCOUP_ACCUM_COMPENSATED: every FP32
+ *               addition into the per-tile partials and into accum carries
+ *               its exact rounding error (TwoSum) into a compensation term,
+ *               as does the product code value x weight; Top-K ranks
+ *               sum + term.  Slower (one more atomic per update).
  *  topk_idx     int32 [n, K] or NULL (accumulate only); topk_val float32 [n, K].
  *  workspace    device scratch of ws_bytes >= scoup_uplift_workspace_size().
  *  stats        HOST scoup_stats* or NULL; when given, the call synchronises
@@ -219,6 +229,20 @@ size_t scoup_similarity_workspace_size(int64_t P, int32_t D, int32_t Q);
  * set with zero rows).  Asynchronous; errors as for scoup_decode. */
 int scoup_similarity(const void* features, int64_t P, int32_t D, const float* feat_norm2, const float* text,
                      int32_t Q, float* out, void* workspace, size_t ws_bytes, void* stream);
+
+/* FP32 comparison forms of scoup_decode and scoup_similarity: the same
+ * results computed with FP32 operands and FP32 FFMA accumulation on the SIMT
+ * cores (no rounding of the inputs), for measuring the BF16 forms against.
+ *  scoup_decode_fp32:     codes float32 [P, C], codebook float32 [C, D],
+ *                         features float32 [P, D].  No workspace.
+ *  scoup_similarity_fp32: features float32 [P, D], text float32 [Q, D],
+ *                         out float32 [P, Q]; workspace as for
+ *                         scoup_similarity (scoup_similarity_workspace_size).
+ * All DEVICE pointers; asynchronous on `stream`; any P, C, D, Q >= 1. */
+int scoup_decode_fp32(const float* codes, int64_t P, int32_t C, const float* codebook, int32_t D,
+                      float* features, void* stream);
+int scoup_similarity_fp32(const float* features, int64_t P, int32_t D, const float* text, int32_t Q,
+                          float* out, void* workspace, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------ */
 /* Uplift without a caller-provided workspace                           */

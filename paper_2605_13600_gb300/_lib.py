@@ -19,6 +19,9 @@ SCOUP_ERR_CAPACITY = -4
 SCOUP_ERR_DEVICE_CHECK = -5
 SCOUP_ERR_TIMEOUT = -6
 
+SCOUP_ACCUM_CONTINUE = 1
+SCOUP_ACCUM_COMPENSATED = 2
+
 
 class ScoupError(RuntimeError):
     def __init__(self, code: int, msg: str):
@@ -73,6 +76,8 @@ PROTOS = {
     "scoup_decode": (ct.c_int, [P, I32, I64, I32, P, I32, P, I32, P, P, SZ, P]),
     "scoup_similarity_workspace_size": (SZ, [I64, I32, I32]),
     "scoup_similarity": (ct.c_int, [P, I64, I32, P, P, I32, P, P, SZ, P]),
+    "scoup_decode_fp32": (ct.c_int, [P, I64, I32, P, I32, P, P]),
+    "scoup_similarity_fp32": (ct.c_int, [P, I64, I32, P, I32, P, P, SZ, P]),
     "scoup_uplift_noalloc_max_bytes": (SZ, []),
     "scoup_uplift_noalloc": (ct.c_int, [ct.POINTER(Scene), P, I32, P, P, I32, P, P, I32, I32, I32, P, I32,
                                         P, P, ct.POINTER(Stats), P]),

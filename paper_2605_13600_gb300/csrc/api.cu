@@ -263,7 +263,8 @@ int scoup_uplift(const scoup_scene* scene, const scoup_camera* cams, int32_t V,
   if (K < 1 || K > C) return fail(SCOUP_ERR_INVALID_ARG, "K=%d outside [1, C=%d]", K, C);
   if (s < 1 || s > 64) return fail(SCOUP_ERR_INVALID_ARG, "s=%d outside [1, 64]", s);
   if (R_total < 0) return fail(SCOUP_ERR_INVALID_ARG, "R_total=%d < 0", R_total);
-  if (accum_mode != 0 && accum_mode != 1) return fail(SCOUP_ERR_INVALID_ARG, "accum_mode must be 0 or 1");
+  if (accum_mode & ~(SCOUP_ACCUM_CONTINUE | SCOUP_ACCUM_COMPENSATED))
+    return fail(SCOUP_ERR_INVALID_ARG, "accum_mode=%d: only SCOUP_ACCUM_CONTINUE and SCOUP_ACCUM_COMPENSATED", accum_mode);
   if (scene->n > 0 && !accum) return fail(SCOUP_ERR_INVALID_ARG, "accum is NULL");
   if ((topk_idx == nullptr) != (topk_val == nullptr))
     return fail(SCOUP_ERR_INVALID_ARG, "topk_idx and topk_val must both be given or both be NULL");
@@ -284,8 +285,11 @@ int scoup_uplift(const scoup_scene* scene, const scoup_camera* cams, int32_t V,
   const int64_t n = scene->n;
   cudaError_t e;
   if ((e = cudaMemsetAsync(ws.hdr, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
-  if (n > 0 && accum_mode == 0 &&
-      (e = cudaMemsetAsync(accum, 0, sizeof(float) * (size_t)n * (size_t)C, st)) != cudaSuccess)
+  const bool compensated = (accum_mode & SCOUP_ACCUM_COMPENSATED) != 0;
+  float* comp = compensated ? accum + (size_t)n * (size_t)C : nullptr;
+  if (n > 0 && !(accum_mode & SCOUP_ACCUM_CONTINUE) &&
+      (e = cudaMemsetAsync(accum, 0, sizeof(float) * (size_t)n * (size_t)C * (compensated ? 2 : 1), st)) !=
+          cudaSuccess)
     return cuda_fail(e, "memset accum");
   if ((e = cudaMemsetAsync(ws.tile_count, 0, sizeof(uint32_t) * ((size_t)max_tiles + 1), st)) != cudaSuccess)
     return cuda_fail(e, "memset");
@@ -318,14 +322,15 @@ int scoup_uplift(const scoup_scene* scene, const scoup_camera* cams, int32_t V,
       {
         PhaseScope ps(SCOUP_PHASE_UPLIFT_TILES, st);
         if ((e = launch_uplift_tiles(ca, ws, v & 1, region_maps + map_offsets[v], R_total, ci, cv, s_eff,
-                                     C, accum, st)) != cudaSuccess)
+                                     C, accum, comp, st)) != cudaSuccess)
           return cuda_fail(e, "uplift tiles");
       }
     }
   }
   if (topk_idx && n > 0) {
     PhaseScope ps(SCOUP_PHASE_TOPK, st);
-    if ((e = launch_topk(accum, n, C, K, topk_idx, topk_val, st)) != cudaSuccess) return cuda_fail(e, "top-k");
+    if ((e = launch_topk(accum, comp, n, C, K, topk_idx, topk_val, st)) != cudaSuccess)
+      return cuda_fail(e, "top-k");
   }
   if (stats) return finish_with_stats(ws.hdr, stats, st);
   return SCOUP_OK;
@@ -541,6 +546,37 @@ int scoup_similarity(const void* features, int64_t P, int32_t D, const float* fe
   return SCOUP_OK;
 }
 
+int scoup_decode_fp32(const float* codes, int64_t P, int32_t C, const float* codebook, int32_t D,
+                      float* features, void* stream) {
+  if (P < 0 || C < 1 || D < 1) return fail(SCOUP_ERR_INVALID_ARG, "bad sizes P=%lld C=%d D=%d", (long long)P, C, D);
+  if (P > 0 && (!codes || !codebook || !features)) return fail(SCOUP_ERR_INVALID_ARG, "NULL array");
+  cudaStream_t st = (cudaStream_t)stream;
+  PhaseScope ps(SCOUP_PHASE_DECODE, st);
+  const cudaError_t e = launch_sgemm(codes, codebook, false, features, P, D, C, nullptr, nullptr, st);
+  return e == cudaSuccess ? SCOUP_OK : cuda_fail(e, "fp32 decode");
+}
+
+int scoup_similarity_fp32(const float* features, int64_t P, int32_t D, const float* text, int32_t Q, float* out,
+                          void* workspace, size_t ws_bytes, void* stream) {
+  if (P < 0 || D < 1 || Q < 1) return fail(SCOUP_ERR_INVALID_ARG, "bad sizes P=%lld D=%d Q=%d", (long long)P, D, Q);
+  if (P > 0 && (!features || !text || !out)) return fail(SCOUP_ERR_INVALID_ARG, "NULL array");
+  const size_t need = align_up(sizeof(WsHeader)) + align_up((size_t)Q * 4) + align_up((size_t)P * 4);
+  if (!workspace || ws_bytes < need) return fail(SCOUP_ERR_OOM, "workspace too small: need %zu bytes", need);
+  cudaStream_t st = (cudaStream_t)stream;
+  char* w = (char*)workspace;
+  float* tn2 = (float*)(w + align_up(sizeof(WsHeader)));
+  float* fn2 = (float*)((char*)tn2 + align_up((size_t)Q * 4));
+  cudaError_t e;
+  PhaseScope ps(SCOUP_PHASE_SIMILARITY, st);
+  if ((e = cudaMemsetAsync(w, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
+  if (P == 0) return SCOUP_OK;
+  if ((e = launch_row_norm2_f32(text, Q, D, tn2, st)) != cudaSuccess) return cuda_fail(e, "text norms");
+  if ((e = launch_row_norm2_f32(features, P, D, fn2, st)) != cudaSuccess) return cuda_fail(e, "norms");
+  if ((e = launch_sgemm(features, text, true, out, P, Q, D, fn2, tn2, st)) != cudaSuccess)
+    return cuda_fail(e, "fp32 similarity");
+  return SCOUP_OK;
+}
+
 int scoup_topk(const float* accum, int64_t n, int32_t C, int32_t K, int32_t* topk_idx,
                float* topk_val, void* stream) {
   if (n < 0) return fail(SCOUP_ERR_INVALID_ARG, "n < 0");
@@ -548,7 +584,7 @@ int scoup_topk(const float* accum, int64_t n, int32_t C, int32_t K, int32_t* top
   if (K < 1 || K > C) return fail(SCOUP_ERR_INVALID_ARG, "K=%d outside [1, C=%d]", K, C);
   if (n > 0 && (!accum || !topk_idx || !topk_val)) return fail(SCOUP_ERR_INVALID_ARG, "NULL array");
   PhaseScope ps(SCOUP_PHASE_TOPK, (cudaStream_t)stream);
-  cudaError_t e = launch_topk(accum, n, C, K, topk_idx, topk_val, (cudaStream_t)stream);
+  cudaError_t e = launch_topk(accum, nullptr, n, C, K, topk_idx, topk_val, (cudaStream_t)stream);
   return e == cudaSuccess ? SCOUP_OK : cuda_fail(e, "top-k");
 }
 

@@ -126,7 +126,7 @@ cudaError_t launch_binning(const CamArgs& cam, int64_t n, const UpliftWs& ws, in
                            cudaStream_t st);
 cudaError_t launch_uplift_tiles(const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* rmap,
                                 int32_t R_total, const int32_t* code_idx, const float* code_val,
-                                int s, int C, float* accum, cudaStream_t st);
+                                int s, int C, float* accum, float* comp, cudaStream_t st);
 size_t render_smem_bytes(int C);
 cudaError_t launch_render_tiles(const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* topk_idx,
                                 const float* topk_val, int K, int C, float* out, float* out_T,
@@ -150,7 +150,10 @@ cudaError_t launch_f32_to_bf16(const float* x, void* y, int64_t n, cudaStream_t 
 cudaError_t launch_transpose_bf16(const float* B, void* Bt, int Cdim, int D, cudaStream_t st);
 cudaError_t launch_row_norm_bf16(const void* X, int64_t R, int D, float* out, int squared, cudaStream_t st);
 bool gemm_tma_available();
-cudaError_t launch_topk(const float* accum, int64_t n, int C, int K, int32_t* idx, float* val,
+cudaError_t launch_sgemm(const float* A, const float* B, bool b_transposed, float* out, int64_t M, int N, int K,
+                         const float* rownorm2, const float* colnorm2, cudaStream_t st);
+cudaError_t launch_row_norm2_f32(const float* X, int64_t R, int D, float* out, cudaStream_t st);
+cudaError_t launch_topk(const float* accum, const float* comp, int64_t n, int C, int K, int32_t* idx, float* val,
                         cudaStream_t st);
 cudaError_t launch_code_topk(const int32_t* ci, const float* cv, int64_t R, int s, int K,
                              int32_t* ci_out, float* cv_out, cudaStream_t st);

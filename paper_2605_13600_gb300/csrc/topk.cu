@@ -5,6 +5,8 @@
 // registers; each of the K rounds picks the largest remaining positive entry
 // (ties to the lower atom index) with a butterfly arg-max across the warp.
 // The row is read once from HBM (coalesced), which makes this kernel HBM-bound.
+// With a compensation array (the compensated uplift) each entry is the FP32
+// sum of the running sum and its compensation.
 #include "scoup_internal.cuh"
 
 namespace scoup {
@@ -17,8 +19,8 @@ __device__ __forceinline__ bool better(float v, int j, float ov, int oj) {
 }
 
 template <int VPL>
-__global__ void __launch_bounds__(256) topk_kernel(const float* __restrict__ acc, int64_t n, int C,
-                                                   int K, int32_t* __restrict__ idx,
+__global__ void __launch_bounds__(256) topk_kernel(const float* __restrict__ acc, const float* __restrict__ comp,
+                                                   int64_t n, int C, int K, int32_t* __restrict__ idx,
                                                    float* __restrict__ val) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -28,7 +30,7 @@ __global__ void __launch_bounds__(256) topk_kernel(const float* __restrict__ acc
 #pragma unroll
     for (int k = 0; k < VPL; ++k) {
       const int j = lane + 32 * k;
-      v[k] = j < C ? a[j] : 0.0f;
+      v[k] = j < C ? (comp ? __fadd_rn(a[j], comp[row * C + j]) : a[j]) : 0.0f;
     }
     unsigned taken = 0u;
     float sum = 0.0f;
@@ -88,26 +90,26 @@ __global__ void code_topk_kernel(const int32_t* __restrict__ ci, const float* __
 }
 
 template <int VPL>
-cudaError_t launch_vpl(const float* acc, int64_t n, int C, int K, int32_t* idx, float* val,
+cudaError_t launch_vpl(const float* acc, const float* comp, int64_t n, int C, int K, int32_t* idx, float* val,
                        cudaStream_t st) {
   int64_t blocks = (n + 7) / 8;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  topk_kernel<VPL><<<(int)blocks, 256, 0, st>>>(acc, n, C, K, idx, val);
+  topk_kernel<VPL><<<(int)blocks, 256, 0, st>>>(acc, comp, n, C, K, idx, val);
   g_launches += 1;
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_topk(const float* acc, int64_t n, int C, int K, int32_t* idx, float* val,
+cudaError_t launch_topk(const float* acc, const float* comp, int64_t n, int C, int K, int32_t* idx, float* val,
                         cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  if (C <= 32) return launch_vpl<1>(acc, n, C, K, idx, val, st);
-  if (C <= 64) return launch_vpl<2>(acc, n, C, K, idx, val, st);
-  if (C <= 128) return launch_vpl<4>(acc, n, C, K, idx, val, st);
-  if (C <= 256) return launch_vpl<8>(acc, n, C, K, idx, val, st);
-  if (C <= 512) return launch_vpl<16>(acc, n, C, K, idx, val, st);
-  return launch_vpl<32>(acc, n, C, K, idx, val, st);
+  if (C <= 32) return launch_vpl<1>(acc, comp, n, C, K, idx, val, st);
+  if (C <= 64) return launch_vpl<2>(acc, comp, n, C, K, idx, val, st);
+  if (C <= 128) return launch_vpl<4>(acc, comp, n, C, K, idx, val, st);
+  if (C <= 256) return launch_vpl<8>(acc, comp, n, C, K, idx, val, st);
+  if (C <= 512) return launch_vpl<16>(acc, comp, n, C, K, idx, val, st);
+  return launch_vpl<32>(acc, comp, n, C, K, idx, val, st);
 }
 
 cudaError_t launch_code_topk(const int32_t* ci, const float* cv, int64_t R, int s, int K,

@@ -22,6 +22,14 @@
 // per-(region, Gaussian) tile partials live in shared memory and are flushed
 // as s global atomics once per window.
 //
+// Compensated form (kComp).  Every FP32 addition into the tile partials and
+// into the global accumulator goes through an atomic that returns the old
+// value; the rounding error of that addition is recovered exactly with
+// Knuth's TwoSum (the atomic rounds to nearest, like the thread's own add) and
+// added to a companion array (shared memory for the partials, accum + n*C in
+// global memory), together with the exact error of the product c * e
+// (fma(c, e, -c*e)).  The value of an entry is then sum + compensation.
+//
 // Load balance.  After the block-wide ordering of a window, each warp walks
 // it independently (records staged per warp, no block barrier) and leaves as
 // soon as its 32 pixels are saturated; the block meets again only at the end
@@ -42,6 +50,7 @@ constexpr int kMaxS = 64;
 constexpr int kGroup = 8;
 constexpr unsigned kFull = 0xffffffffu;
 
+template <bool kComp>
 struct TileSmem {
   uint32_t bstart[kNB + 1];
   uint32_t bcur[kNB];
@@ -50,6 +59,7 @@ struct TileSmem {
   float4 stage_b[kThreads / 32][32];
   int stage_g[kThreads / 32][32];
   float part[kMaxSlots][kWin];
+  float part_c[kComp ? kMaxSlots : 1][kComp ? kWin : 1];
   int slot_region[kMaxSlots];
   int slot_idx[kMaxSlots][kMaxS];
   float slot_val[kMaxSlots][kMaxS];
@@ -77,7 +87,8 @@ struct Buckets {
 
 // Block-wide: the rank-th smallest (0-based) key among those in bucket b
 // with (first || key > last).  Keys are unique; requires rank < their count.
-__device__ unsigned long long select_in_bucket(TileSmem& sm, const unsigned long long* __restrict__ keys,
+template <class Smem>
+__device__ unsigned long long select_in_bucket(Smem& sm, const unsigned long long* __restrict__ keys,
                                                int n, const Buckets& bk, int b, unsigned long long last,
                                                bool first, int rank) {
   const int tid = threadIdx.x;
@@ -158,13 +169,48 @@ __device__ __forceinline__ float transpose_reduce8(const float (&v)[kGroup], int
   return d;
 }
 
-__global__ void __launch_bounds__(kThreads, 4) uplift_tile_kernel(
+// Error of s = fl(a + b) (Knuth's TwoSum): a + b = s + err exactly.
+__device__ __forceinline__ float two_sum_err(float a, float b, float s) {
+  const float bp = __fsub_rn(s, a);
+  const float ap = __fsub_rn(s, bp);
+  return __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+
+// part[i] += v (shared memory), compensated when kComp.
+template <bool kComp>
+__device__ __forceinline__ void part_add(float* part, float* part_c, int i, float v) {
+  if constexpr (!kComp) {
+    atomicAdd(&part[i], v);
+  } else {
+    const float old = atomicAdd(&part[i], v);
+    const float err = two_sum_err(old, v, __fadd_rn(old, v));
+    if (err != 0.0f) atomicAdd(&part_c[i], err);
+  }
+}
+
+// accum[x] += c * (v + vc) (global memory), compensated when kComp (vc is the
+// compensation of v; 0 in the plain form).
+template <bool kComp>
+__device__ __forceinline__ void acc_add(float* accum, float* comp, int64_t x, float c, float v, float vc) {
+  if constexpr (!kComp) {
+    atomicAdd(&accum[x], c * v);
+  } else {
+    const float p = __fmul_rn(c, v);
+    const float perr = __fmaf_rn(c, v, -p);  // c * v - p exactly
+    const float old = atomicAdd(&accum[x], p);
+    const float err = __fadd_rn(__fadd_rn(two_sum_err(old, p, __fadd_rn(old, p)), perr), __fmul_rn(c, vc));
+    if (err != 0.0f) atomicAdd(&comp[x], err);
+  }
+}
+
+template <bool kComp>
+__global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
     CamArgs cam, const ProjRec* __restrict__ proj, const unsigned long long* __restrict__ keys,
     const uint32_t* __restrict__ tile_start, int slot, const int32_t* __restrict__ rmap,
     int32_t R_total, const int32_t* __restrict__ code_idx, const float* __restrict__ code_val, int s,
-    int C, float* __restrict__ accum, WsHeader* __restrict__ hdr) {
+    int C, float* __restrict__ accum, float* __restrict__ comp, WsHeader* __restrict__ hdr) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  TileSmem& sm = *reinterpret_cast<TileSmem*>(smem_raw);
+  TileSmem<kComp>& sm = *reinterpret_cast<TileSmem<kComp>*>(smem_raw);
   const int tile = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t begin = tile_start[tile];
@@ -200,6 +246,8 @@ __global__ void __launch_bounds__(kThreads, 4) uplift_tile_kernel(
     if (lane == 0) sm.warp_nreg[warp] = __popc(leaders);
   }
   for (int k = tid; k < kMaxSlots * kWin; k += kThreads) (&sm.part[0][0])[k] = 0.0f;
+  if constexpr (kComp)
+    for (int k = tid; k < kMaxSlots * kWin; k += kThreads) (&sm.part_c[0][0])[k] = 0.0f;
   for (int b = tid; b < kNB; b += kThreads) sm.bcur[b] = 0u;
   if (tid < 4) sm.cnt[tid] = 0ull;
   __syncthreads();
@@ -433,13 +481,14 @@ __global__ void __launch_bounds__(kThreads, 4) uplift_tile_kernel(
             int jq = idx[0];
 #pragma unroll
             for (int u = 1; u < kGroup; ++u) jq = (lane >> 2) == u ? idx[u] : jq;
-            if ((lane & 3) == 0 && S > 0.0f) atomicAdd(&sm.part[wslot][j0 + jq], S);
+            if ((lane & 3) == 0 && S > 0.0f)
+              part_add<kComp>(sm.part[wslot], sm.part_c[kComp ? wslot : 0], j0 + jq, S);
           } else if (has) {
 #pragma unroll
             for (int u = 0; u < kGroup; ++u) {
               if (!(e[u] > 0.0f)) continue;
               if (my_slot >= 0) {
-                atomicAdd(&sm.part[my_slot][j0 + idx[u]], e[u]);
+                part_add<kComp>(sm.part[my_slot], sm.part_c[kComp ? my_slot : 0], j0 + idx[u], e[u]);
               } else if (region >= 0) {
                 // more regions in this tile than slots: scatter this pixel directly
                 const int64_t g = st_g[idx[u]];
@@ -447,7 +496,7 @@ __global__ void __launch_bounds__(kThreads, 4) uplift_tile_kernel(
                   const int64_t row = (int64_t)region * s + a;
                   const int jj = code_idx[row];
                   if (jj >= 0 && jj < C) {
-                    atomicAdd(&accum[g * C + jj], code_val[row] * e[u]);
+                    acc_add<kComp>(accum, comp, g * C + jj, code_val[row], e[u], 0.0f);
                     ++n_atom;
                   }
                 }
@@ -467,12 +516,14 @@ __global__ void __launch_bounds__(kThreads, 4) uplift_tile_kernel(
       for (int q = 0; q < nslots; ++q) {
         const float v = sm.part[q][p];
         if (v > 0.0f) {
+          const float vc = kComp ? sm.part_c[kComp ? q : 0][kComp ? p : 0] : 0.0f;
           for (int a = 0; a < s; ++a) {
             const int jj = sm.slot_idx[q][a];
-            if (jj >= 0) { atomicAdd(&accum[g * C + jj], sm.slot_val[q][a] * v); ++n_atom; }
+            if (jj >= 0) { acc_add<kComp>(accum, comp, g * C + jj, sm.slot_val[q][a], v, vc); ++n_atom; }
           }
           ++n_flush;
           sm.part[q][p] = 0.0f;
+          if constexpr (kComp) sm.part_c[q][p] = 0.0f;
         }
       }
     }
@@ -514,20 +565,30 @@ __global__ void __launch_bounds__(kThreads, 4) uplift_tile_kernel(
 
 }  // namespace
 
-cudaError_t launch_uplift_tiles(const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* rmap,
-                                int32_t R_total, const int32_t* code_idx, const float* code_val,
-                                int s, int C, float* accum, cudaStream_t st) {
+template <bool kComp>
+cudaError_t launch_tiles_t(const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* rmap,
+                           int32_t R_total, const int32_t* code_idx, const float* code_val, int s, int C,
+                           float* accum, float* comp, cudaStream_t st) {
   const int ntiles = cam.gx * cam.gy;
-  if (ntiles <= 0) return cudaSuccess;
-  const size_t smem = sizeof(TileSmem);
-  static_assert(sizeof(TileSmem) <= 55 * 1024, "4 CTAs per SM");
-  cudaError_t err = cudaFuncSetAttribute(uplift_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const size_t smem = sizeof(TileSmem<kComp>);
+  cudaError_t err = cudaFuncSetAttribute(uplift_tile_kernel<kComp>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
   if (err != cudaSuccess) return err;
-  uplift_tile_kernel<<<ntiles, kThreads, smem, st>>>(cam, ws.proj, ws.keys, ws.tile_start, slot, rmap,
-                                                     R_total, code_idx, code_val, s, C, accum, ws.hdr);
+  uplift_tile_kernel<kComp><<<ntiles, kThreads, smem, st>>>(cam, ws.proj, ws.keys, ws.tile_start, slot, rmap,
+                                                            R_total, code_idx, code_val, s, C, accum, comp,
+                                                            ws.hdr);
   g_launches += 1;
   return cudaGetLastError();
+}
+
+cudaError_t launch_uplift_tiles(const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* rmap,
+                                int32_t R_total, const int32_t* code_idx, const float* code_val,
+                                int s, int C, float* accum, float* comp, cudaStream_t st) {
+  static_assert(sizeof(TileSmem<false>) <= 55 * 1024, "4 CTAs per SM");
+  static_assert(sizeof(TileSmem<true>) <= 74 * 1024, "3 CTAs per SM");
+  if (cam.gx * cam.gy <= 0) return cudaSuccess;
+  if (comp) return launch_tiles_t<true>(cam, ws, slot, rmap, R_total, code_idx, code_val, s, C, accum, comp, st);
+  return launch_tiles_t<false>(cam, ws, slot, rmap, R_total, code_idx, code_val, s, C, accum, nullptr, st);
 }
 
 }  // namespace scoup

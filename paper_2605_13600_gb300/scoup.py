@@ -13,7 +13,7 @@ from typing import Optional, Sequence
 import numpy as np
 
 from . import _lib
-from ._lib import Camera, Scene, ScoupError, Stats, check, load
+from ._lib import SCOUP_ACCUM_COMPENSATED, SCOUP_ACCUM_CONTINUE, Camera, Scene, ScoupError, Stats, check, load
 
 
 def _ptr(t) -> Optional[int]:
@@ -86,8 +86,13 @@ def scoup_uplift_plan(scene: Scene, cams: Sequence, workspace, stream=None) -> i
 def scoup_uplift(scene: Scene, cams: Sequence, region_maps, map_offsets, R_total: int, code_idx,
                  code_val, s: int, C: int, K: int, accum, accum_mode: int, topk_idx, topk_val,
                  workspace, stats: bool = True, stream=None):
-    """Returns the stats dict (synchronising) when stats=True, else None."""
+    """Returns the stats dict (synchronising) when stats=True, else None.
+
+    With SCOUP_ACCUM_COMPENSATED in accum_mode, accum holds 2 * n * C floats
+    (the sums, then their compensation terms)."""
     import torch
+    if accum is not None and accum.numel() < scene.n * C * (2 if accum_mode & SCOUP_ACCUM_COMPENSATED else 1):
+        raise ValueError("accum is too small for n x C (x 2 when compensated)")
     _need(region_maps, torch.int32, "region_maps")
     _need(code_idx, torch.int32, "code_idx")
     _need(code_val, torch.float32, "code_val")
@@ -282,6 +287,36 @@ def scoup_similarity(features, text, out, feat_norm2=None, workspace=None, strea
     return workspace
 
 
+def scoup_decode_fp32(codes, codebook, features, stream=None) -> None:
+    """FP32 SIMT comparison form of scoup_decode: features [P, D] = codes [P, C] @ codebook [C, D]."""
+    import torch
+    for t, nm in ((codes, "codes"), (codebook, "codebook"), (features, "features")):
+        _need(t, torch.float32, nm)
+    P, C = codes.shape
+    D = codebook.shape[1]
+    if codebook.shape[0] != C or tuple(features.shape) != (P, D):
+        raise ValueError("shape mismatch")
+    check(load().scoup_decode_fp32(_ptr(codes), P, C, _ptr(codebook), D, _ptr(features), _stream(stream)))
+
+
+def scoup_similarity_fp32(features, text, out, workspace=None, stream=None):
+    """FP32 SIMT comparison form of scoup_similarity (float32 features)."""
+    import torch
+    for t, nm in ((features, "features"), (text, "text"), (out, "out")):
+        _need(t, torch.float32, nm)
+    P, D = features.shape
+    Q = text.shape[0]
+    if text.shape[1] != D or tuple(out.shape) != (P, Q):
+        raise ValueError("shape mismatch")
+    if workspace is None:
+        workspace = torch.empty(scoup_similarity_workspace_size(P, D, Q), dtype=torch.uint8,
+                                device=features.device)
+    _need(workspace, torch.uint8, "workspace")
+    check(load().scoup_similarity_fp32(_ptr(features), P, D, _ptr(text), Q, _ptr(out), _ptr(workspace),
+                                       workspace.numel(), _stream(stream)))
+    return workspace
+
+
 def scoup_read_stats(workspace, stream=None) -> dict:
     st = Stats()
     check(load().scoup_read_stats(_ptr(workspace), workspace.numel(), ct.byref(st), _stream(stream)))
@@ -314,7 +349,7 @@ class Uplift:
     """
 
     def __init__(self, wl, device: str = "cuda", dup_capacity: Optional[int] = None,
-                 headroom: float = 1.0):
+                 headroom: float = 1.0, compensated: bool = False):
         import torch
         dev = torch.device(device)
         sc = wl.scene
@@ -343,22 +378,32 @@ class Uplift:
         self.dup_capacity = dup_capacity
         self.workspace = torch.empty(scoup_uplift_workspace_size(n, maxw, maxh, dup_capacity) + extra,
                                      dtype=torch.uint8, device=dev)
-        self.accum = torch.empty((n, self.C), dtype=torch.float32, device=dev)
+        self.compensated = bool(compensated)
+        self.accum = torch.empty(((2, n, self.C) if compensated else (n, self.C)), dtype=torch.float32,
+                                 device=dev)
         self.topk_idx = torch.empty((n, self.K), dtype=torch.int32, device=dev)
         self.topk_val = torch.empty((n, self.K), dtype=torch.float32, device=dev)
 
     def run(self, stats: bool = True, accum_mode: int = 0, views=None, stream=None):
         cams = self.cams if views is None else [self.cams[v] for v in views]
         offs = self.map_offsets if views is None else self.map_offsets[list(views)]
+        if self.compensated:
+            accum_mode |= SCOUP_ACCUM_COMPENSATED
         return scoup_uplift(self.scene, cams, self.region_maps, offs, self.R_total, self.code_idx,
                             self.code_val, self.s, self.C, self.K, self.accum, accum_mode,
                             self.topk_idx, self.topk_val, self.workspace, stats=stats, stream=stream)
 
+    def accum_value(self):
+        """The accumulator [n, C] (sum + compensation in the compensated form)."""
+        if self.compensated:
+            return self.accum[0].double() + self.accum[1].double()
+        return self.accum
 
-__all__ = ["ScoupError", "scene_struct", "camera_array", "scoup_version",
+
+__all__ = ["ScoupError", "SCOUP_ACCUM_CONTINUE", "SCOUP_ACCUM_COMPENSATED", "scene_struct", "camera_array", "scoup_version",
            "scoup_uplift_workspace_size", "scoup_uplift_plan", "scoup_uplift", "scoup_topk",
            "scoup_read_stats", "scoup_uplift_noalloc", "scoup_uplift_noalloc_max_bytes",
            "scoup_profile_enable", "scoup_profile_read", "scoup_launch_count",
            "scoup_render", "scoup_render_backward", "Render", "Uplift",
            "scoup_decode_workspace_size", "scoup_decode", "scoup_similarity_workspace_size",
-           "scoup_similarity"]
+           "scoup_similarity", "scoup_decode_fp32", "scoup_similarity_fp32"]

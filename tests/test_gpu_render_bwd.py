@@ -66,7 +66,7 @@ def test_autograd_function(gb, oracle_lib):
     rng = np.random.default_rng(1)
     cb = torch.as_tensor(rng.normal(size=(24, 10)).astype(np.float32), device="cuda")
     target = torch.as_tensor(rng.normal(size=(40, 48, 10)).astype(np.float32), device="cuda")
-    _, _, risk, _ = oracle_lib.render(scene, idx, val.astype(np.float64), 24, cam)
+    Wo, _, risk, _ = oracle_lib.render(scene, idx, val.astype(np.float64), 24, cam)
     keep = torch.as_tensor(~risk, device="cuda").float()[..., None]
     r = gb.Render(scene, idx, val, 24, [cam])
     op = torch.as_tensor(scene.opacity, device="cuda").clone().requires_grad_(True)
@@ -74,7 +74,10 @@ def test_autograd_function(gb, oracle_lib):
     W = SparseRender.apply(op, tv, r, 0)
     loss = (keep * (W @ cb - target) ** 2).sum()
     loss.backward()
-    g = (keep * 2.0 * (W.detach() @ cb - target) @ cb.T).cpu().numpy().astype(np.float64)
+    # the oracle's gradient input comes from its own forward render, in FP64
+    cb64 = cb.cpu().numpy().astype(np.float64)
+    keep64 = (~risk).astype(np.float64)[..., None]
+    g = keep64 * 2.0 * (Wo @ cb64 - target.cpu().numpy().astype(np.float64)) @ cb64.T
     dv_o, do_o = oracle_lib.render_backward(scene, idx, val.astype(np.float64), 24, cam, g)
     _compare(tv.grad.cpu().numpy(), dv_o, "d_val")
     _compare(op.grad.cpu().numpy(), do_o, "d_opacity")
