@@ -184,6 +184,90 @@ int scoup_render_backward(const scoup_scene* scene, const int32_t* topk_idx, con
                           scoup_stats* stats, void* stream);
 
 /* ------------------------------------------------------------------ */
+/* Batched uplift: many scenes with their own views, one graph launch   */
+/* ------------------------------------------------------------------ */
+
+/* The paper uplifts one scene at a time; batching is this library's form
+ * for workloads of many scenes with uneven sizes.  Each item is the
+ * argument set of one scoup_uplift call (same meaning and layout); C, K and
+ * accum_mode are common to the batch. */
+typedef struct scoup_batch_item {
+  scoup_scene scene;
+  const scoup_camera* cams;     /* HOST [V]; read when the batch is captured */
+  int32_t V;
+  const int32_t* region_maps;   /* DEVICE, views packed as for scoup_uplift */
+  const int64_t* map_offsets;   /* HOST [V] */
+  int32_t R_total;
+  const int32_t* code_idx;      /* DEVICE [R_total, s] */
+  const float* code_val;        /* DEVICE [R_total, s] */
+  int32_t s;
+  float* accum;                 /* DEVICE [n, C] ([2, n, C] when compensated) */
+  int32_t* topk_idx;            /* DEVICE [n, K] or NULL */
+  float* topk_val;              /* DEVICE [n, K] or NULL */
+} scoup_batch_item;
+
+typedef struct scoup_plan scoup_plan;  /* opaque */
+
+typedef struct scoup_tune_entry {
+  int32_t lanes;
+  int32_t warp_w;
+  float ms;  /* best of two timed runs on the view sample */
+} scoup_tune_entry;
+
+#define SCOUP_MAX_TUNE 16
+typedef struct scoup_plan_info {
+  int32_t lanes;            /* scenes run concurrently on this many streams */
+  int32_t warp_w;           /* tile-kernel warp pixel block: warp_w x (32 / warp_w) */
+  int32_t tuned;            /* 1 once scoup_autotune has chosen lanes and warp_w */
+  int32_t graph_kernels;    /* kernel launches in one replay of the captured graph (0 before) */
+  int64_t workspace_bytes;  /* device memory held by the lane workspaces */
+  int32_t n_tune;
+  scoup_tune_entry tune[SCOUP_MAX_TUNE];  /* the autotuner's measurements */
+} scoup_plan_info;
+
+#define SCOUP_BATCH_EAGER 1  /* scoup_uplift_batched flag: launch directly, no graph */
+
+/* Creates a plan for the batch: counts every view's (Gaussian, tile) pairs
+ * exactly (synchronising `stream`), sizes one uplift workspace for the
+ * largest scene and allocates it for each lane (default lanes: min(4, B),
+ * warp block 8x4).  The plan keeps a copy of `items` (the arrays they point
+ * to must stay valid and unchanged in size while the plan lives).  The plan
+ * owns its device memory until scoup_plan_destroy. */
+int scoup_plan_create(const scoup_batch_item* items, int32_t B, int32_t C, int32_t K, int32_t accum_mode,
+                      scoup_plan** plan, void* stream);
+
+/* Sets the lane count (1..8) and the tile-kernel warp block width (4, 8 or
+ * 16) by hand; drops a captured graph. */
+int scoup_plan_set(scoup_plan* plan, int32_t lanes, int32_t warp_w);
+
+/* Autotuner: runs the batch restricted to `sample_views` evenly spaced views
+ * per scene for every lanes in {1, 2, 4, 8} (<= B) and warp block in
+ * {8x4, 16x2, 4x8}, times each (CUDA events on `stream`, best of two after a
+ * warm-up) and keeps the fastest (scoup_plan_info_get lists the timings).
+ * Overwrites the items' accum and Top-K outputs; refused with
+ * SCOUP_ACCUM_CONTINUE.  Synchronises `stream`. */
+int scoup_autotune(scoup_plan* plan, int32_t sample_views, void* stream);
+
+/* Uplifts every scene of the batch (results as scoup_uplift per item).  The
+ * first call captures the whole batch -- fork to the lanes, every launch of
+ * every scene, a copy of each scene's counters, join -- into a CUDA graph on
+ * `stream` (the stream must not be capturing already); later calls replay
+ * it with one graph launch.  Camera parameters and map offsets are read
+ * when the graph is captured.  With SCOUP_BATCH_EAGER the launches are
+ * issued directly (same lanes, no graph).  Asynchronous; do not run the same
+ * plan on two streams at once (the lanes' workspaces are shared). */
+int scoup_uplift_batched(scoup_plan* plan, int32_t flags, void* stream);
+
+/* Per-scene counters of the last batched run (HOST stats[B]); synchronises
+ * `stream` and returns the first device-side error of any scene. */
+int scoup_plan_stats(scoup_plan* plan, scoup_stats* stats, void* stream);
+
+int scoup_plan_info_get(const scoup_plan* plan, scoup_plan_info* info);
+
+/* Frees the plan's device memory, streams and graph (NULL is accepted). */
+int scoup_plan_destroy(scoup_plan* plan);
+
+/* ------------------------------------------------------------------ */
 /* Codebook decode and text similarity (tensor cores, BF16 inputs)      */
 /* ------------------------------------------------------------------ */
 

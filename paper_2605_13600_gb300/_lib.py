@@ -51,6 +51,27 @@ class Stats(ct.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
+class BatchItem(ct.Structure):
+    _fields_ = [("scene", Scene), ("cams", ct.c_void_p), ("V", ct.c_int32), ("region_maps", ct.c_void_p),
+                ("map_offsets", ct.c_void_p), ("R_total", ct.c_int32), ("code_idx", ct.c_void_p),
+                ("code_val", ct.c_void_p), ("s", ct.c_int32), ("accum", ct.c_void_p),
+                ("topk_idx", ct.c_void_p), ("topk_val", ct.c_void_p)]
+
+
+class TuneEntry(ct.Structure):
+    _fields_ = [("lanes", ct.c_int32), ("warp_w", ct.c_int32), ("ms", ct.c_float)]
+
+
+SCOUP_MAX_TUNE = 16
+SCOUP_BATCH_EAGER = 1
+
+
+class PlanInfo(ct.Structure):
+    _fields_ = [("lanes", ct.c_int32), ("warp_w", ct.c_int32), ("tuned", ct.c_int32),
+                ("graph_kernels", ct.c_int32), ("workspace_bytes", ct.c_int64), ("n_tune", ct.c_int32),
+                ("tune", TuneEntry * SCOUP_MAX_TUNE)]
+
+
 _lib = None
 
 P = ct.c_void_p
@@ -81,6 +102,13 @@ PROTOS = {
     "scoup_uplift_noalloc_max_bytes": (SZ, []),
     "scoup_uplift_noalloc": (ct.c_int, [ct.POINTER(Scene), P, I32, P, P, I32, P, P, I32, I32, I32, P, I32,
                                         P, P, ct.POINTER(Stats), P]),
+    "scoup_plan_create": (ct.c_int, [P, I32, I32, I32, I32, ct.POINTER(ct.c_void_p), P]),
+    "scoup_plan_set": (ct.c_int, [P, I32, I32]),
+    "scoup_autotune": (ct.c_int, [P, I32, P]),
+    "scoup_uplift_batched": (ct.c_int, [P, I32, P]),
+    "scoup_plan_stats": (ct.c_int, [P, P, P]),
+    "scoup_plan_info_get": (ct.c_int, [P, ct.POINTER(PlanInfo)]),
+    "scoup_plan_destroy": (ct.c_int, [P]),
     "scoup_profile_enable": (ct.c_int, [I32]),
     "scoup_profile_read": (ct.c_int, [P, P, I32]),
     "scoup_launch_count": (I64, []),

@@ -46,6 +46,8 @@ struct PhaseScope {
   cudaEvent_t a = nullptr;
   PhaseScope(int ph, cudaStream_t s) : phase(ph), st(s) {
     if (!g_prof_on) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     a = prof_event();
     cudaEventRecord(a, st);
@@ -199,6 +201,118 @@ int finish_with_stats(const WsHeader* dev_hdr, scoup_stats* stats, cudaStream_t 
 
 namespace scoup {
 int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
+int uplift_call(const UpliftCall& c, void* workspace, size_t ws_bytes, int warp_w, const WsHeader** hdr_out,
+                cudaStream_t st) {
+  const scoup_scene* scene = c.scene;
+  const scoup_camera* cams = c.cams;
+  const int32_t V = c.V, R_total = c.R_total, s = c.s, C = c.C, K = c.K, accum_mode = c.accum_mode;
+  const int32_t* region_maps = c.region_maps;
+  const int64_t* map_offsets = c.map_offsets;
+  const int32_t* code_idx = c.code_idx;
+  const float* code_val = c.code_val;
+  float* accum = c.accum;
+  int32_t* topk_idx = c.topk_idx;
+  float* topk_val = c.topk_val;
+  int rc = check_scene(scene);
+  if (rc) return rc;
+  int max_tiles = 1;
+  if ((rc = check_cams(cams, V, &max_tiles))) return rc;
+  if (C < 1 || C > 1024) return fail(SCOUP_ERR_INVALID_ARG, "C=%d outside [1, 1024]", C);
+  if (K < 1 || K > C) return fail(SCOUP_ERR_INVALID_ARG, "K=%d outside [1, C=%d]", K, C);
+  if (s < 1 || s > 64) return fail(SCOUP_ERR_INVALID_ARG, "s=%d outside [1, 64]", s);
+  if (R_total < 0) return fail(SCOUP_ERR_INVALID_ARG, "R_total=%d < 0", R_total);
+  if (accum_mode & ~(SCOUP_ACCUM_CONTINUE | SCOUP_ACCUM_COMPENSATED))
+    return fail(SCOUP_ERR_INVALID_ARG, "accum_mode=%d: only SCOUP_ACCUM_CONTINUE and SCOUP_ACCUM_COMPENSATED", accum_mode);
+  if (scene->n > 0 && !accum) return fail(SCOUP_ERR_INVALID_ARG, "accum is NULL");
+  if ((topk_idx == nullptr) != (topk_val == nullptr))
+    return fail(SCOUP_ERR_INVALID_ARG, "topk_idx and topk_val must both be given or both be NULL");
+  if (V > 0 && (!region_maps || !map_offsets)) return fail(SCOUP_ERR_INVALID_ARG, "region maps are NULL");
+  if (V > 0 && R_total > 0 && (!code_idx || !code_val)) return fail(SCOUP_ERR_INVALID_ARG, "code table is NULL");
+  for (int v = 0; v < V; ++v)
+    if (map_offsets[v] < 0) return fail(SCOUP_ERR_INVALID_ARG, "map_offsets[%d] < 0", v);
+  if (!workspace) return fail(SCOUP_ERR_INVALID_ARG, "workspace is NULL");
+  const int64_t code_rows_k = s > K ? (int64_t)R_total * K : 0;
+  const size_t fixed = uplift_fixed_bytes(scene->n, max_tiles, code_rows_k);
+  if (ws_bytes < fixed)
+    return fail(SCOUP_ERR_OOM, "workspace too small: %zu < %zu bytes before tile lists", ws_bytes, fixed);
+
+  int32_t* fci = nullptr;
+  float* fcv = nullptr;
+  UpliftWs ws = carve(workspace, ws_bytes, scene->n, max_tiles, code_rows_k, &fci, &fcv);
+  const int64_t n = scene->n;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(ws.hdr, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
+  const bool compensated = (accum_mode & SCOUP_ACCUM_COMPENSATED) != 0;
+  float* comp = compensated ? accum + (size_t)n * (size_t)C : nullptr;
+  if (n > 0 && !(accum_mode & SCOUP_ACCUM_CONTINUE) &&
+      (e = cudaMemsetAsync(accum, 0, sizeof(float) * (size_t)n * (size_t)C * (compensated ? 2 : 1), st)) !=
+          cudaSuccess)
+    return cuda_fail(e, "memset accum");
+  if ((e = cudaMemsetAsync(ws.tile_count, 0, sizeof(uint32_t) * ((size_t)max_tiles + 1), st)) != cudaSuccess)
+    return cuda_fail(e, "memset");
+  const int32_t* ci = code_idx;
+  const float* cv = code_val;
+  int s_eff = s;
+  if (s > K && R_total > 0) {
+    PhaseScope ps(SCOUP_PHASE_CODE_TOPK, st);
+    if ((e = launch_code_topk(code_idx, code_val, R_total, s, K, fci, fcv, st)) != cudaSuccess)
+      return cuda_fail(e, "code top-k");
+    ci = fci;
+    cv = fcv;
+    s_eff = K;
+  }
+  if (n > 0 && V > 0) {
+    {
+      PhaseScope ps(SCOUP_PHASE_TAU, st);
+      if ((e = launch_reorder(*scene, ws, st)) != cudaSuccess) return cuda_fail(e, "reorder");
+    }
+    for (int v = 0; v < V; ++v) {
+      const CamArgs ca = cam_args(cams[v]);
+      {
+        PhaseScope ps(SCOUP_PHASE_PREPROCESS, st);
+        if ((e = launch_preprocess(*scene, ca, ws, v & 1, st)) != cudaSuccess) return cuda_fail(e, "preprocess");
+      }
+      {
+        PhaseScope ps(SCOUP_PHASE_BINNING, st);
+        if ((e = launch_binning(ca, n, ws, v & 1, st)) != cudaSuccess) return cuda_fail(e, "binning");
+      }
+      {
+        PhaseScope ps(SCOUP_PHASE_UPLIFT_TILES, st);
+        if ((e = launch_uplift_tiles(ca, ws, v & 1, region_maps + map_offsets[v], R_total, ci, cv, s_eff,
+                                     C, accum, comp, warp_w, st)) != cudaSuccess)
+          return cuda_fail(e, "uplift tiles");
+      }
+    }
+  }
+  if (topk_idx && n > 0) {
+    PhaseScope ps(SCOUP_PHASE_TOPK, st);
+    if ((e = launch_topk(accum, comp, n, C, K, topk_idx, topk_val, st)) != cudaSuccess)
+      return cuda_fail(e, "top-k");
+  }
+  if (hdr_out) *hdr_out = ws.hdr;
+  return SCOUP_OK;
+}
+
+size_t uplift_required_bytes(int64_t n, const scoup_camera* cams, int32_t V, int32_t s, int32_t K, int32_t R_total,
+                             int64_t dup_capacity) {
+  int max_tiles = 1;
+  for (int v = 0; v < V; ++v) {
+    const int t = tiles_of(cams[v].width, cams[v].height);
+    if (t > max_tiles) max_tiles = t;
+  }
+  const int64_t code_rows_k = s > K ? (int64_t)R_total * K : 0;
+  return uplift_fixed_bytes(n, max_tiles, code_rows_k) + sizeof(unsigned long long) * (size_t)dup_capacity;
+}
+
+int uplift_stats(const WsHeader* dev_hdr, scoup_stats* stats, cudaStream_t st) {
+  return finish_with_stats(dev_hdr, stats, st);
+}
+
+void header_stats(const WsHeader& h, scoup_stats* stats) { read_header(h, stats); }
+
+
+
 }  // namespace scoup
 
 using namespace scoup;
@@ -255,84 +369,13 @@ int scoup_uplift(const scoup_scene* scene, const scoup_camera* cams, int32_t V,
                  const int32_t* code_idx, const float* code_val, int32_t s, int32_t C, int32_t K,
                  float* accum, int32_t accum_mode, int32_t* topk_idx, float* topk_val,
                  void* workspace, size_t ws_bytes, scoup_stats* stats, void* stream) {
-  int rc = check_scene(scene);
-  if (rc) return rc;
-  int max_tiles = 1;
-  if ((rc = check_cams(cams, V, &max_tiles))) return rc;
-  if (C < 1 || C > 1024) return fail(SCOUP_ERR_INVALID_ARG, "C=%d outside [1, 1024]", C);
-  if (K < 1 || K > C) return fail(SCOUP_ERR_INVALID_ARG, "K=%d outside [1, C=%d]", K, C);
-  if (s < 1 || s > 64) return fail(SCOUP_ERR_INVALID_ARG, "s=%d outside [1, 64]", s);
-  if (R_total < 0) return fail(SCOUP_ERR_INVALID_ARG, "R_total=%d < 0", R_total);
-  if (accum_mode & ~(SCOUP_ACCUM_CONTINUE | SCOUP_ACCUM_COMPENSATED))
-    return fail(SCOUP_ERR_INVALID_ARG, "accum_mode=%d: only SCOUP_ACCUM_CONTINUE and SCOUP_ACCUM_COMPENSATED", accum_mode);
-  if (scene->n > 0 && !accum) return fail(SCOUP_ERR_INVALID_ARG, "accum is NULL");
-  if ((topk_idx == nullptr) != (topk_val == nullptr))
-    return fail(SCOUP_ERR_INVALID_ARG, "topk_idx and topk_val must both be given or both be NULL");
-  if (V > 0 && (!region_maps || !map_offsets)) return fail(SCOUP_ERR_INVALID_ARG, "region maps are NULL");
-  if (V > 0 && R_total > 0 && (!code_idx || !code_val)) return fail(SCOUP_ERR_INVALID_ARG, "code table is NULL");
-  for (int v = 0; v < V; ++v)
-    if (map_offsets[v] < 0) return fail(SCOUP_ERR_INVALID_ARG, "map_offsets[%d] < 0", v);
-  if (!workspace) return fail(SCOUP_ERR_INVALID_ARG, "workspace is NULL");
-  const int64_t code_rows_k = s > K ? (int64_t)R_total * K : 0;
-  const size_t fixed = uplift_fixed_bytes(scene->n, max_tiles, code_rows_k);
-  if (ws_bytes < fixed)
-    return fail(SCOUP_ERR_OOM, "workspace too small: %zu < %zu bytes before tile lists", ws_bytes, fixed);
-
-  cudaStream_t st = (cudaStream_t)stream;
-  int32_t* fci = nullptr;
-  float* fcv = nullptr;
-  UpliftWs ws = carve(workspace, ws_bytes, scene->n, max_tiles, code_rows_k, &fci, &fcv);
-  const int64_t n = scene->n;
-  cudaError_t e;
-  if ((e = cudaMemsetAsync(ws.hdr, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
-  const bool compensated = (accum_mode & SCOUP_ACCUM_COMPENSATED) != 0;
-  float* comp = compensated ? accum + (size_t)n * (size_t)C : nullptr;
-  if (n > 0 && !(accum_mode & SCOUP_ACCUM_CONTINUE) &&
-      (e = cudaMemsetAsync(accum, 0, sizeof(float) * (size_t)n * (size_t)C * (compensated ? 2 : 1), st)) !=
-          cudaSuccess)
-    return cuda_fail(e, "memset accum");
-  if ((e = cudaMemsetAsync(ws.tile_count, 0, sizeof(uint32_t) * ((size_t)max_tiles + 1), st)) != cudaSuccess)
-    return cuda_fail(e, "memset");
-  const int32_t* ci = code_idx;
-  const float* cv = code_val;
-  int s_eff = s;
-  if (s > K && R_total > 0) {
-    PhaseScope ps(SCOUP_PHASE_CODE_TOPK, st);
-    if ((e = launch_code_topk(code_idx, code_val, R_total, s, K, fci, fcv, st)) != cudaSuccess)
-      return cuda_fail(e, "code top-k");
-    ci = fci;
-    cv = fcv;
-    s_eff = K;
-  }
-  if (n > 0 && V > 0) {
-    {
-      PhaseScope ps(SCOUP_PHASE_TAU, st);
-      if ((e = launch_reorder(*scene, ws, st)) != cudaSuccess) return cuda_fail(e, "reorder");
-    }
-    for (int v = 0; v < V; ++v) {
-      const CamArgs ca = cam_args(cams[v]);
-      {
-        PhaseScope ps(SCOUP_PHASE_PREPROCESS, st);
-        if ((e = launch_preprocess(*scene, ca, ws, v & 1, st)) != cudaSuccess) return cuda_fail(e, "preprocess");
-      }
-      {
-        PhaseScope ps(SCOUP_PHASE_BINNING, st);
-        if ((e = launch_binning(ca, n, ws, v & 1, st)) != cudaSuccess) return cuda_fail(e, "binning");
-      }
-      {
-        PhaseScope ps(SCOUP_PHASE_UPLIFT_TILES, st);
-        if ((e = launch_uplift_tiles(ca, ws, v & 1, region_maps + map_offsets[v], R_total, ci, cv, s_eff,
-                                     C, accum, comp, st)) != cudaSuccess)
-          return cuda_fail(e, "uplift tiles");
-      }
-    }
-  }
-  if (topk_idx && n > 0) {
-    PhaseScope ps(SCOUP_PHASE_TOPK, st);
-    if ((e = launch_topk(accum, comp, n, C, K, topk_idx, topk_val, st)) != cudaSuccess)
-      return cuda_fail(e, "top-k");
-  }
-  if (stats) return finish_with_stats(ws.hdr, stats, st);
+  const UpliftCall c{scene, cams, V, region_maps, map_offsets, R_total, code_idx, code_val, s, C, K,
+                     accum, accum_mode, topk_idx, topk_val};
+  const WsHeader* hdr = nullptr;
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int rc = uplift_call(c, workspace, ws_bytes, 8, &hdr, st);
+  if (rc != SCOUP_OK) return rc;
+  if (stats) return finish_with_stats(hdr, stats, st);
   return SCOUP_OK;
 }
 

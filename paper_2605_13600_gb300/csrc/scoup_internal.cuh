@@ -117,6 +117,33 @@ struct UpliftWs {
 // Records msg as the calling thread's last error and returns code.
 int set_error(int code, const char* msg);
 
+// Arguments of one uplift call (the scoup_uplift parameters).
+struct UpliftCall {
+  const scoup_scene* scene;
+  const scoup_camera* cams;
+  int32_t V;
+  const int32_t* region_maps;
+  const int64_t* map_offsets;
+  int32_t R_total;
+  const int32_t* code_idx;
+  const float* code_val;
+  int32_t s, C, K;
+  float* accum;
+  int32_t accum_mode;
+  int32_t* topk_idx;
+  float* topk_val;
+};
+
+// Validates and enqueues one uplift on `st` without synchronising; warp_w is
+// the tile kernel's warp pixel-block width (8, 16 or 4).  *hdr_out receives
+// the workspace header that holds the call's status and counters.
+int uplift_call(const UpliftCall& c, void* workspace, size_t ws_bytes, int warp_w, const struct WsHeader** hdr_out,
+                cudaStream_t st);
+size_t uplift_required_bytes(int64_t n, const scoup_camera* cams, int32_t V, int32_t s, int32_t K, int32_t R_total,
+                             int64_t dup_capacity);
+int uplift_stats(const struct WsHeader* dev_hdr, scoup_stats* stats, cudaStream_t st);
+void header_stats(const struct WsHeader& h, scoup_stats* stats);
+
 // Launchers (each defined in its own translation unit).
 size_t reorder_scratch_bytes();
 cudaError_t launch_reorder(const scoup_scene& sc, const UpliftWs& ws, cudaStream_t st);
@@ -126,7 +153,7 @@ cudaError_t launch_binning(const CamArgs& cam, int64_t n, const UpliftWs& ws, in
                            cudaStream_t st);
 cudaError_t launch_uplift_tiles(const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* rmap,
                                 int32_t R_total, const int32_t* code_idx, const float* code_val,
-                                int s, int C, float* accum, float* comp, cudaStream_t st);
+                                int s, int C, float* accum, float* comp, int warp_w, cudaStream_t st);
 size_t render_smem_bytes(int C);
 cudaError_t launch_render_tiles(const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* topk_idx,
                                 const float* topk_val, int K, int C, float* out, float* out_T,

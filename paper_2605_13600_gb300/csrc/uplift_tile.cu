@@ -1,7 +1,11 @@
 // uplift_tile.cu -- per-tile front-to-back compositing and sparse scatter
 // (paper Sec. 3 Eq. 2; Sec. 4.2 Eq. 5; Algorithm 1).
 //
-// One CTA per 16x16 tile, one pixel per thread; each warp covers an 8x4 block.
+// One CTA per 16x16 tile, one pixel per thread; each warp covers a kBW x
+// (32 / kBW) pixel block (8x4 by default; 16x2 and 4x8 are the other shapes
+// the autotuner may pick).  The shape changes only which pixels share a warp
+// (and so the order of the FP32 sums): membership is always decided on the
+// 16x16 tile.
 //
 // Ordering.  The tile's key list (depth bits << 32 | Gaussian id, unordered)
 // is read twice: a histogram pass over kNB depth buckets (a monotone map of
@@ -203,7 +207,7 @@ __device__ __forceinline__ void acc_add(float* accum, float* comp, int64_t x, fl
   }
 }
 
-template <bool kComp>
+template <bool kComp, int kBW>
 __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
     CamArgs cam, const ProjRec* __restrict__ proj, const unsigned long long* __restrict__ keys,
     const uint32_t* __restrict__ tile_start, int slot, const int32_t* __restrict__ rmap,
@@ -229,9 +233,11 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
   }
 
   const int tx = tile % cam.gx, ty = tile / cam.gx;
-  const float bx0 = (float)(tx * kTile + (warp & 1) * 8), by0 = (float)(ty * kTile + (warp >> 1) * 4);
-  const int px = tx * kTile + (warp & 1) * 8 + (lane & 7);
-  const int py = ty * kTile + (warp >> 1) * 4 + (lane >> 3);
+  constexpr int kBH = 32 / kBW, kWarpsX = kTile / kBW;
+  const int bxi = tx * kTile + (warp % kWarpsX) * kBW, byi = ty * kTile + (warp / kWarpsX) * kBH;
+  const float bx0 = (float)bxi, by0 = (float)byi;
+  const int px = bxi + lane % kBW;
+  const int py = byi + lane / kBW;
   const bool inside = px < cam.width && py < cam.height;
   int region = inside ? rmap[(int64_t)py * cam.width + px] : -1;
   if (region >= R_total) { atomicOr(&hdr->status, kStatDeviceCheck); region = -1; }
@@ -439,7 +445,7 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
         st_a[lane] = pr.a;
         st_b[lane] = pr.b;
         st_g[lane] = g;
-        rel = box_may_hit(pr, bx0, by0, 8.0f, 4.0f);
+        rel = box_may_hit(pr, bx0, by0, (float)kBW, (float)kBH);
       }
       unsigned rmask = __ballot_sync(kFull, rel);
       __syncwarp();
@@ -565,30 +571,43 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
 
 }  // namespace
 
-template <bool kComp>
+template <bool kComp, int kBW>
 cudaError_t launch_tiles_t(const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* rmap,
                            int32_t R_total, const int32_t* code_idx, const float* code_val, int s, int C,
                            float* accum, float* comp, cudaStream_t st) {
   const int ntiles = cam.gx * cam.gy;
   const size_t smem = sizeof(TileSmem<kComp>);
-  cudaError_t err = cudaFuncSetAttribute(uplift_tile_kernel<kComp>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+  cudaError_t err = cudaFuncSetAttribute(uplift_tile_kernel<kComp, kBW>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  uplift_tile_kernel<kComp><<<ntiles, kThreads, smem, st>>>(cam, ws.proj, ws.keys, ws.tile_start, slot, rmap,
-                                                            R_total, code_idx, code_val, s, C, accum, comp,
-                                                            ws.hdr);
+  uplift_tile_kernel<kComp, kBW><<<ntiles, kThreads, smem, st>>>(cam, ws.proj, ws.keys, ws.tile_start, slot,
+                                                                 rmap, R_total, code_idx, code_val, s, C, accum,
+                                                                 comp, ws.hdr);
   g_launches += 1;
   return cudaGetLastError();
 }
 
+template <bool kComp>
+cudaError_t launch_tiles_shape(int warp_w, const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* rmap,
+                               int32_t R_total, const int32_t* code_idx, const float* code_val, int s, int C,
+                               float* accum, float* comp, cudaStream_t st) {
+  switch (warp_w) {
+    case 16: return launch_tiles_t<kComp, 16>(cam, ws, slot, rmap, R_total, code_idx, code_val, s, C, accum, comp, st);
+    case 4: return launch_tiles_t<kComp, 4>(cam, ws, slot, rmap, R_total, code_idx, code_val, s, C, accum, comp, st);
+    default: return launch_tiles_t<kComp, 8>(cam, ws, slot, rmap, R_total, code_idx, code_val, s, C, accum, comp, st);
+  }
+}
+
 cudaError_t launch_uplift_tiles(const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* rmap,
                                 int32_t R_total, const int32_t* code_idx, const float* code_val,
-                                int s, int C, float* accum, float* comp, cudaStream_t st) {
+                                int s, int C, float* accum, float* comp, int warp_w, cudaStream_t st) {
   static_assert(sizeof(TileSmem<false>) <= 55 * 1024, "4 CTAs per SM");
   static_assert(sizeof(TileSmem<true>) <= 74 * 1024, "3 CTAs per SM");
   if (cam.gx * cam.gy <= 0) return cudaSuccess;
-  if (comp) return launch_tiles_t<true>(cam, ws, slot, rmap, R_total, code_idx, code_val, s, C, accum, comp, st);
-  return launch_tiles_t<false>(cam, ws, slot, rmap, R_total, code_idx, code_val, s, C, accum, nullptr, st);
+  if (comp)
+    return launch_tiles_shape<true>(warp_w, cam, ws, slot, rmap, R_total, code_idx, code_val, s, C, accum, comp, st);
+  return launch_tiles_shape<false>(warp_w, cam, ws, slot, rmap, R_total, code_idx, code_val, s, C, accum, nullptr,
+                                   st);
 }
 
 }  // namespace scoup

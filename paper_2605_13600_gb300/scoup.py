@@ -13,7 +13,8 @@ from typing import Optional, Sequence
 import numpy as np
 
 from . import _lib
-from ._lib import SCOUP_ACCUM_COMPENSATED, SCOUP_ACCUM_CONTINUE, Camera, Scene, ScoupError, Stats, check, load
+from ._lib import (SCOUP_ACCUM_COMPENSATED, SCOUP_ACCUM_CONTINUE, SCOUP_BATCH_EAGER, BatchItem, Camera,
+                   PlanInfo, Scene, ScoupError, Stats, check, load)
 
 
 def _ptr(t) -> Optional[int]:
@@ -400,10 +401,105 @@ class Uplift:
         return self.accum
 
 
+class BatchedUplift:
+    """Many uplift workloads (scenes with their own views) run as one batch:
+    a plan with per-lane workspaces, an optional autotuning pass and a CUDA
+    graph replayed by ``run()``.  Every workload is copied to the GPU once;
+    ``accum[b]``, ``topk_idx[b]``, ``topk_val[b]`` hold scene b's outputs."""
+
+    def __init__(self, wls, device: str = "cuda", compensated: bool = False, stream=None):
+        import torch
+        dev = torch.device(device)
+        self.device = dev
+        self.wls = list(wls)
+        if not self.wls:
+            raise ValueError("empty batch")
+        self.C, self.K = int(self.wls[0].C), int(self.wls[0].K)
+        self.compensated = bool(compensated)
+        self._keep = []
+        self.accum, self.topk_idx, self.topk_val, self.scenes = [], [], [], []
+        items = (BatchItem * len(self.wls))()
+        for b, wl in enumerate(self.wls):
+            if int(wl.C) != self.C or int(wl.K) != self.K:
+                raise ValueError("C and K must be common to the batch")
+            sc = wl.scene
+            t = {k: torch.as_tensor(getattr(sc, k), device=dev).contiguous()
+                 for k in ("means", "scales", "quats", "opacity")}
+            sstruct = scene_struct(t["means"], t["scales"], t["quats"], t["opacity"])
+            rm = torch.as_tensor(wl.region_maps, device=dev).contiguous()
+            ci = torch.as_tensor(wl.code_idx, device=dev).contiguous()
+            cv = torch.as_tensor(wl.code_val, device=dev).contiguous()
+            cams = camera_array(wl.cams)
+            offs = np.ascontiguousarray(np.asarray(wl.map_offsets, np.int64)[:max(1, len(wl.cams))])
+            n = sc.n
+            acc = torch.empty(((2, n, self.C) if compensated else (n, self.C)), dtype=torch.float32, device=dev)
+            ti = torch.empty((n, self.K), dtype=torch.int32, device=dev)
+            tv = torch.empty((n, self.K), dtype=torch.float32, device=dev)
+            it = items[b]
+            it.scene = sstruct
+            it.cams = ct.cast(cams, ct.c_void_p)
+            it.V = len(wl.cams)
+            it.region_maps = _ptr(rm)
+            it.map_offsets = offs.ctypes.data_as(ct.c_void_p)
+            it.R_total = int(wl.code_idx.shape[0])
+            it.code_idx, it.code_val, it.s = _ptr(ci), _ptr(cv), int(wl.s)
+            it.accum, it.topk_idx, it.topk_val = _ptr(acc), _ptr(ti), _ptr(tv)
+            self._keep += [t, sstruct, rm, ci, cv, cams, offs]
+            self.accum.append(acc)
+            self.topk_idx.append(ti)
+            self.topk_val.append(tv)
+            self.scenes.append(sstruct)
+        self._items = items
+        self.plan = ct.c_void_p()
+        mode = SCOUP_ACCUM_COMPENSATED if compensated else 0
+        check(load().scoup_plan_create(ct.cast(items, ct.c_void_p), len(self.wls), self.C, self.K, mode,
+                                       ct.byref(self.plan), _stream(stream)))
+
+    def autotune(self, sample_views: int = 4, stream=None) -> dict:
+        check(load().scoup_autotune(self.plan, int(sample_views), _stream(stream)))
+        return self.info()
+
+    def set(self, lanes: int, warp_w: int) -> None:
+        check(load().scoup_plan_set(self.plan, int(lanes), int(warp_w)))
+
+    def run(self, eager: bool = False, stream=None) -> None:
+        check(load().scoup_uplift_batched(self.plan, SCOUP_BATCH_EAGER if eager else 0, _stream(stream)))
+
+    def stats(self, stream=None) -> list:
+        arr = (Stats * len(self.wls))()
+        check(load().scoup_plan_stats(self.plan, ct.cast(arr, ct.c_void_p), _stream(stream)))
+        return [arr[b].as_dict() for b in range(len(self.wls))]
+
+    def info(self) -> dict:
+        pi = PlanInfo()
+        check(load().scoup_plan_info_get(self.plan, ct.byref(pi)))
+        return {"lanes": pi.lanes, "warp_w": pi.warp_w, "tuned": bool(pi.tuned), "graph_kernels": pi.graph_kernels,
+                "workspace_bytes": int(pi.workspace_bytes),
+                "tune": [{"lanes": pi.tune[i].lanes, "warp_w": pi.tune[i].warp_w, "ms": float(pi.tune[i].ms)}
+                         for i in range(pi.n_tune)]}
+
+    def accum_value(self, b: int):
+        if self.compensated:
+            return self.accum[b][0].double() + self.accum[b][1].double()
+        return self.accum[b]
+
+    def close(self) -> None:
+        if getattr(self, "plan", None) is not None and self.plan.value:
+            load().scoup_plan_destroy(self.plan)
+            self.plan = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 __all__ = ["ScoupError", "SCOUP_ACCUM_CONTINUE", "SCOUP_ACCUM_COMPENSATED", "scene_struct", "camera_array", "scoup_version",
            "scoup_uplift_workspace_size", "scoup_uplift_plan", "scoup_uplift", "scoup_topk",
            "scoup_read_stats", "scoup_uplift_noalloc", "scoup_uplift_noalloc_max_bytes",
            "scoup_profile_enable", "scoup_profile_read", "scoup_launch_count",
            "scoup_render", "scoup_render_backward", "Render", "Uplift",
            "scoup_decode_workspace_size", "scoup_decode", "scoup_similarity_workspace_size",
-           "scoup_similarity", "scoup_decode_fp32", "scoup_similarity_fp32"]
+           "scoup_similarity", "scoup_decode_fp32", "scoup_similarity_fp32", "BatchedUplift",
+           "SCOUP_BATCH_EAGER"]
