@@ -47,6 +47,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU oracle sample budget")
     ap.add_argument("--render-views", type=int, default=8,
                     help="views of the 1920x1080 render + decode measurement (0 = skip)")
+    ap.add_argument("--batch-scenes", type=int, default=16,
+                    help="scenes of the batched-uplift measurement (0 = skip)")
     return ap.parse_args()
 
 
@@ -359,13 +361,19 @@ def run_gb300(args, dist):
     if args.render_views > 0:
         rd = render_decode_leg(args, dist, wl, up, dev, pk)
 
+    bt = None
+    if args.batch_scenes > 0:
+        del up
+        torch.cuda.empty_cache()
+        bt = batched_leg(args, dist, dev)
+
     if dist.rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded stand-in for pretrained 3DGS scenes with SAM/CLIP region codes)",
-            "config": {"workload": WORKLOAD, "n_gaussians": wl.scene.n, "views": len(up.cams),
+            "config": {"workload": WORKLOAD, "n_gaussians": wl.scene.n, "views": V,
                        "width": 988, "height": 731, "regions_per_view": 200, "C": wl.C, "s": wl.s,
                        "K": wl.K, "contributions_per_step": contrib,
                        "evaluated_pairs_per_step": st0["evaluated_pairs"],
@@ -375,6 +383,7 @@ def run_gb300(args, dist):
             "clocks": clk, "phase_ms_per_step": step_ms,
             "stats": {k: st0[k] for k in ("visible", "duplicates", "flushes", "atomics")},
             "render_decode": rd,
+            "batched": bt,
         }
         print(json.dumps(line), flush=True)
 
@@ -470,6 +479,80 @@ def render_decode_leg(args, dist, wl, up, dev, pk):
                             "per_launch_ms": t_gemm * 1e3,
                             "hbm_gbs": (2.0 * P * wl.C + 2.0 * P * D) / t_gemm / 1e9,
                             "peak_source": pk["source"] + " bf16 burst"},
+    }
+
+
+def batched_leg(args, dist, dev):
+    """Secondary measurement: 16 scenes of uneven size (200k-2M Gaussians,
+    50-300 views, 640x480 to 1296x968), uplifted (a) as per-scene plain calls
+    one after another on one stream and (b) as one autotuned batch replayed
+    from a CUDA graph.  Same metric as the headline (contributions/s)."""
+    import torch
+
+    import synth
+    import paper_2605_13600_gb300 as gb
+
+    t_gen = time.perf_counter()
+    wls = [synth.uplift_cfg3_scene(b, device=str(dev)) for b in range(args.batch_scenes)]
+    t_gen = time.perf_counter() - t_gen
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(1, min(args.steps, 3))
+
+    # (a) plain: one scoup_uplift per scene, back to back
+    ups = [gb.Uplift(wl, device=str(dev)) for wl in wls]
+    sts = [u.run(stats=True) for u in ups]
+    contrib = sum(st["contributions"] for st in sts)
+    for u in ups:
+        u.run(stats=False)
+    torch.cuda.synchronize()
+    dist.barrier()
+    ev0.record(stream)
+    for _ in range(reps):
+        for u in ups:
+            u.run(stats=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_plain = dist.max(ev0.elapsed_time(ev1) / 1e3 / reps)
+    del ups
+    torch.cuda.empty_cache()
+
+    # (b) batched: plan, autotune on 4 views per scene, graph replay
+    bu = gb.BatchedUplift(wls, device=str(dev))
+    t_tune = time.perf_counter()
+    info = bu.autotune(sample_views=4)
+    t_tune = time.perf_counter() - t_tune
+    bu.run()
+    st_b = bu.stats()
+    if any(s["status"] != 0 for s in st_b):
+        raise RuntimeError("batched uplift status")
+    contrib_b = sum(s["contributions"] for s in st_b)
+    bu.run()
+    torch.cuda.synchronize()
+    dist.barrier()
+    l0 = gb.scoup_launch_count()
+    ev0.record(stream)
+    for _ in range(reps):
+        bu.run()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = dist.max(ev0.elapsed_time(ev1) / 1e3 / reps)
+    launches = (gb.scoup_launch_count() - l0) // reps
+    info = bu.info()
+    bu.close()
+    return {
+        "metric": METRIC, "unit": UNIT,
+        "workload": f"uplift_batch_{len(wls)}scenes_200k-2M_50-300views_640x480-1296x968_C256_s8_K8",
+        "scenes": [w.name for w in wls], "views": sum(len(w.cams) for w in wls),
+        "gaussians": sum(w.scene.n for w in wls), "contributions": contrib,
+        "contributions_batched": contrib_b,
+        "plain": {"value": dist.world * contrib / t_plain, "ms_per_batch": t_plain * 1e3,
+                  "form": "one scoup_uplift per scene, back to back on one stream"},
+        "batched": {"value": dist.world * contrib_b / t_batch, "ms_per_batch": t_batch * 1e3,
+                    "form": "scoup_uplift_batched: autotuned lanes + warp block, one CUDA graph launch",
+                    "lanes": info["lanes"], "warp_w": info["warp_w"], "graph_kernels": info["graph_kernels"],
+                    "gpu_launches": int(launches), "tune": info["tune"], "tune_s": t_tune},
+        "speedup": t_plain / t_batch, "timed_batches": reps, "generation_s": t_gen,
     }
 
 

@@ -200,7 +200,9 @@ def voronoi_map(seeds_xy: np.ndarray, width: int, height: int, device: str = "cp
     sidx = torch.arange(R, device=device, dtype=torch.int64)
     out = torch.empty(height * width, dtype=torch.int64, device=device)
     xs_all = torch.arange(width, device=device, dtype=torch.int64)
-    rows_per_chunk = max(1, (1 << 22) // max(1, width * R))
+    # chunking only bounds memory: the integer keys make the result independent of it
+    budget = (1 << 26) if str(device).startswith("cuda") else (1 << 22)
+    rows_per_chunk = max(1, budget // max(1, width * R))
     for y0 in range(0, height, rows_per_chunk):
         y1 = min(height, y0 + rows_per_chunk)
         ys = torch.arange(y0, y1, device=device, dtype=torch.int64)
