@@ -494,7 +494,7 @@ size_t scoup_decode_workspace_size(int64_t P, int32_t C, int32_t D) {
 int scoup_decode(const void* codes, int32_t codes_dtype, int64_t P, int32_t C, const float* codebook, int32_t D,
                  void* features, int32_t out_dtype, float* feat_norm2, void* workspace, size_t ws_bytes,
                  void* stream) {
-  if (P < 0) return fail(SCOUP_ERR_INVALID_ARG, "P < 0");
+  if (P < 0 || P > 0x7fffffffLL) return fail(SCOUP_ERR_INVALID_ARG, "P=%lld outside [0, 2^31)", (long long)P);
   if (C < 8 || C % 8 || C > 4096) return fail(SCOUP_ERR_INVALID_ARG, "C=%d must be a multiple of 8 in [8, 4096]", C);
   if (D < 16 || D % 16) return fail(SCOUP_ERR_INVALID_ARG, "D=%d must be a positive multiple of 16", D);
   if (codes_dtype != 0 && codes_dtype != 1) return fail(SCOUP_ERR_INVALID_ARG, "codes_dtype must be 0 (f32) or 1 (bf16)");
@@ -517,7 +517,9 @@ int scoup_decode(const void* codes, int32_t codes_dtype, int64_t P, int32_t C, c
   if (feat_norm2 && (e = cudaMemsetAsync(feat_norm2, 0, sizeof(float) * (size_t)P, st)) != cudaSuccess)
     return cuda_fail(e, "memset");
   if ((e = launch_transpose_bf16(codebook, Bt, C, D, st)) != cudaSuccess) return cuda_fail(e, "codebook");
-  const int64_t chunk = decode_chunk_rows(P);
+  // bf16 codes feed the GEMM directly (one launch); f32 codes are rounded to
+  // bf16 chunk by chunk in the workspace first
+  const int64_t chunk = codes_dtype == 1 ? P : decode_chunk_rows(P);
   for (int64_t r0 = 0; r0 < P; r0 += chunk) {
     const int64_t rows = P - r0 < chunk ? P - r0 : chunk;
     const void* A;
@@ -550,11 +552,12 @@ size_t scoup_similarity_workspace_size(int64_t P, int32_t D, int32_t Q) {
 
 int scoup_similarity(const void* features, int64_t P, int32_t D, const float* feat_norm2, const float* text,
                      int32_t Q, float* out, void* workspace, size_t ws_bytes, void* stream) {
-  if (P < 0) return fail(SCOUP_ERR_INVALID_ARG, "P < 0");
+  if (P < 0 || P > 0x7fffffffLL) return fail(SCOUP_ERR_INVALID_ARG, "P=%lld outside [0, 2^31)", (long long)P);
   if (D < 8 || D % 8) return fail(SCOUP_ERR_INVALID_ARG, "D=%d must be a positive multiple of 8", D);
   if (Q < 16 || Q % 16 || Q > 256) return fail(SCOUP_ERR_INVALID_ARG, "Q=%d must be a multiple of 16 in [16, 256]", Q);
   if (P > 0 && (!features || !text || !out)) return fail(SCOUP_ERR_INVALID_ARG, "NULL array");
-  if ((uintptr_t)features & 15u) return fail(SCOUP_ERR_INVALID_ARG, "features must be 16-byte aligned");
+  if (((uintptr_t)features & 15u) || ((uintptr_t)out & 15u))
+    return fail(SCOUP_ERR_INVALID_ARG, "features and out must be 16-byte aligned");
   if (!workspace || ws_bytes < scoup_similarity_workspace_size(P, D, Q))
     return fail(SCOUP_ERR_OOM, "workspace too small: need %zu bytes", scoup_similarity_workspace_size(P, D, Q));
   if (!gemm_tma_available()) return fail(SCOUP_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");

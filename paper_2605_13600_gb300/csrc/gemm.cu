@@ -3,18 +3,21 @@
 //
 //   out[M, N] = A[M, K] * Bt[N, K]^T      (A, Bt bf16, K-major; f32 accumulate)
 //
-// One CTA computes a BM x BN tile (BM = 128).  Warp 0 issues TMA loads of
-// 128-byte-swizzled K-major A and Bt tiles (BK = 64 bf16 = one swizzle row)
-// into a kStages-deep shared-memory ring guarded by mbarriers; warp 1
-// allocates BN TMEM columns and one thread issues tcgen05.mma (M=128, N=BN,
-// K=16, four per stage), releasing each stage with tcgen05.commit; warps 2-5
-// read the f32 accumulator back with tcgen05.ld (each warp its 32-lane TMEM
-// quarter, one output row per thread) and run the epilogue:
+// Persistent: one CTA per SM walks the output in units of BM x BN (BM = 128).
+// Warp 0 streams 128-byte-swizzled K-major A and Bt tiles (BK = 64 bf16, one
+// swizzle row) with TMA into a kStages ring guarded by mbarriers; warp 1
+// allocates two BN-column TMEM accumulators and one thread issues
+// tcgen05.mma (M=128, N=BN, K=16) into them alternately, so the epilogue of
+// one unit overlaps the MMAs of the next; warps 2-5 each own a 32-lane TMEM
+// quarter (32 output rows), read 128-byte row chunks back with tcgen05.ld,
+// apply the epilogue, stage them 128-byte-swizzled in shared memory and write
+// them with TMA tile stores (double-buffered per warp).  Epilogues:
 //   kOutBF16 : bf16 output, optional per-row sum of squares of the rounded values
 //   kOutF32  : f32 output
 //   kOutCos  : f32 output / (|row| |column|), 0 where |row| < 1e-12
 // Every mbarrier wait is bounded; a wait that gives up records an error in
-// *status and the CTA frees its TMEM and leaves.
+// *status, raises the CTA's abort flag, and every role leaves after draining
+// its own copies in flight; TMEM is freed on every path.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -22,38 +25,58 @@
 #include "sm100_ptx.cuh"
 
 namespace scoup {
-
-
 namespace {
 
 constexpr int BM = 128, BK = 64;
-constexpr int kStages = 2;
 constexpr int kGemmThreads = 192;
 constexpr uint32_t kWaitIters = 1u << 22;
 
 template <int BN>
-struct GemmSmem {
-  alignas(1024) __nv_bfloat16 a[kStages][BM * BK];
-  alignas(1024) __nv_bfloat16 b[kStages][BN * BK];
-  uint64_t full[kStages];
-  uint64_t empty[kStages];
-  uint64_t done;
-  uint32_t tmem;
-  int abort;
+struct GemmCfg {
+  static constexpr int kStages = BN >= 256 ? 3 : 4;
+  static constexpr uint32_t kTmemCols = 2 * BN;  // two accumulators
 };
+
+template <int BN>
+struct GemmSmem {
+  alignas(1024) __nv_bfloat16 a[GemmCfg<BN>::kStages][BM * BK];
+  alignas(1024) __nv_bfloat16 b[GemmCfg<BN>::kStages][BN * BK];
+  alignas(1024) unsigned char out[4][2][32 * 128];  // per epilogue warp, two 32-row x 128-byte chunks
+  uint64_t full[GemmCfg<BN>::kStages];
+  uint64_t empty[GemmCfg<BN>::kStages];
+  uint64_t acc_full[2];
+  uint64_t acc_empty[2];
+  uint64_t drain;
+  uint32_t tmem;
+  volatile int abort;
+};
+
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort, int* status) {
+  if (ptx::mbar_wait_bounded(bar, parity, kWaitIters)) return true;
+  atomicOr(status, kStatTimeout);
+  *abort = 1;
+  return false;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float x, float y) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
 
 template <int BN>
 __global__ void __launch_bounds__(kGemmThreads, 1) gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                     const __grid_constant__ CUtensorMap tmB,
+                                                                    const __grid_constant__ CUtensorMap tmO,
                                                                     GemmEpi ep) {
+  using Cfg = GemmCfg<BN>;
+  constexpr int kStages = Cfg::kStages;
   extern __shared__ __align__(1024) unsigned char gsm_raw[];
-  // align the carve-up to 1024 bytes (swizzle atoms)
   unsigned char* base = gsm_raw + ((1024 - (ptx::smem_u32(gsm_raw) & 1023u)) & 1023u);
   GemmSmem<BN>& sm = *reinterpret_cast<GemmSmem<BN>*>(base);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   const int kt = (ep.K + BK - 1) / BK;
-  constexpr uint32_t kTmemCols = BN < 32 ? 32 : BN;
+  const int n_tiles = (ep.N + BN - 1) / BN;
+  const int units = ((ep.M + BM - 1) / BM) * n_tiles;
   constexpr uint32_t kBytesA = BM * BK * 2, kBytesB = BN * BK * 2;
   constexpr uint32_t idesc = ptx::idesc_bf16_f32(BM, BN);
 
@@ -62,14 +85,19 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_bf16_kernel(const __grid
       ptx::mbar_init(&sm.full[s], 1);
       ptx::mbar_init(&sm.empty[s], 1);
     }
-    ptx::mbar_init(&sm.done, 1);
+    for (int b = 0; b < 2; ++b) {
+      ptx::mbar_init(&sm.acc_full[b], 1);
+      ptx::mbar_init(&sm.acc_empty[b], 4);
+    }
+    ptx::mbar_init(&sm.drain, 1);
     sm.abort = 0;
     ptx::fence_mbar_init();
     ptx::prefetch_tmap(&tmA);
     ptx::prefetch_tmap(&tmB);
+    ptx::prefetch_tmap(&tmO);
   }
   if (warp == 1) {
-    ptx::tmem_alloc(&sm.tmem, kTmemCols);
+    ptx::tmem_alloc(&sm.tmem, Cfg::kTmemCols);
     ptx::tmem_relinquish();
   }
   ptx::tc_fence_before();
@@ -79,103 +107,136 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_bf16_kernel(const __grid
 
   if (warp == 0 && lane == 0) {
     // ---- TMA producer ----
-    for (int kb = 0; kb < kt; ++kb) {
-      const int s = kb % kStages;
-      if (kb >= kStages && !ptx::mbar_wait_bounded(&sm.empty[s], ((kb / kStages) - 1) & 1, kWaitIters)) {
-        atomicOr(ep.status, kStatTimeout);
-        sm.abort = 1;
-        break;
+    int it = 0;
+    for (int u = blockIdx.x; u < units && !sm.abort; u += gridDim.x) {
+      const int m0 = (u / n_tiles) * BM, n0 = (u % n_tiles) * BN;
+      for (int kb = 0; kb < kt; ++kb, ++it) {
+        const int s = it % kStages;
+        if (it >= kStages && !wait_or_abort(&sm.empty[s], ((it / kStages) - 1) & 1, &sm.abort, ep.status)) break;
+        ptx::mbar_arrive_expect_tx(&sm.full[s], kBytesA + kBytesB);
+        ptx::tma_load_2d(sm.a[s], &tmA, &sm.full[s], kb * BK, m0);
+        ptx::tma_load_2d(sm.b[s], &tmB, &sm.full[s], kb * BK, n0);
       }
-      ptx::mbar_arrive_expect_tx(&sm.full[s], kBytesA + kBytesB);
-      ptx::tma_load_2d(sm.a[s], &tmA, &sm.full[s], kb * BK, m0);
-      ptx::tma_load_2d(sm.b[s], &tmB, &sm.full[s], kb * BK, n0);
     }
     // wait (bounded) for the last copy issued into each stage before leaving
-    for (int s = 0; s < kStages && s < kt; ++s) {
-      const int kb_last = s + ((kt - 1 - s) / kStages) * kStages;
-      if (!ptx::mbar_wait_bounded(&sm.full[s], (kb_last / kStages) & 1, kWaitIters)) atomicOr(ep.status, kStatTimeout);
+    for (int s = 0; s < kStages && s < it; ++s) {
+      const int last = s + ((it - 1 - s) / kStages) * kStages;
+      if (!ptx::mbar_wait_bounded(&sm.full[s], (last / kStages) & 1, kWaitIters)) atomicOr(ep.status, kStatTimeout);
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer ----
+    int it = 0, local = 0;
     bool ok = true;
-    for (int kb = 0; kb < kt && ok; ++kb) {
-      const int s = kb % kStages;
-      if (!ptx::mbar_wait_bounded(&sm.full[s], (kb / kStages) & 1, kWaitIters)) {
-        atomicOr(ep.status, kStatTimeout);
-        ok = false;
-        break;
-      }
+    for (int u = blockIdx.x; u < units && ok && !sm.abort; u += gridDim.x, ++local) {
+      const int b = local & 1, use = local >> 1;
+      if (local >= 2 && !wait_or_abort(&sm.acc_empty[b], (use - 1) & 1, &sm.abort, ep.status)) break;
       ptx::tc_fence_after();
-      const uint32_t sa = ptx::smem_u32(sm.a[s]), sb = ptx::smem_u32(sm.b[s]);
+      const uint32_t d = tmem + (uint32_t)(b * BN);
+      for (int kb = 0; kb < kt; ++kb, ++it) {
+        const int s = it % kStages;
+        if (!wait_or_abort(&sm.full[s], (it / kStages) & 1, &sm.abort, ep.status)) {
+          ok = false;
+          break;
+        }
+        ptx::tc_fence_after();
+        const uint32_t sa = ptx::smem_u32(sm.a[s]), sb = ptx::smem_u32(sm.b[s]);
 #pragma unroll
-      for (int k = 0; k < BK / 16; ++k) {
-        const uint64_t da = ptx::smem_desc_k128(sa + k * 32);
-        const uint64_t db = ptx::smem_desc_k128(sb + k * 32);
-        ptx::mma_f16(tmem, da, db, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+        for (int k = 0; k < BK / 16; ++k)
+          ptx::mma_f16(d, ptx::smem_desc_k128(sa + k * 32), ptx::smem_desc_k128(sb + k * 32), idesc,
+                       (kb > 0 || k > 0) ? 1u : 0u);
+        ptx::mma_commit(&sm.empty[s]);
       }
-      ptx::mma_commit(&sm.empty[s]);
+      if (ok) ptx::mma_commit(&sm.acc_full[b]);
     }
-    ptx::mma_commit(&sm.done);  // arrives once every issued MMA has completed
+    // every issued MMA has completed once `drain` flips
+    ptx::mma_commit(&sm.drain);
+    if (!ptx::mbar_wait_bounded(&sm.drain, 0, kWaitIters)) atomicOr(ep.status, kStatTimeout);
   } else if (warp >= 2) {
     // ---- epilogue ----
     const int q = warp & 3;  // TMEM lane quarter this warp may access
-    const int row = m0 + q * 32 + lane;
-    const bool waited = ptx::mbar_wait_bounded(&sm.done, 0, kWaitIters);
-    ptx::tc_fence_after();
-    if (!waited) {
-      if (lane == 0) atomicOr(ep.status, kStatTimeout);
-    } else {
-      float ss = 0.0f;
+    constexpr int kCW = 64;  // bf16 columns per 128-byte chunk (32 for f32 output)
+    const bool f32out = ep.mode != kOutBF16;
+    const int cw = f32out ? 32 : kCW;
+    int local = 0, sbuf = 0;
+    for (int u = blockIdx.x; u < units && !sm.abort; u += gridDim.x, ++local) {
+      const int m0 = (u / n_tiles) * BM, n0 = (u % n_tiles) * BN;
+      const int b = local & 1, use = local >> 1;
+      if (!wait_or_abort(&sm.acc_full[b], use & 1, &sm.abort, ep.status)) break;
+      ptx::tc_fence_after();
+      const int row = m0 + q * 32 + lane;
       float rinv = 0.0f;
       if (ep.mode == kOutCos && row < ep.M) {
         const float rn = sqrtf(ep.rownorm2[row]);
         rinv = rn < 1e-12f ? 0.0f : 1.0f / rn;
       }
-#pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 32) {
-        float v[32];
-        ptx::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-        if (row >= ep.M) continue;
-        const int col0 = n0 + c0;
-        if (ep.mode == kOutBF16) {
-          __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(ep.out) + (int64_t)row * ep.ldo + col0;
+      float ss = 0.0f;
+      const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN);
+      for (int c0 = 0; c0 < BN; c0 += cw) {
+        float v[kCW];
+        ptx::tmem_ld32(tbase + (uint32_t)c0, *reinterpret_cast<float(*)[32]>(&v[0]));
+        if (!f32out) ptx::tmem_ld32(tbase + (uint32_t)(c0 + 32), *reinterpret_cast<float(*)[32]>(&v[32]));
+        if (c0 + cw >= BN) {
+          // the accumulator is drained: the MMA warp may reuse it
+          ptx::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(&sm.acc_empty[b]);
+        }
+        // a box that starts past the last row or column stores nothing: skip it
+        if (n0 + c0 >= ep.N || m0 + q * 32 >= ep.M) continue;
+        unsigned char* buf = sm.out[q][sbuf];
+        if (lane == 0) ptx::bulk_wait_read<1>();  // this buffer's previous store has read it
+        __syncwarp();
+        unsigned char* rowp = buf + lane * 128;
+        if (!f32out) {
 #pragma unroll
-          for (int i = 0; i < 32; i += 2) {
-            if (col0 + i + 1 < ep.N) {
-              const __nv_bfloat162 h = __floats2bfloat162_rn(v[i], v[i + 1]);
-              *reinterpret_cast<__nv_bfloat162*>(o + i) = h;
-              const float2 f = __bfloat1622float2(h);
-              ss += f.x * f.x + f.y * f.y;
-            } else if (col0 + i < ep.N) {
-              const __nv_bfloat16 h = __float2bfloat16_rn(v[i]);
-              o[i] = h;
-              const float f = __bfloat162float(h);
-              ss += f * f;
+          for (int j = 0; j < 8; ++j) {
+            uint4 w;
+            w.x = pack_bf16x2(v[8 * j + 0], v[8 * j + 1]);
+            w.y = pack_bf16x2(v[8 * j + 2], v[8 * j + 3]);
+            w.z = pack_bf16x2(v[8 * j + 4], v[8 * j + 5]);
+            w.w = pack_bf16x2(v[8 * j + 6], v[8 * j + 7]);
+            *reinterpret_cast<uint4*>(rowp + ((j ^ (lane & 7)) << 4)) = w;
+            if (ep.rownorm2) {
+              const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&w);
+#pragma unroll
+              for (int t = 0; t < 4; ++t) {
+                const float2 f = __bfloat1622float2(h[t]);
+                ss = fmaf(f.x, f.x, fmaf(f.y, f.y, ss));
+              }
             }
           }
         } else {
-          float* o = reinterpret_cast<float*>(ep.out) + (int64_t)row * ep.ldo + col0;
+          if (ep.mode == kOutCos) {
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            if (col0 + i < ep.N) {
-              float x = v[i];
-              if (ep.mode == kOutCos) {
-                const float cn = ep.colnorm[col0 + i];
-                x = (rinv == 0.0f || cn == 0.0f) ? 0.0f : x * rinv / cn;
-              }
-              o[i] = x;
+            for (int i = 0; i < 32; ++i) {
+              const int c = n0 + c0 + i;
+              const float cn = c < ep.N ? ep.colnorm[c] : 0.0f;
+              v[i] = (rinv == 0.0f || cn == 0.0f) ? 0.0f : v[i] * rinv / cn;
             }
           }
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            *reinterpret_cast<float4*>(rowp + ((j ^ (lane & 7)) << 4)) =
+                make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
         }
+        ptx::fence_async_shared();
+        __syncwarp();
+        if (lane == 0) {
+          ptx::tma_store_2d(&tmO, buf, n0 + c0, m0 + q * 32);
+          ptx::bulk_commit();
+        }
+        sbuf ^= 1;
       }
-      if (ep.mode == kOutBF16 && ep.rownorm2 && row < ep.M) atomicAdd(&ep.rownorm2[row], ss);
+      if (!f32out && ep.rownorm2 && row < ep.M) atomicAdd(&ep.rownorm2[row], ss);
     }
+    if (lane == 0) ptx::bulk_wait<0>();  // stores complete before the CTA leaves
+    __syncwarp();
   }
   ptx::tc_fence_before();
   __syncthreads();
   if (warp == 1) {
     ptx::tc_fence_after();
-    ptx::tmem_dealloc(tmem, kTmemCols);
+    ptx::tmem_dealloc(tmem, Cfg::kTmemCols);
   }
 }
 
@@ -204,28 +265,46 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// K-major bf16 matrix [rows, K] (row stride K elements), box [box_rows, 64], 128-byte swizzle.
-bool make_tmap(CUtensorMap* m, const void* ptr, int64_t rows, int K, int box_rows) {
+// Row-major 2-D matrix [rows, cols] (row stride cols elements), box
+// [box_rows, box_cols], 128-byte swizzle (box_cols x element size = 128 bytes).
+bool make_tmap(CUtensorMap* m, const void* ptr, CUtensorMapDataType dt, int esize, int64_t rows, int64_t cols,
+               int box_cols, int box_rows) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)K * 2};
-  cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * (cuuint64_t)esize};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1u, 1u};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+  return enc(m, dt, 2, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+  }
+  return n;
 }
 
 template <int BN>
 cudaError_t launch_bn(const void* A, const void* Bt, const GemmEpi& ep, cudaStream_t st) {
-  CUtensorMap ta, tb;
-  if (!make_tmap(&ta, A, ep.M, ep.K, BM) || !make_tmap(&tb, Bt, ep.N, ep.K, BN)) return cudaErrorInvalidValue;
+  CUtensorMap ta, tb, to;
+  const bool f32out = ep.mode != kOutBF16;
+  if (!make_tmap(&ta, A, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ep.M, ep.K, BK, BM) ||
+      !make_tmap(&tb, Bt, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ep.N, ep.K, BK, BN) ||
+      !(f32out ? make_tmap(&to, ep.out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ep.M, ep.ldo, 32, 32)
+               : make_tmap(&to, ep.out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ep.M, ep.ldo, 64, 32)))
+    return cudaErrorInvalidValue;
   const size_t smem = sizeof(GemmSmem<BN>) + 1024;
   cudaError_t e = cudaFuncSetAttribute(gemm_bf16_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)((ep.M + BM - 1) / BM), (unsigned)((ep.N + BN - 1) / BN));
-  gemm_bf16_kernel<BN><<<grid, kGemmThreads, smem, st>>>(ta, tb, ep);
+  const int64_t units = ((int64_t)(ep.M + BM - 1) / BM) * ((ep.N + BN - 1) / BN);
+  const int grid = (int)(units < num_sms() ? units : num_sms());
+  gemm_bf16_kernel<BN><<<grid, kGemmThreads, smem, st>>>(ta, tb, to, ep);
   g_launches += 1;
   return cudaGetLastError();
 }
@@ -278,7 +357,9 @@ int blocks_for(int64_t n, int per) {
 
 cudaError_t launch_gemm_bf16(const void* A, const void* Bt, const GemmEpi& ep, cudaStream_t st) {
   if (ep.M <= 0 || ep.N <= 0) return cudaSuccess;
-  if (ep.N <= 32) return launch_bn<32>(A, Bt, ep, st);
+  // bf16 output is read back from TMEM 64 columns at a time: BN >= 64 (the
+  // columns past N are the zero fill of the Bt tile)
+  if (ep.N <= 32 && ep.mode != kOutBF16) return launch_bn<32>(A, Bt, ep, st);
   if (ep.N <= 64) return launch_bn<64>(A, Bt, ep, st);
   if (ep.N <= 128) return launch_bn<128>(A, Bt, ep, st);
   return launch_bn<256>(A, Bt, ep, st);
