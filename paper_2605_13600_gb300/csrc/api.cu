@@ -93,7 +93,8 @@ size_t uplift_fixed_bytes(int64_t n, int max_tiles, int64_t code_rows_k) {
   b += align_up(sizeof(ProjRec) * un);                    // proj
   b += align_up(sizeof(uint32_t) * un);                   // depth
   b += align_up(sizeof(ushort4) * un);                    // rect
-  b += 3 * align_up(sizeof(uint32_t) * ((size_t)max_tiles + 1));
+  b += 4 * align_up(sizeof(uint32_t) * ((size_t)max_tiles + 1));
+  b += align_up(binning_run_base_bytes(n));                // binning: reserved-run offsets
   b += 2 * align_up((size_t)code_rows_k * 4);             // filtered codes (s > K)
   return b;
 }
@@ -118,6 +119,8 @@ UpliftWs carve(void* ws, size_t bytes, int64_t n, int max_tiles, int64_t code_ro
   w.depth = (uint32_t*)take(sizeof(uint32_t) * un);
   w.rect = (ushort4*)take(sizeof(ushort4) * un);
   w.tile_count = (uint32_t*)take(sizeof(uint32_t) * ((size_t)max_tiles + 1));
+  w.tile_glob = (uint32_t*)take(sizeof(uint32_t) * ((size_t)max_tiles + 1));
+  w.run_base = (uint32_t*)take(binning_run_base_bytes(n));
   w.tile_start = (uint32_t*)take(sizeof(uint32_t) * ((size_t)max_tiles + 1));
   w.tile_fill = (uint32_t*)take(sizeof(uint32_t) * ((size_t)max_tiles + 1));
   *codes_i = (int32_t*)take((size_t)code_rows_k * 4);
@@ -249,7 +252,8 @@ int uplift_call(const UpliftCall& c, void* workspace, size_t ws_bytes, int warp_
       (e = cudaMemsetAsync(accum, 0, sizeof(float) * (size_t)n * (size_t)C * (compensated ? 2 : 1), st)) !=
           cudaSuccess)
     return cuda_fail(e, "memset accum");
-  if ((e = cudaMemsetAsync(ws.tile_count, 0, sizeof(uint32_t) * ((size_t)max_tiles + 1), st)) != cudaSuccess)
+  if ((e = cudaMemsetAsync(ws.tile_glob, 0, sizeof(uint32_t) * ((size_t)max_tiles + 1), st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(ws.tile_count, 0, sizeof(uint32_t) * ((size_t)max_tiles + 1), st)) != cudaSuccess)
     return cuda_fail(e, "memset");
   const int32_t* ci = code_idx;
   const float* cv = code_val;
@@ -404,7 +408,8 @@ int scoup_render(const scoup_scene* scene, const int32_t* topk_idx, const float*
   const CamArgs ca = cam_args(*cam);
   cudaError_t e;
   if ((e = cudaMemsetAsync(ws.hdr, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
-  if ((e = cudaMemsetAsync(ws.tile_count, 0, sizeof(uint32_t) * ((size_t)max_tiles + 1), st)) != cudaSuccess)
+  if ((e = cudaMemsetAsync(ws.tile_glob, 0, sizeof(uint32_t) * ((size_t)max_tiles + 1), st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(ws.tile_count, 0, sizeof(uint32_t) * ((size_t)max_tiles + 1), st)) != cudaSuccess)
     return cuda_fail(e, "memset");
   {
     PhaseScope ps(SCOUP_PHASE_TAU, st);
@@ -455,7 +460,8 @@ int scoup_render_backward(const scoup_scene* scene, const int32_t* topk_idx, con
   const CamArgs ca = cam_args(*cam);
   cudaError_t e;
   if ((e = cudaMemsetAsync(ws.hdr, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
-  if ((e = cudaMemsetAsync(ws.tile_count, 0, sizeof(uint32_t) * ((size_t)max_tiles + 1), st)) != cudaSuccess)
+  if ((e = cudaMemsetAsync(ws.tile_glob, 0, sizeof(uint32_t) * ((size_t)max_tiles + 1), st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(ws.tile_count, 0, sizeof(uint32_t) * ((size_t)max_tiles + 1), st)) != cudaSuccess)
     return cuda_fail(e, "memset");
   {
     PhaseScope ps(SCOUP_PHASE_TAU, st);

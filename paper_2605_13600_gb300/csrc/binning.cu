@@ -10,11 +10,13 @@
 //
 // The Gaussians arrive in spatial (Morton) order, so one CTA's chunk covers a
 // compact block of tiles.  Each warp expands the (Gaussian, tile) items of its
-// 32 Gaussians cooperatively, one item per lane per round.  Counting and
-// filling are privatised per CTA in shared memory over the chunk's tile
-// bounding box: global atomics are one per (CTA, tile), and the keys of a CTA
-// land in one contiguous run per tile.  Rectangles larger than kBigRect tiles
-// go straight to the global counters.
+// 32 Gaussians cooperatively, one item per lane per round.  Counting is
+// privatised per CTA in shared memory over the chunk's tile bounding box; the
+// counting pass reserves the CTA's run in each tile list right away (one
+// global atomic per (CTA, tile)) and keeps the run's offset, so the filling
+// pass expands the items only once and writes each CTA's keys of a tile into
+// one contiguous run.  Rectangles larger than kBigRect tiles go to separate
+// global counters and are placed after the reserved runs.
 #include "scoup_internal.cuh"
 
 namespace scoup {
@@ -39,6 +41,13 @@ __device__ __forceinline__ bool big(const ushort4& r) { return (r.z - r.x) * (r.
 // numbered by an exclusive scan of the rectangle areas and dealt out 32 at a
 // time, one per lane, so every lane works on one item per round whatever the
 // rectangle sizes.  f(src_lane, tx, ty) is called for each item.
+// q = local / w for 0 <= local < 2^22, 1 <= w: (local + 0.5) / w lies at
+// least 0.5 / w away from an integer, far more than the error of the
+// approximate quotient, so truncation gives the exact integer quotient.
+__device__ __forceinline__ int div_small(int local, int w) {
+  return local < (1 << 22) ? (int)__fdividef((float)local + 0.5f, (float)w) : local / w;
+}
+
 template <typename F>
 __device__ __forceinline__ void expand_items(const ushort4& r, F&& f) {
   const int lane = threadIdx.x & 31;
@@ -65,7 +74,7 @@ __device__ __forceinline__ void expand_items(const ushort4& r, F&& f) {
     const int p_src = __shfl_sync(kFull, packed, src);
     if (item < total) {
       const int local = item - e_src;
-      const int yy = local / w_src;
+      const int yy = div_small(local, w_src);
       f(src, (p_src & 0xffff) + (local - yy * w_src), (p_src >> 16) + yy);
     }
   }
@@ -103,7 +112,9 @@ __device__ LocalBox chunk_box(const ushort4* __restrict__ rects, int64_t lo, int
 }
 
 __global__ void __launch_bounds__(kBinThreads) count_kernel(const ushort4* __restrict__ rects, int64_t n,
-                                                            int gx, uint32_t* __restrict__ tile_count) {
+                                                            int gx, uint32_t* __restrict__ tile_count,
+                                                            uint32_t* __restrict__ tile_glob,
+                                                            uint32_t* __restrict__ run_base) {
   __shared__ uint32_t s_cnt[kLocalMax];
   const int64_t lo = blockIdx.x * kChunk, hi = min(n, lo + kChunk);
   const LocalBox box = chunk_box(rects, lo, hi);
@@ -117,20 +128,25 @@ __global__ void __launch_bounds__(kBinThreads) count_kernel(const ushort4* __res
     const unsigned lmask = __ballot_sync(kFull, box.ok && !big(r));
     expand_items(r, [&](int src, int tx, int ty) {
       if ((lmask >> src) & 1u) atomicAdd(&s_cnt[box.idx(tx, ty)], 1u);
-      else atomicAdd(&tile_count[ty * gx + tx], 1u);
+      else atomicAdd(&tile_glob[ty * gx + tx], 1u);
     });
   }
   __syncthreads();
-  if (box.ok)
+  // reserve this CTA's run in every tile of its box (offset inside the tile's list)
+  if (box.ok) {
+    uint32_t* base = run_base + (int64_t)blockIdx.x * kLocalMax;
     for (int t = threadIdx.x; t < area; t += blockDim.x) {
       const uint32_t c = s_cnt[t];
-      if (c) atomicAdd(&tile_count[(box.y0 + t / box.w) * gx + box.x0 + t % box.w], c);
+      base[t] = c ? atomicAdd(&tile_count[(box.y0 + t / box.w) * gx + box.x0 + t % box.w], c) : 0u;
     }
+  }
 }
 
-// Exclusive scan of the tile counts (one CTA), capacity check, and reset of
-// the counters and fill cursors for the next view.
+// Exclusive scan of the tile counts (reserved runs + big-rectangle items; one
+// CTA), capacity check; the fill cursor of a tile starts after its reserved
+// runs; the counters are reset for the next view.
 __global__ void __launch_bounds__(1024) scan_kernel(uint32_t* __restrict__ tile_count,
+                                                    uint32_t* __restrict__ tile_glob,
                                                     uint32_t* __restrict__ tile_start,
                                                     uint32_t* __restrict__ tile_fill, int ntiles,
                                                     int64_t capacity, WsHeader* __restrict__ hdr,
@@ -142,7 +158,8 @@ __global__ void __launch_bounds__(1024) scan_kernel(uint32_t* __restrict__ tile_
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int base = 0; base < ntiles; base += blockDim.x) {
     const int t = base + threadIdx.x;
-    uint32_t v = t < ntiles ? tile_count[t] : 0u;
+    const uint32_t local = t < ntiles ? tile_count[t] : 0u;
+    uint32_t v = t < ntiles ? local + tile_glob[t] : 0u;
     uint32_t x = v;
     for (int off = 1; off < 32; off <<= 1) {
       uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
@@ -164,7 +181,8 @@ __global__ void __launch_bounds__(1024) scan_kernel(uint32_t* __restrict__ tile_
     if (t < ntiles) {
       tile_start[t] = (uint32_t)(carry + excl);
       tile_count[t] = 0u;
-      tile_fill[t] = 0u;
+      tile_glob[t] = 0u;
+      tile_fill[t] = local;
     }
     __syncthreads();
     if (threadIdx.x == blockDim.x - 1) s_carry = carry + excl + v;
@@ -185,7 +203,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(uint32_t* __restrict__ tile_
 __global__ void __launch_bounds__(kBinThreads) fill_kernel(
     const ushort4* __restrict__ rects, const uint32_t* __restrict__ depth, const int32_t* __restrict__ orig,
     int64_t n, int gx, const uint32_t* __restrict__ tile_start, uint32_t* __restrict__ tile_fill,
-    unsigned long long* __restrict__ keys, const WsHeader* __restrict__ hdr) {
+    const uint32_t* __restrict__ run_base, unsigned long long* __restrict__ keys, const WsHeader* __restrict__ hdr) {
   __shared__ uint32_t s_cnt[kLocalMax];
   __shared__ uint32_t s_base[kLocalMax];
   if (hdr->status & kStatCapacity) return;
@@ -193,21 +211,10 @@ __global__ void __launch_bounds__(kBinThreads) fill_kernel(
   const LocalBox box = chunk_box(rects, lo, hi);
   const int area = box.w * box.h;
   if (box.ok) {
-    for (int t = threadIdx.x; t < area; t += blockDim.x) s_cnt[t] = 0u;
-    __syncthreads();
-    for (int k = 0; k < (int)(kChunk / kBinThreads); ++k) {
-      const int64_t i = lo + (int64_t)k * kBinThreads + threadIdx.x;
-      ushort4 r = i < hi ? rects[i] : make_ushort4(0, 0, 0, 0);
-      if (big(r)) r = make_ushort4(0, 0, 0, 0);
-      expand_items(r, [&](int, int tx, int ty) { atomicAdd(&s_cnt[box.idx(tx, ty)], 1u); });
-    }
-    __syncthreads();
+    // the runs reserved by the counting pass (same chunk, same box)
+    const uint32_t* base = run_base + (int64_t)blockIdx.x * kLocalMax;
     for (int t = threadIdx.x; t < area; t += blockDim.x) {
-      const uint32_t c = s_cnt[t];
-      if (c) {
-        const int tt = (box.y0 + t / box.w) * gx + box.x0 + t % box.w;
-        s_base[t] = tile_start[tt] + atomicAdd(&tile_fill[tt], c);
-      }
+      s_base[t] = tile_start[(box.y0 + t / box.w) * gx + box.x0 + t % box.w] + base[t];
       s_cnt[t] = 0u;
     }
     __syncthreads();
@@ -244,7 +251,7 @@ __global__ void __launch_bounds__(kBinThreads) fill_kernel(
       const unsigned long long key = __shfl_sync(kFull, my_key, src);
       if (item < total) {
         const int local = item - e_src;
-        const int yy = local / w_src;
+        const int yy = div_small(local, w_src);
         const int tx = (p_src & 0xffff) + (local - yy * w_src), ty = (p_src >> 16) + yy;
         uint32_t pos;
         if ((lmask >> src) & 1u) {
@@ -262,16 +269,21 @@ __global__ void __launch_bounds__(kBinThreads) fill_kernel(
 
 }  // namespace
 
+size_t binning_run_base_bytes(int64_t n) {
+  return sizeof(uint32_t) * (size_t)((n + kChunk - 1) / kChunk) * (size_t)kLocalMax;
+}
+
 cudaError_t launch_binning(const CamArgs& cam, int64_t n, const UpliftWs& ws, int slot,
                            cudaStream_t st) {
   const int ntiles = cam.gx * cam.gy;
   const int blocks = (int)((n + kChunk - 1) / kChunk);
-  if (n > 0) count_kernel<<<blocks, kBinThreads, 0, st>>>(ws.rect, n, cam.gx, ws.tile_count);
-  scan_kernel<<<1, 1024, 0, st>>>(ws.tile_count, ws.tile_start, ws.tile_fill, ntiles, ws.dup_capacity,
-                                  ws.hdr, slot);
+  if (n > 0)
+    count_kernel<<<blocks, kBinThreads, 0, st>>>(ws.rect, n, cam.gx, ws.tile_count, ws.tile_glob, ws.run_base);
+  scan_kernel<<<1, 1024, 0, st>>>(ws.tile_count, ws.tile_glob, ws.tile_start, ws.tile_fill, ntiles,
+                                  ws.dup_capacity, ws.hdr, slot);
   if (n > 0)
     fill_kernel<<<blocks, kBinThreads, 0, st>>>(ws.rect, ws.depth, ws.sp.orig, n, cam.gx, ws.tile_start,
-                                                ws.tile_fill, ws.keys, ws.hdr);
+                                                ws.tile_fill, ws.run_base, ws.keys, ws.hdr);
   g_launches += n > 0 ? 3 : 1;
   return cudaGetLastError();
 }

@@ -61,8 +61,11 @@ __device__ __forceinline__ bool box_may_hit(const ProjRec& r, float x0, float y0
   if (!(qa < 0.0f && qc < 0.0f)) return true;
   const float x1 = x0 + (w - 1.0f), y1 = y0 + (h - 1.0f);
   if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return true;
-  const float kx = -qb / (2.0f * qc);  // argmax over dy along an edge x = const: dy = kx * dx
-  const float ky = -qb / (2.0f * qa);  // argmax over dx along an edge y = const: dx = ky * dy
+  // argmax over dy along an edge x = const (dy = kx * dx) and over dx along an
+  // edge y = const (dx = ky * dy); an approximate quotient only moves the
+  // evaluation point slightly on a flat maximum, far inside the margin below
+  const float kx = __fdividef(-qb, 2.0f * qc);
+  const float ky = __fdividef(-qb, 2.0f * qa);
   float best = -INFINITY;
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
@@ -106,7 +109,9 @@ struct UpliftWs {
   uint32_t* depth;          // [n] float bits of camera depth, spatial order
   ushort4* rect;            // [n] listed tiles (x_lo, y_lo, x_hi, y_hi), spatial order: the 3DGS
                             //     rectangle cut to the alpha >= 1/255 ellipse's box; empty if culled
-  uint32_t* tile_count;     // [max_tiles + 1]
+  uint32_t* tile_count;     // [max_tiles + 1] runs reserved per tile (binning)
+  uint32_t* tile_glob;      // [max_tiles + 1] big-rectangle items per tile (binning)
+  uint32_t* run_base;       // [chunks x box tiles] offset of each binning CTA's run in a tile list
   uint32_t* tile_start;     // [max_tiles + 1]
   uint32_t* tile_fill;      // [max_tiles]
   unsigned long long* keys; // [dup_capacity] (depth bits << 32 | gid)
@@ -149,6 +154,7 @@ size_t reorder_scratch_bytes();
 cudaError_t launch_reorder(const scoup_scene& sc, const UpliftWs& ws, cudaStream_t st);
 cudaError_t launch_preprocess(const scoup_scene& sc, const CamArgs& cam, const UpliftWs& ws,
                               int slot, cudaStream_t st);
+size_t binning_run_base_bytes(int64_t n);
 cudaError_t launch_binning(const CamArgs& cam, int64_t n, const UpliftWs& ws, int slot,
                            cudaStream_t st);
 cudaError_t launch_uplift_tiles(const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* rmap,

@@ -64,6 +64,7 @@ struct TileSmem {
   int stage_g[kThreads / 32][32];
   float part[kMaxSlots][kWin];
   float part_c[kComp ? kMaxSlots : 1][kComp ? kWin : 1];
+  uint32_t nz[kMaxSlots][kWin / 32];  // window entries whose partial became non-zero
   int slot_region[kMaxSlots];
   int slot_idx[kMaxSlots][kMaxS];
   float slot_val[kMaxSlots][kMaxS];
@@ -180,13 +181,13 @@ __device__ __forceinline__ float two_sum_err(float a, float b, float s) {
   return __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
 }
 
-// part[i] += v (shared memory), compensated when kComp.
+// part[i] += v (v > 0, shared memory), compensated when kComp; the first
+// addition into an entry marks it in the non-zero mask nz.
 template <bool kComp>
-__device__ __forceinline__ void part_add(float* part, float* part_c, int i, float v) {
-  if constexpr (!kComp) {
-    atomicAdd(&part[i], v);
-  } else {
-    const float old = atomicAdd(&part[i], v);
+__device__ __forceinline__ void part_add(float* part, float* part_c, uint32_t* nz, int i, float v) {
+  const float old = atomicAdd(&part[i], v);
+  if (old == 0.0f) atomicOr(&nz[i >> 5], 1u << (i & 31));
+  if constexpr (kComp) {
     const float err = two_sum_err(old, v, __fadd_rn(old, v));
     if (err != 0.0f) atomicAdd(&part_c[i], err);
   }
@@ -254,6 +255,7 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
   for (int k = tid; k < kMaxSlots * kWin; k += kThreads) (&sm.part[0][0])[k] = 0.0f;
   if constexpr (kComp)
     for (int k = tid; k < kMaxSlots * kWin; k += kThreads) (&sm.part_c[0][0])[k] = 0.0f;
+  for (int k = tid; k < kMaxSlots * (kWin / 32); k += kThreads) (&sm.nz[0][0])[k] = 0u;
   for (int b = tid; b < kNB; b += kThreads) sm.bcur[b] = 0u;
   if (tid < 4) sm.cnt[tid] = 0ull;
   __syncthreads();
@@ -304,6 +306,11 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
     if (sm.slot_region[q] == region) my_slot = q;
   const bool uniform = __all_sync(kFull, region == __shfl_sync(kFull, region, 0));
   const int wslot = uniform ? my_slot : -1;
+  // slots present among the warp's pixels, and whether some pixel's region got no slot
+  unsigned wslots = 0u;
+  for (int q = 0; q < nslots; ++q)
+    if (__any_sync(kFull, my_slot == q)) wslots |= 1u << q;
+  const bool any_unslotted = __any_sync(kFull, my_slot < 0 && region >= 0);
   __syncthreads();
 
   float T = 1.0f;
@@ -482,32 +489,40 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
 #pragma unroll
         for (int u = 0; u < kGroup; ++u) has |= e[u] > 0.0f;
         if (__any_sync(kFull, has)) {
+          int jq = idx[0];
+#pragma unroll
+          for (int u = 1; u < kGroup; ++u) jq = (lane >> 2) == u ? idx[u] : jq;
           if (wslot >= 0) {
             const float S = transpose_reduce8(e, lane);
-            int jq = idx[0];
-#pragma unroll
-            for (int u = 1; u < kGroup; ++u) jq = (lane >> 2) == u ? idx[u] : jq;
             if ((lane & 3) == 0 && S > 0.0f)
-              part_add<kComp>(sm.part[wslot], sm.part_c[kComp ? wslot : 0], j0 + jq, S);
-          } else if (has) {
+              part_add<kComp>(sm.part[wslot], sm.part_c[kComp ? wslot : 0], sm.nz[wslot], j0 + jq, S);
+          } else {
+            // pixels of several regions: one masked transpose reduction per slot present
+            for (unsigned qm = wslots; qm != 0u; qm &= qm - 1u) {
+              const int q = __ffs(qm) - 1;
+              float v[kGroup];
+#pragma unroll
+              for (int u = 0; u < kGroup; ++u) v[u] = my_slot == q ? e[u] : 0.0f;
+              const float S = transpose_reduce8(v, lane);
+              if ((lane & 3) == 0 && S > 0.0f)
+                part_add<kComp>(sm.part[q], sm.part_c[kComp ? q : 0], sm.nz[q], j0 + jq, S);
+            }
+          }
+          if (any_unslotted && has && my_slot < 0 && region >= 0) {
+            // more regions in this tile than slots: scatter this pixel directly
 #pragma unroll
             for (int u = 0; u < kGroup; ++u) {
               if (!(e[u] > 0.0f)) continue;
-              if (my_slot >= 0) {
-                part_add<kComp>(sm.part[my_slot], sm.part_c[kComp ? my_slot : 0], j0 + idx[u], e[u]);
-              } else if (region >= 0) {
-                // more regions in this tile than slots: scatter this pixel directly
-                const int64_t g = st_g[idx[u]];
-                for (int a = 0; a < s; ++a) {
-                  const int64_t row = (int64_t)region * s + a;
-                  const int jj = code_idx[row];
-                  if (jj >= 0 && jj < C) {
-                    acc_add<kComp>(accum, comp, g * C + jj, code_val[row], e[u], 0.0f);
-                    ++n_atom;
-                  }
+              const int64_t g = st_g[idx[u]];
+              for (int a = 0; a < s; ++a) {
+                const int64_t row = (int64_t)region * s + a;
+                const int jj = code_idx[row];
+                if (jj >= 0 && jj < C) {
+                  acc_add<kComp>(accum, comp, g * C + jj, code_val[row], e[u], 0.0f);
+                  ++n_atom;
                 }
-                ++n_flush;
               }
+              ++n_flush;
             }
           }
         }
@@ -517,23 +532,45 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
     }
     __syncthreads();
     // ---- flush the (region, Gaussian) tile partials of this window ----
-    for (int p = tid; p < m; p += kThreads) {
-      const int64_t g = (int64_t)(sm.win[p] & 0xffffffffull);
-      for (int q = 0; q < nslots; ++q) {
-        const float v = sm.part[q][p];
-        if (v > 0.0f) {
-          const float vc = kComp ? sm.part_c[kComp ? q : 0][kComp ? p : 0] : 0.0f;
-          for (int a = 0; a < s; ++a) {
-            const int jj = sm.slot_idx[q][a];
-            if (jj >= 0) { acc_add<kComp>(accum, comp, g * C + jj, sm.slot_val[q][a], v, vc); ++n_atom; }
+    // Only the entries marked in nz are visited.  A warp takes one 32-entry
+    // mask word at a time and 32 / min(s, 32) of its set entries per step;
+    // each lane issues the atomics of one code entry.  (Numbering the set
+    // entries across all warps balances better but costs more per entry:
+    // measured slower.)  Visited entries are cleared here, the mask below.
+    const int nwords = (m + 31) >> 5;
+    const int nw = nslots * nwords;
+    {
+      const int lanes_per = s < 32 ? s : 32;
+      const int per = 32 / lanes_per;
+      const int sub = lane / lanes_per, a0 = lane - sub * lanes_per;
+      for (int wi = warp; wi < nw; wi += kThreads / 32) {
+        const int q = wi / nwords, w = wi - q * nwords;
+        unsigned bits = sm.nz[q][w];
+        while (bits != 0u) {
+          const int take = min(per, __popc(bits));
+          const int p = sub < take ? w * 32 + (int)__fns(bits, 0, sub + 1) : -1;
+          for (int t = 0; t < take; ++t) bits &= bits - 1u;
+          const float v = p >= 0 ? sm.part[q][p] : 0.0f;
+          const float vc = (kComp && p >= 0) ? sm.part_c[kComp ? q : 0][kComp ? p : 0] : 0.0f;
+          __syncwarp();
+          if (p >= 0) {
+            if (a0 == 0) {
+              sm.part[q][p] = 0.0f;
+              if constexpr (kComp) sm.part_c[q][p] = 0.0f;
+              ++n_flush;
+            }
+            const int64_t g = (int64_t)(sm.win[p] & 0xffffffffull);
+            for (int a = a0; a < s; a += lanes_per) {
+              const int jj = sm.slot_idx[q][a];
+              if (jj >= 0) { acc_add<kComp>(accum, comp, g * C + jj, sm.slot_val[q][a], v, vc); ++n_atom; }
+            }
           }
-          ++n_flush;
-          sm.part[q][p] = 0.0f;
-          if constexpr (kComp) sm.part_c[q][p] = 0.0f;
         }
       }
     }
     all_done = __syncthreads_and(done) != 0;
+    // the mask words were read by every warp above: clear them for the next window
+    for (int wi = tid; wi < nw; wi += kThreads) sm.nz[wi / nwords][wi % nwords] = 0u;
 
     // ---- advance to the next window ----
     if (in_split) {
