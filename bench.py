@@ -49,6 +49,8 @@ def parse_args():
                     help="views of the 1920x1080 render + decode measurement (0 = skip)")
     ap.add_argument("--batch-scenes", type=int, default=16,
                     help="scenes of the batched-uplift measurement (0 = skip)")
+    ap.add_argument("--decode-rows", type=int, default=0,
+                    help="only time the bf16 decode GEMM on this many rows of codes (C=256, D=512) and exit")
     return ap.parse_args()
 
 
@@ -561,8 +563,49 @@ def batched_leg(args, dist, dev):
     }
 
 
+def decode_only(args):
+    """The decode GEMM alone on `--decode-rows` rows of seeded sparse bf16 codes
+    (C = 256 atoms, D = 512): a small case for kernel profiles."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2605_13600_gb300 as gb
+    from paper_2605_13600_gb300 import build as gbuild
+    gbuild.build()
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(4)
+    P, C, D = args.decode_rows, 256, 512
+    codebook = torch.from_numpy(synth.unit_rows(rng, C, D)).to(dev)
+    codes = torch.zeros((P, C), dtype=torch.float32, device=dev)
+    idx = torch.randint(0, C, (P, 8), device=dev, generator=torch.Generator(device=dev).manual_seed(4))
+    codes.scatter_(1, idx, torch.rand((P, 8), device=dev, generator=torch.Generator(device=dev).manual_seed(5)))
+    codes = codes.to(torch.bfloat16)
+    feats = torch.empty((P, D), dtype=torch.bfloat16, device=dev)
+    n2 = torch.empty((P,), dtype=torch.float32, device=dev)
+    ws = torch.empty(gb.scoup_decode_workspace_size(P, C, D), dtype=torch.uint8, device=dev)
+    for _ in range(max(3, args.warmup)):
+        gb.scoup_decode(codes, codebook, feats, n2, workspace=ws)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        gb.scoup_decode(codes, codebook, feats, n2, workspace=ws)
+    ev1.record()
+    torch.cuda.synchronize()
+    if gb.scoup_read_stats(ws)["status"] != 0:
+        raise RuntimeError("decode status")
+    t = ev0.elapsed_time(ev1) / 1e3 / args.steps
+    nbytes = 2.0 * P * (C + D)
+    print(json.dumps({"decode_rows": P, "ms_per_launch": t * 1e3, "gbs": nbytes / t / 1e9,
+                      "tflops": 2.0 * P * C * D / t / 1e12}), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.decode_rows > 0:
+        decode_only(args)
+        return
     dist = Dist()
     try:
         if args.impl == "reference":
