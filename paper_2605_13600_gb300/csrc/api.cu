@@ -395,7 +395,7 @@ int scoup_render(const scoup_scene* scene, const int32_t* topk_idx, const float*
   if (!out_codes) return fail(SCOUP_ERR_INVALID_ARG, "out_codes is NULL");
   if (scene->n > 0 && (!topk_idx || !topk_val)) return fail(SCOUP_ERR_INVALID_ARG, "Top-K arrays are NULL");
   if (!workspace) return fail(SCOUP_ERR_INVALID_ARG, "workspace is NULL");
-  if (render_smem_bytes(C) > 227 * 1024)
+  if (render_smem_bytes(C, K) > 227 * 1024)
     return fail(SCOUP_ERR_INVALID_ARG, "C=%d needs more shared memory than a CTA has", C);
   const size_t fixed = uplift_fixed_bytes(scene->n, max_tiles, 0);
   if (ws_bytes < fixed)

@@ -160,7 +160,7 @@ cudaError_t launch_binning(const CamArgs& cam, int64_t n, const UpliftWs& ws, in
 cudaError_t launch_uplift_tiles(const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* rmap,
                                 int32_t R_total, const int32_t* code_idx, const float* code_val,
                                 int s, int C, float* accum, float* comp, int warp_w, cudaStream_t st);
-size_t render_smem_bytes(int C);
+size_t render_smem_bytes(int C, int K);
 cudaError_t launch_render_tiles(const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* topk_idx,
                                 const float* topk_val, int K, int C, float* out, float* out_T,
                                 int32_t* out_last, cudaStream_t st);
