@@ -47,6 +47,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU oracle sample budget")
     ap.add_argument("--render-views", type=int, default=8,
                     help="views of the 1920x1080 render + decode measurement (0 = skip)")
+    ap.add_argument("--dense-views", type=int, default=20,
+                    help="views of the dense (D=512) vs sparse uplift comparison (0 = skip)")
     ap.add_argument("--batch-scenes", type=int, default=16,
                     help="scenes of the batched-uplift measurement (0 = skip)")
     ap.add_argument("--decode-rows", type=int, default=0,
@@ -363,6 +365,10 @@ def run_gb300(args, dist):
     if args.render_views > 0:
         rd = render_decode_leg(args, dist, wl, up, dev, pk)
 
+    dn = None
+    if args.dense_views > 0:
+        dn = dense_leg(args, dist, wl, up, dev)
+
     bt = None
     if args.batch_scenes > 0:
         del up
@@ -385,6 +391,7 @@ def run_gb300(args, dist):
             "clocks": clk, "phase_ms_per_step": step_ms,
             "stats": {k: st0[k] for k in ("visible", "duplicates", "flushes", "atomics")},
             "render_decode": rd,
+            "dense_vs_sparse": dn,
             "batched": bt,
         }
         print(json.dumps(line), flush=True)
@@ -487,6 +494,43 @@ def render_decode_leg(args, dist, wl, up, dev, pk):
                                             "frac": flops / t_gemm / 1e12 / pk["bf16_tflops"]},
                             "peak_source": pk["source"] + " (HBM copy; bf16 burst)"},
     }
+
+
+def dense_leg(args, dist, wl, up, dev):
+    """Secondary measurement: the dense feature uplift of Eq. 3 (a 512-d unit
+    feature per region, plus the normaliser Z) against the sparse uplift
+    (s = 8 entries per region) on the same views, both accumulate-only: the
+    time ratio the paper's O(|S_i| D) -> O(|S_i| K) argument predicts."""
+    import torch
+
+    import synth
+    import paper_2605_13600_gb300 as gb
+
+    views = range(min(args.dense_views, len(up.cams)))
+    dwl = synth.dense_feature_codes(wl, D=512, seed=7)
+    dup = gb.Uplift(dwl, device=str(dev), topk=False)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    for name, u in (("sparse_s8", up), ("dense_d512", dup)):
+        st = u.run(stats=True, views=views, topk=False)
+        if st["status"] != 0:
+            raise RuntimeError(f"{name} status {st['status']}")
+        u.run(stats=False, views=views, topk=False)
+        torch.cuda.synchronize()
+        dist.barrier()
+        ev0.record(stream)
+        for _ in range(2):
+            u.run(stats=False, views=views, topk=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t = dist.max(ev0.elapsed_time(ev1) / 1e3 / 2)
+        out[name] = {"ms": t * 1e3, "contributions_per_s": dist.world * st["contributions"] / t,
+                     "accumulator_atomics": st["atomics"], "entries_per_region": u.s}
+    del dup
+    torch.cuda.empty_cache()
+    return {"views": len(views), "workload": WORKLOAD, "accumulate_only": True, **out,
+            "time_ratio_dense_over_sparse": out["dense_d512"]["ms"] / out["sparse_s8"]["ms"]}
 
 
 def batched_leg(args, dist, dev):

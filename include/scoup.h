@@ -129,8 +129,13 @@ int scoup_uplift_plan(const scoup_scene* scene, const scoup_camera* cams, int32_
  *  workspace    device scratch of ws_bytes >= scoup_uplift_workspace_size().
  *  stats        HOST scoup_stats* or NULL; when given, the call synchronises
  *               `stream` and returns the device status.
- * Limits: 1 <= K <= C <= 1024, 1 <= s <= 64, V >= 0, n >= 0 (n = 0 and V = 0
- * are valid and produce empty / padded outputs). */
+ * Limits: 1 <= K <= C <= 1024, 1 <= s <= 1024, V >= 0, n >= 0 (n = 0 and V = 0
+ * are valid and produce empty / padded outputs).
+ *
+ * Dense feature uplift (Eq. 3, the formulation sparse coding replaces) is the
+ * same call with each region's D-dimensional feature as its code: C = s = K =
+ * D + 1, code_idx[r] = (0, 1, ..., D), code_val[r] = (F_r, 1), topk_idx NULL;
+ * then f_i = accum[i][0:D] / accum[i][D] (accum[i][D] = Z_i). */
 int scoup_uplift(const scoup_scene* scene, const scoup_camera* cams, int32_t V,
                  const int32_t* region_maps, const int64_t* map_offsets, int32_t R_total,
                  const int32_t* code_idx, const float* code_val, int32_t s, int32_t C, int32_t K,

@@ -223,7 +223,7 @@ int uplift_call(const UpliftCall& c, void* workspace, size_t ws_bytes, int warp_
   if ((rc = check_cams(cams, V, &max_tiles))) return rc;
   if (C < 1 || C > 1024) return fail(SCOUP_ERR_INVALID_ARG, "C=%d outside [1, 1024]", C);
   if (K < 1 || K > C) return fail(SCOUP_ERR_INVALID_ARG, "K=%d outside [1, C=%d]", K, C);
-  if (s < 1 || s > 64) return fail(SCOUP_ERR_INVALID_ARG, "s=%d outside [1, 64]", s);
+  if (s < 1 || s > 1024) return fail(SCOUP_ERR_INVALID_ARG, "s=%d outside [1, 1024]", s);
   if (R_total < 0) return fail(SCOUP_ERR_INVALID_ARG, "R_total=%d < 0", R_total);
   if (accum_mode & ~(SCOUP_ACCUM_CONTINUE | SCOUP_ACCUM_COMPENSATED))
     return fail(SCOUP_ERR_INVALID_ARG, "accum_mode=%d: only SCOUP_ACCUM_CONTINUE and SCOUP_ACCUM_COMPENSATED", accum_mode);

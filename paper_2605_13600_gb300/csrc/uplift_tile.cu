@@ -54,7 +54,8 @@ constexpr int kWin = 256;
 constexpr int kLogNB = 10;
 constexpr int kNB = 1 << kLogNB;
 constexpr int kMaxSlots = 4;
-constexpr int kMaxS = 64;
+constexpr int kMaxS = 64;  // codes of up to kMaxS entries are staged in shared memory; longer
+                           // ones (dense features, Eq. 3) are read from the code table in the flush
 constexpr int kGroup = 8;
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -297,7 +298,7 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
     if (tid == kThreads - 1) sm.bstart[kNB] = run;
   }
   const int nslots = sm.nslots;
-  for (int k = tid; k < nslots * s; k += kThreads) {
+  for (int k = tid; k < (s <= kMaxS ? nslots * s : 0); k += kThreads) {
     const int q = k / s, a = k - q * s;
     const int64_t row = (int64_t)sm.slot_region[q] * s + a;
     int j = code_idx[row];
@@ -565,8 +566,18 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
             }
             const int64_t g = (int64_t)(sm.win[p] & 0xffffffffull);
             for (int a = a0; a < s; a += lanes_per) {
-              const int jj = sm.slot_idx[q][a];
-              if (jj >= 0) { acc_add<kComp>(accum, comp, g * C + jj, sm.slot_val[q][a], v, vc); ++n_atom; }
+              int jj;
+              float cval;
+              if (s <= kMaxS) {
+                jj = sm.slot_idx[q][a];
+                cval = sm.slot_val[q][a];
+              } else {
+                const int64_t row = (int64_t)sm.slot_region[q] * s + a;
+                jj = code_idx[row];
+                cval = code_val[row];
+                if (jj >= C) { atomicOr(&hdr->status, kStatDeviceCheck); jj = -1; }
+              }
+              if (jj >= 0) { acc_add<kComp>(accum, comp, g * C + jj, cval, v, vc); ++n_atom; }
             }
           }
         }

@@ -350,7 +350,7 @@ class Uplift:
     """
 
     def __init__(self, wl, device: str = "cuda", dup_capacity: Optional[int] = None,
-                 headroom: float = 1.0, compensated: bool = False):
+                 headroom: float = 1.0, compensated: bool = False, topk: bool = True):
         import torch
         dev = torch.device(device)
         sc = wl.scene
@@ -382,17 +382,20 @@ class Uplift:
         self.compensated = bool(compensated)
         self.accum = torch.empty(((2, n, self.C) if compensated else (n, self.C)), dtype=torch.float32,
                                  device=dev)
-        self.topk_idx = torch.empty((n, self.K), dtype=torch.int32, device=dev)
-        self.topk_val = torch.empty((n, self.K), dtype=torch.float32, device=dev)
+        self.topk_idx = torch.empty((n, self.K), dtype=torch.int32, device=dev) if topk else None
+        self.topk_val = torch.empty((n, self.K), dtype=torch.float32, device=dev) if topk else None
 
-    def run(self, stats: bool = True, accum_mode: int = 0, views=None, stream=None):
+    def run(self, stats: bool = True, accum_mode: int = 0, views=None, stream=None, topk: bool = True):
+        """One uplift; topk=False (or an Uplift built with topk=False) accumulates only."""
+        topk = topk and self.topk_idx is not None
         cams = self.cams if views is None else [self.cams[v] for v in views]
         offs = self.map_offsets if views is None else self.map_offsets[list(views)]
         if self.compensated:
             accum_mode |= SCOUP_ACCUM_COMPENSATED
         return scoup_uplift(self.scene, cams, self.region_maps, offs, self.R_total, self.code_idx,
                             self.code_val, self.s, self.C, self.K, self.accum, accum_mode,
-                            self.topk_idx, self.topk_val, self.workspace, stats=stats, stream=stream)
+                            self.topk_idx if topk else None, self.topk_val if topk else None,
+                            self.workspace, stats=stats, stream=stream)
 
     def accum_value(self):
         """The accumulator [n, C] (sum + compensation in the compensated form)."""

@@ -33,7 +33,7 @@ __all__ = [
     "gaussians", "look_at", "camera_at", "fibonacci_cameras", "band_cameras",
     "voronoi_map", "region_codes", "sparse_topk_codes", "unit_rows",
     "tiny_workload", "uplift_cfg1", "uplift_cfg2", "uplift_cfg3_scene",
-    "render_cfg4", "render_cfg5",
+    "render_cfg4", "render_cfg5", "dense_feature_codes",
 ]
 
 
@@ -231,6 +231,23 @@ def unit_rows(rng: np.random.Generator, rows: int, dim: int) -> np.ndarray:
     x = rng.normal(0.0, 1.0, size=(rows, dim))
     x /= np.linalg.norm(x, axis=1, keepdims=True)
     return x.astype(np.float32)
+
+
+def dense_feature_codes(wl: "UpliftWorkload", D: int = 512, seed: int = 7) -> "UpliftWorkload":
+    """The same views and regions with a dense D-dimensional unit feature per
+    region (a synthetic stand-in for per-mask CLIP features) written as a code
+    over C = D + 1 atoms: atoms 0..D-1 carry the feature, atom D carries 1, so
+    an accumulate-only uplift gives sum e F in columns 0..D-1 and Z in column D
+    (dense feature uplift, Eq. 3, as the same aggregation)."""
+    rng = np.random.default_rng(seed)
+    R = int(wl.code_idx.shape[0])
+    feats = unit_rows(rng, R, D)
+    ci = np.tile(np.arange(D + 1, dtype=np.int32), (R, 1))
+    cv = np.concatenate([feats, np.ones((R, 1), np.float32)], axis=1)
+    out = UpliftWorkload(f"{wl.name}_dense{D}", wl.scene, wl.cams, wl.region_maps, wl.map_offsets,
+                         ci, cv, D + 1, D + 1, D + 1, wl.regions_per_view)
+    out.region_features = feats
+    return out
 
 
 def _draw_seeds(rng, cams, R_per_view):
