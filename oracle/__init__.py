@@ -92,6 +92,12 @@ def _load():
         lib.orc_decode.restype = None
         lib.orc_similarity.argtypes = [P, i64, i32, P, i32, P]
         lib.orc_similarity.restype = None
+        lib.orc_entropy.argtypes = [P, i64, i32, P]
+        lib.orc_entropy.restype = None
+        lib.orc_entropy_filter.argtypes = [P, i64, i64, P]
+        lib.orc_entropy_filter.restype = None
+        lib.orc_relevancy.argtypes = [P, P, i64, i32, ct.c_double, P]
+        lib.orc_relevancy.restype = None
         lib.orc_render_backward.argtypes = [P, P, P, P, i64, P, P, i32, i32, ct.POINTER(Camera),
                                             P, P, P]
         lib.orc_render_backward.restype = i32
@@ -237,6 +243,35 @@ def similarity(F: np.ndarray, text: np.ndarray) -> np.ndarray:
     out = np.zeros((P, Q), np.float64)
     lib.orc_similarity(_p(Fm), P, D, _p(t), Q, _p(out))
     return out.reshape(F.shape[:-1] + (Q,))
+
+
+def entropy(acc: np.ndarray) -> np.ndarray:
+    """H_i = -sum p log p of each row's positive coefficients (0 for empty rows)."""
+    lib = _load()
+    a = _f64(acc)
+    n, C = a.shape
+    H = np.zeros(n, np.float64)
+    lib.orc_entropy(_p(a), n, C, _p(H))
+    return H
+
+
+def entropy_filter(H: np.ndarray, keep: int) -> np.ndarray:
+    """uint8 mask of the `keep` lowest-entropy rows (ties to the lower index)."""
+    lib = _load()
+    h = _f64(H)
+    m = np.zeros(h.shape[0], np.uint8)
+    lib.orc_entropy_filter(_p(h), h.shape[0], int(keep), _p(m))
+    return m
+
+
+def relevancy(s_query: np.ndarray, s_canon: np.ndarray, alpha: float = 10.0) -> np.ndarray:
+    """Eq. 9 relevancy from query similarities [P] and canonical similarities [P, k]."""
+    lib = _load()
+    q = _f64(s_query).reshape(-1)
+    c = _f64(s_canon).reshape(q.shape[0], -1)
+    R = np.zeros(q.shape[0], np.float64)
+    lib.orc_relevancy(_p(q), _p(c), q.shape[0], c.shape[1], float(alpha), _p(R))
+    return R
 
 
 def render_backward(scene, topk_idx, topk_val, C: int, cam, dL_dWhat: np.ndarray):

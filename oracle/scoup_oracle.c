@@ -851,3 +851,62 @@ int orc_render_backward(const float* means, const float* scales, const float* qu
 }
 
 void orc_free(void* p) { free(p); }
+
+/* ---- entropy of the coefficient distribution, entropy filter ---------- */
+
+void orc_entropy(const double* acc, int64_t n, int C, double* H)
+{
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    const double* w = acc + i * C;
+    double total = 0.0;
+    for (int l = 0; l < C; ++l)
+      if (w[l] > 0.0) total += w[l];
+    double h = 0.0;
+    if (total > 0.0)
+      for (int l = 0; l < C; ++l)
+        if (w[l] > 0.0) {
+          const double pl = w[l] / total;
+          h -= pl * log(pl);
+        }
+    H[i] = h;
+  }
+}
+
+static const double* g_filter_H;
+
+static int cmp_entropy_rank(const void* pa, const void* pb)
+{
+  const int64_t a = *(const int64_t*)pa, b = *(const int64_t*)pb;
+  if (g_filter_H[a] < g_filter_H[b]) return -1;
+  if (g_filter_H[a] > g_filter_H[b]) return 1;
+  return (a > b) - (a < b);
+}
+
+void orc_entropy_filter(const double* H, int64_t n, int64_t keep, unsigned char* keep_mask)
+{
+  int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  for (int64_t i = 0; i < n; ++i) order[i] = i;
+  g_filter_H = H;
+  qsort(order, (size_t)n, sizeof(int64_t), cmp_entropy_rank);
+  for (int64_t i = 0; i < n; ++i) keep_mask[i] = 0;
+  for (int64_t r = 0; r < keep && r < n; ++r) keep_mask[order[r]] = 1;
+  free(order);
+}
+
+/* ---- relevancy score (App. B) ------------------------------------------ */
+
+void orc_relevancy(const double* s_query, const double* s_canon, int64_t P, int n_canon, double alpha,
+                   double* R)
+{
+  for (int64_t p = 0; p < P; ++p) {
+    const double eq = exp(alpha * s_query[p]);
+    double r = 1.0;
+    for (int k = 0; k < n_canon; ++k) {
+      const double ek = exp(alpha * s_canon[p * n_canon + k]);
+      const double v = eq / (eq + ek);
+      if (v < r) r = v;
+    }
+    R[p] = r;
+  }
+}

@@ -109,6 +109,21 @@ void orc_decode(const double* What, int64_t P, int C, const float* codebook, int
 /* Cosine similarity of F[P*D] rows with text[Q*D] rows; 0 where |F| < 1e-12. */
 void orc_similarity(const double* F, int64_t P, int D, const float* text, int Q, double* out);
 
+/* Entropy of each Gaussian's coefficient distribution (the entropy analysis
+ * of Top-K filtering): with p_l = w_l / sum_l w_l over the positive entries of
+ * row i, H_i = -sum_l p_l log p_l; a row with no positive entry gets 0. */
+void orc_entropy(const double* acc, int64_t n, int C, double* H);
+
+/* Entropy filter: keep[i] = 1 for the `keep` rows of lowest entropy (ties to
+ * the lower index), 0 for the others. */
+void orc_entropy_filter(const double* H, int64_t n, int64_t keep, unsigned char* keep_mask);
+
+/* Relevancy score of a query (App. B, Eq. 9): for each pixel p,
+ * R(p) = min_k e^{a s_q} / (e^{a s_q} + e^{a s_k}) with s_q the similarity to the
+ * query and s_k the similarities to the n_canon canonical phrases, a = alpha. */
+void orc_relevancy(const double* s_query, const double* s_canon, int64_t P, int n_canon, double alpha,
+                   double* R);
+
 /* Gradient through Eq. 7 of a loss with dL/dWhat given per pixel:
  * d_val[n*K] += sum_p e_i(p) g_p[idx_ik];
  * d_opacity[n] += sum_p dalpha/do * (T_i (g_p . w_i) - S_after / (1 - alpha_i)). */
