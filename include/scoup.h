@@ -188,6 +188,37 @@ int scoup_render_backward(const scoup_scene* scene, const int32_t* topk_idx, con
                           float* d_topk_val, float* d_opacity, void* workspace, size_t ws_bytes,
                           scoup_stats* stats, void* stream);
 
+/* Top-K + L1 normalisation (Eq. 6) as scoup_topk, fused with the entropy of
+ * each row's coefficient distribution (the entropy analysis of Top-K
+ * filtering): with p_l = w_l / sum w over the positive entries,
+ * entropy[i] = -sum_l p_l log p_l (0 for a row with no positive entry).
+ *  comp      DEVICE float32 [n, C] compensation terms of a compensated uplift
+ *            (the second half of its accum), or NULL.
+ *  entropy   DEVICE float32 [n].  Asynchronous. */
+int scoup_topk_entropy(const float* accum, const float* comp, int64_t n, int32_t C, int32_t K, int32_t* topk_idx,
+                       float* topk_val, float* entropy, void* stream);
+
+/* Entropy filter: keeps the `keep` Gaussians of lowest entropy (ties to the
+ * lower index) and clears the Top-K rows of all others to (-1, 0).
+ *  entropy    DEVICE float32 [n] (e.g. from scoup_topk_entropy).
+ *  topk_idx, topk_val  DEVICE [n, K], modified in place, or both NULL.
+ *  keep_mask  DEVICE uint8 [n] (1 kept, 0 removed) or NULL.
+ *  workspace  DEVICE, >= scoup_entropy_filter_workspace_size() bytes.
+ * Exact selection in 8 histogram passes whose digits are read back on the
+ * host: the call synchronises `stream`. */
+size_t scoup_entropy_filter_workspace_size(void);
+int scoup_entropy_filter(const float* entropy, int64_t n, int64_t keep, int32_t K, int32_t* topk_idx,
+                         float* topk_val, uint8_t* keep_mask, void* workspace, size_t ws_bytes, void* stream);
+
+/* Relevancy score of text queries (App. B, Eq. 9):
+ *   R[p][q] = min_k exp(a s_q) / (exp(a s_q) + exp(a s_k))
+ * from the similarities sim [P, ncols] (scoup_similarity output) whose first
+ * n_canon columns are the canonical phrases and the other ncols - n_canon the
+ * queries; a = alpha (10 in the paper).  R DEVICE float32 [P, ncols - n_canon].
+ * Asynchronous. */
+int scoup_relevancy(const float* sim, int64_t P, int32_t ncols, int32_t n_canon, float alpha, float* R,
+                    void* stream);
+
 /* ------------------------------------------------------------------ */
 /* Batched uplift: many scenes with their own views, one graph launch   */
 /* ------------------------------------------------------------------ */

@@ -98,6 +98,10 @@ PROTOS = {
     "scoup_similarity_workspace_size": (SZ, [I64, I32, I32]),
     "scoup_similarity": (ct.c_int, [P, I64, I32, P, P, I32, P, P, SZ, P]),
     "scoup_decode_fp32": (ct.c_int, [P, I64, I32, P, I32, P, P]),
+    "scoup_topk_entropy": (ct.c_int, [P, P, I64, I32, I32, P, P, P, P]),
+    "scoup_entropy_filter_workspace_size": (SZ, []),
+    "scoup_entropy_filter": (ct.c_int, [P, I64, I64, I32, P, P, P, P, SZ, P]),
+    "scoup_relevancy": (ct.c_int, [P, I64, I32, I32, ct.c_float, P, P]),
     "scoup_similarity_fp32": (ct.c_int, [P, I64, I32, P, I32, P, P, SZ, P]),
     "scoup_uplift_noalloc_max_bytes": (SZ, []),
     "scoup_uplift_noalloc": (ct.c_int, [ct.POINTER(Scene), P, I32, P, P, I32, P, P, I32, I32, I32, P, I32,

@@ -291,7 +291,7 @@ int uplift_call(const UpliftCall& c, void* workspace, size_t ws_bytes, int warp_
   }
   if (topk_idx && n > 0) {
     PhaseScope ps(SCOUP_PHASE_TOPK, st);
-    if ((e = launch_topk(accum, comp, n, C, K, topk_idx, topk_val, st)) != cudaSuccess)
+    if ((e = launch_topk(accum, comp, n, C, K, topk_idx, topk_val, nullptr, st)) != cudaSuccess)
       return cuda_fail(e, "top-k");
   }
   if (hdr_out) *hdr_out = ws.hdr;
@@ -636,8 +636,46 @@ int scoup_topk(const float* accum, int64_t n, int32_t C, int32_t K, int32_t* top
   if (K < 1 || K > C) return fail(SCOUP_ERR_INVALID_ARG, "K=%d outside [1, C=%d]", K, C);
   if (n > 0 && (!accum || !topk_idx || !topk_val)) return fail(SCOUP_ERR_INVALID_ARG, "NULL array");
   PhaseScope ps(SCOUP_PHASE_TOPK, (cudaStream_t)stream);
-  cudaError_t e = launch_topk(accum, nullptr, n, C, K, topk_idx, topk_val, (cudaStream_t)stream);
+  cudaError_t e = launch_topk(accum, nullptr, n, C, K, topk_idx, topk_val, nullptr, (cudaStream_t)stream);
   return e == cudaSuccess ? SCOUP_OK : cuda_fail(e, "top-k");
+}
+
+int scoup_topk_entropy(const float* accum, const float* comp, int64_t n, int32_t C, int32_t K, int32_t* topk_idx,
+                       float* topk_val, float* entropy, void* stream) {
+  if (n < 0) return fail(SCOUP_ERR_INVALID_ARG, "n < 0");
+  if (C < 1 || C > 1024) return fail(SCOUP_ERR_INVALID_ARG, "C=%d outside [1, 1024]", C);
+  if (K < 1 || K > C) return fail(SCOUP_ERR_INVALID_ARG, "K=%d outside [1, C=%d]", K, C);
+  if (n > 0 && (!accum || !topk_idx || !topk_val || !entropy)) return fail(SCOUP_ERR_INVALID_ARG, "NULL array");
+  PhaseScope ps(SCOUP_PHASE_TOPK, (cudaStream_t)stream);
+  cudaError_t e = launch_topk(accum, comp, n, C, K, topk_idx, topk_val, entropy, (cudaStream_t)stream);
+  return e == cudaSuccess ? SCOUP_OK : cuda_fail(e, "top-k + entropy");
+}
+
+size_t scoup_entropy_filter_workspace_size(void) { return 1024; }
+
+int scoup_entropy_filter(const float* entropy, int64_t n, int64_t keep, int32_t K, int32_t* topk_idx,
+                         float* topk_val, uint8_t* keep_mask, void* workspace, size_t ws_bytes, void* stream) {
+  if (n < 0 || n > 0x7fffffffLL) return fail(SCOUP_ERR_INVALID_ARG, "n=%lld outside [0, 2^31)", (long long)n);
+  if (keep < 0) return fail(SCOUP_ERR_INVALID_ARG, "keep < 0");
+  if ((topk_idx == nullptr) != (topk_val == nullptr))
+    return fail(SCOUP_ERR_INVALID_ARG, "topk_idx and topk_val must both be given or both be NULL");
+  if (topk_idx && K < 1) return fail(SCOUP_ERR_INVALID_ARG, "K < 1");
+  if (n > 0 && !entropy) return fail(SCOUP_ERR_INVALID_ARG, "entropy is NULL");
+  if (!workspace || ws_bytes < scoup_entropy_filter_workspace_size())
+    return fail(SCOUP_ERR_OOM, "workspace too small: need %zu bytes", scoup_entropy_filter_workspace_size());
+  if (n == 0) return SCOUP_OK;
+  return entropy_filter_run(entropy, n, keep, K, topk_idx, topk_val, keep_mask, (uint32_t*)workspace,
+                            (cudaStream_t)stream);
+}
+
+int scoup_relevancy(const float* sim, int64_t P, int32_t ncols, int32_t n_canon, float alpha, float* R,
+                    void* stream) {
+  if (P < 0) return fail(SCOUP_ERR_INVALID_ARG, "P < 0");
+  if (n_canon < 1 || ncols <= n_canon) return fail(SCOUP_ERR_INVALID_ARG, "need 1 <= n_canon < ncols");
+  if (P > 0 && (!sim || !R)) return fail(SCOUP_ERR_INVALID_ARG, "NULL array");
+  PhaseScope ps(SCOUP_PHASE_SIMILARITY, (cudaStream_t)stream);
+  cudaError_t e = launch_relevancy(sim, P, ncols, n_canon, alpha, R, (cudaStream_t)stream);
+  return e == cudaSuccess ? SCOUP_OK : cuda_fail(e, "relevancy");
 }
 
 int scoup_read_stats(const void* workspace, size_t ws_bytes, scoup_stats* stats, void* stream) {

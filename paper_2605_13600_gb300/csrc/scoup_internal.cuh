@@ -187,7 +187,11 @@ cudaError_t launch_sgemm(const float* A, const float* B, bool b_transposed, floa
                          const float* rownorm2, const float* colnorm2, cudaStream_t st);
 cudaError_t launch_row_norm2_f32(const float* X, int64_t R, int D, float* out, cudaStream_t st);
 cudaError_t launch_topk(const float* accum, const float* comp, int64_t n, int C, int K, int32_t* idx, float* val,
-                        cudaStream_t st);
+                        float* entropy, cudaStream_t st);
+int entropy_filter_run(const float* H, int64_t n, int64_t keep, int K, int32_t* idx, float* val, uint8_t* mask,
+                       uint32_t* hist, cudaStream_t st);
+cudaError_t launch_relevancy(const float* sim, int64_t P, int ncols, int n_canon, float alpha, float* R,
+                             cudaStream_t st);
 cudaError_t launch_code_topk(const int32_t* ci, const float* cv, int64_t R, int s, int K,
                              int32_t* ci_out, float* cv_out, cudaStream_t st);
 

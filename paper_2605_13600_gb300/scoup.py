@@ -318,6 +318,45 @@ def scoup_similarity_fp32(features, text, out, workspace=None, stream=None):
     return workspace
 
 
+def scoup_topk_entropy(accum, K: int, topk_idx, topk_val, entropy, comp=None, stream=None) -> None:
+    """Eq. 6 Top-K of accum [n, C] plus the entropy [n] of every row's coefficients."""
+    import torch
+    for t, nm in ((accum, "accum"), (topk_val, "topk_val"), (entropy, "entropy"), (comp, "comp")):
+        _need(t, torch.float32, nm)
+    _need(topk_idx, torch.int32, "topk_idx")
+    n, C = accum.shape
+    check(load().scoup_topk_entropy(_ptr(accum), _ptr(comp), n, C, int(K), _ptr(topk_idx), _ptr(topk_val),
+                                    _ptr(entropy), _stream(stream)))
+
+
+def scoup_entropy_filter(entropy, keep: int, topk_idx=None, topk_val=None, keep_mask=None, workspace=None,
+                         stream=None):
+    """Keep the `keep` lowest-entropy Gaussians; clear the others' Top-K rows (synchronises)."""
+    import torch
+    _need(entropy, torch.float32, "entropy")
+    _need(topk_idx, torch.int32, "topk_idx")
+    _need(topk_val, torch.float32, "topk_val")
+    _need(keep_mask, torch.uint8, "keep_mask")
+    if workspace is None:
+        workspace = torch.empty(int(load().scoup_entropy_filter_workspace_size()), dtype=torch.uint8,
+                                device=entropy.device)
+    K = int(topk_idx.shape[1]) if topk_idx is not None else 0
+    check(load().scoup_entropy_filter(_ptr(entropy), entropy.numel(), int(keep), K, _ptr(topk_idx),
+                                      _ptr(topk_val), _ptr(keep_mask), _ptr(workspace), workspace.numel(),
+                                      _stream(stream)))
+
+
+def scoup_relevancy(sim, n_canon: int, R, alpha: float = 10.0, stream=None) -> None:
+    """Eq. 9 relevancy R [P, ncols - n_canon] from similarities sim [P, ncols] (canonical columns first)."""
+    import torch
+    _need(sim, torch.float32, "sim")
+    _need(R, torch.float32, "R")
+    P, ncols = sim.shape
+    if tuple(R.shape) != (P, ncols - n_canon):
+        raise ValueError("R must be [P, ncols - n_canon]")
+    check(load().scoup_relevancy(_ptr(sim), P, ncols, int(n_canon), float(alpha), _ptr(R), _stream(stream)))
+
+
 def scoup_read_stats(workspace, stream=None) -> dict:
     st = Stats()
     check(load().scoup_read_stats(_ptr(workspace), workspace.numel(), ct.byref(st), _stream(stream)))
@@ -505,4 +544,4 @@ __all__ = ["ScoupError", "SCOUP_ACCUM_CONTINUE", "SCOUP_ACCUM_COMPENSATED", "sce
            "scoup_render", "scoup_render_backward", "Render", "Uplift",
            "scoup_decode_workspace_size", "scoup_decode", "scoup_similarity_workspace_size",
            "scoup_similarity", "scoup_decode_fp32", "scoup_similarity_fp32", "BatchedUplift",
-           "SCOUP_BATCH_EAGER"]
+           "SCOUP_BATCH_EAGER", "scoup_topk_entropy", "scoup_entropy_filter", "scoup_relevancy"]
