@@ -142,6 +142,31 @@ int scoup_uplift(const scoup_scene* scene, const scoup_camera* cams, int32_t V,
                  float* accum, int32_t accum_mode, int32_t* topk_idx, float* topk_val,
                  void* workspace, size_t ws_bytes, scoup_stats* stats, void* stream);
 
+/* One semantic level of a multi-level uplift: the region maps of every view
+ * (packed as for scoup_uplift, same map_offsets for all levels) and the
+ * level's code table. */
+typedef struct scoup_level {
+  const int32_t* region_maps;  /* DEVICE int32, -1 = unlabelled at this level */
+  int32_t R_total;
+  const int32_t* code_idx;     /* DEVICE [R_total, s] */
+  const float* code_val;       /* DEVICE [R_total, s] */
+  int32_t s;
+} scoup_level;
+
+/* Uplift of L <= 3 semantic levels in one pass (the paper runs its three SAM
+ * levels as independent uplifts, Sec. 5.1; the compositing weights e do not
+ * depend on the level, so one rasterisation serves them all).  Results are
+ * those of L scoup_uplift calls, one per level:
+ *  accum     DEVICE float32 [n, L*C]; level l in columns [l*C, (l+1)*C)
+ *            ([2, n, L*C] with SCOUP_ACCUM_COMPENSATED).
+ *  topk_idx, topk_val  DEVICE [L, n, K] or NULL.
+ * Limits as for scoup_uplift, and per level s <= K, sum of s <= 64,
+ * R_total < 2^21 - 1.  Workspace and stats as for scoup_uplift. */
+int scoup_uplift_levels(const scoup_scene* scene, const scoup_camera* cams, int32_t V, const int64_t* map_offsets,
+                        const scoup_level* levels, int32_t L, int32_t C, int32_t K, float* accum,
+                        int32_t accum_mode, int32_t* topk_idx, float* topk_val, void* workspace, size_t ws_bytes,
+                        scoup_stats* stats, void* stream);
+
 /* Top-K + L1 normalisation (Eq. 6) of an accumulator accum[n, C] alone:
  * positive entries only, ordered by (value desc, atom index asc), divided by
  * the sum of the kept values; rows without positive entries give (-1, 0). */

@@ -51,6 +51,11 @@ class Stats(ct.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
+class Level(ct.Structure):
+    _fields_ = [("region_maps", ct.c_void_p), ("R_total", ct.c_int32), ("code_idx", ct.c_void_p),
+                ("code_val", ct.c_void_p), ("s", ct.c_int32)]
+
+
 class BatchItem(ct.Structure):
     _fields_ = [("scene", Scene), ("cams", ct.c_void_p), ("V", ct.c_int32), ("region_maps", ct.c_void_p),
                 ("map_offsets", ct.c_void_p), ("R_total", ct.c_int32), ("code_idx", ct.c_void_p),
@@ -88,6 +93,8 @@ PROTOS = {
     "scoup_uplift": (ct.c_int, [ct.POINTER(Scene), P, I32, P, P, I32, P, P, I32, I32, I32, P, I32,
                                 P, P, P, SZ, ct.POINTER(Stats), P]),
     "scoup_topk": (ct.c_int, [P, I64, I32, I32, P, P, P]),
+    "scoup_uplift_levels": (ct.c_int, [ct.POINTER(Scene), P, I32, P, P, I32, I32, I32, P, I32, P, P, P, SZ,
+                                       ct.POINTER(Stats), P]),
     "scoup_render": (ct.c_int, [ct.POINTER(Scene), P, P, I32, I32, ct.POINTER(Camera), P, P, P, P, SZ,
                                 ct.POINTER(Stats), P]),
     "scoup_render_backward": (ct.c_int, [ct.POINTER(Scene), P, P, I32, I32, ct.POINTER(Camera), P, P, P, P,

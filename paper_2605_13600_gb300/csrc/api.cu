@@ -209,11 +209,22 @@ int uplift_call(const UpliftCall& c, void* workspace, size_t ws_bytes, int warp_
                 cudaStream_t st) {
   const scoup_scene* scene = c.scene;
   const scoup_camera* cams = c.cams;
-  const int32_t V = c.V, R_total = c.R_total, s = c.s, C = c.C, K = c.K, accum_mode = c.accum_mode;
-  const int32_t* region_maps = c.region_maps;
+  const int32_t V = c.V, C = c.C, K = c.K, accum_mode = c.accum_mode;
   const int64_t* map_offsets = c.map_offsets;
-  const int32_t* code_idx = c.code_idx;
-  const float* code_val = c.code_val;
+  // the semantic levels (one for the single-level form)
+  scoup_level lv[kMaxLevels];
+  int L = 1;
+  if (c.L <= 0) {
+    lv[0] = scoup_level{c.region_maps, c.R_total, c.code_idx, c.code_val, c.s};
+  } else {
+    if (c.L > kMaxLevels || !c.levels) return fail(SCOUP_ERR_INVALID_ARG, "L=%d outside [1, %d]", c.L, kMaxLevels);
+    L = c.L;
+    for (int l = 0; l < L; ++l) lv[l] = c.levels[l];
+  }
+  const int32_t R_total = lv[0].R_total, s = lv[0].s;
+  const int32_t* region_maps = lv[0].region_maps;
+  const int32_t* code_idx = lv[0].code_idx;
+  const float* code_val = lv[0].code_val;
   float* accum = c.accum;
   int32_t* topk_idx = c.topk_idx;
   float* topk_val = c.topk_val;
@@ -223,19 +234,32 @@ int uplift_call(const UpliftCall& c, void* workspace, size_t ws_bytes, int warp_
   if ((rc = check_cams(cams, V, &max_tiles))) return rc;
   if (C < 1 || C > 1024) return fail(SCOUP_ERR_INVALID_ARG, "C=%d outside [1, 1024]", C);
   if (K < 1 || K > C) return fail(SCOUP_ERR_INVALID_ARG, "K=%d outside [1, C=%d]", K, C);
-  if (s < 1 || s > 1024) return fail(SCOUP_ERR_INVALID_ARG, "s=%d outside [1, 1024]", s);
-  if (R_total < 0) return fail(SCOUP_ERR_INVALID_ARG, "R_total=%d < 0", R_total);
+  int s_tot = 0;
+  for (int l = 0; l < L; ++l) {
+    if (lv[l].s < 1 || lv[l].s > 1024) return fail(SCOUP_ERR_INVALID_ARG, "s=%d outside [1, 1024]", lv[l].s);
+    if (lv[l].R_total < 0) return fail(SCOUP_ERR_INVALID_ARG, "R_total=%d < 0", lv[l].R_total);
+    if (V > 0 && !lv[l].region_maps) return fail(SCOUP_ERR_INVALID_ARG, "region maps of level %d are NULL", l);
+    if (V > 0 && lv[l].R_total > 0 && (!lv[l].code_idx || !lv[l].code_val))
+      return fail(SCOUP_ERR_INVALID_ARG, "code table of level %d is NULL", l);
+    if (L > 1 && lv[l].s > K)
+      return fail(SCOUP_ERR_INVALID_ARG, "level %d: s=%d > K=%d (levels take codes of at most K entries)", l,
+                  lv[l].s, K);
+    if (L > 1 && lv[l].R_total >= (1 << 21) - 1)
+      return fail(SCOUP_ERR_INVALID_ARG, "level %d: R_total=%d above 2^21 - 2", l, lv[l].R_total);
+    s_tot += lv[l].s;
+  }
+  if (L > 1 && s_tot > 64) return fail(SCOUP_ERR_INVALID_ARG, "levels: sum of s = %d above 64", s_tot);
+  const int Crow = L * C;
   if (accum_mode & ~(SCOUP_ACCUM_CONTINUE | SCOUP_ACCUM_COMPENSATED))
     return fail(SCOUP_ERR_INVALID_ARG, "accum_mode=%d: only SCOUP_ACCUM_CONTINUE and SCOUP_ACCUM_COMPENSATED", accum_mode);
   if (scene->n > 0 && !accum) return fail(SCOUP_ERR_INVALID_ARG, "accum is NULL");
   if ((topk_idx == nullptr) != (topk_val == nullptr))
     return fail(SCOUP_ERR_INVALID_ARG, "topk_idx and topk_val must both be given or both be NULL");
   if (V > 0 && (!region_maps || !map_offsets)) return fail(SCOUP_ERR_INVALID_ARG, "region maps are NULL");
-  if (V > 0 && R_total > 0 && (!code_idx || !code_val)) return fail(SCOUP_ERR_INVALID_ARG, "code table is NULL");
   for (int v = 0; v < V; ++v)
     if (map_offsets[v] < 0) return fail(SCOUP_ERR_INVALID_ARG, "map_offsets[%d] < 0", v);
   if (!workspace) return fail(SCOUP_ERR_INVALID_ARG, "workspace is NULL");
-  const int64_t code_rows_k = s > K ? (int64_t)R_total * K : 0;
+  const int64_t code_rows_k = (L == 1 && s > K) ? (int64_t)R_total * K : 0;
   const size_t fixed = uplift_fixed_bytes(scene->n, max_tiles, code_rows_k);
   if (ws_bytes < fixed)
     return fail(SCOUP_ERR_OOM, "workspace too small: %zu < %zu bytes before tile lists", ws_bytes, fixed);
@@ -247,9 +271,9 @@ int uplift_call(const UpliftCall& c, void* workspace, size_t ws_bytes, int warp_
   cudaError_t e;
   if ((e = cudaMemsetAsync(ws.hdr, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
   const bool compensated = (accum_mode & SCOUP_ACCUM_COMPENSATED) != 0;
-  float* comp = compensated ? accum + (size_t)n * (size_t)C : nullptr;
+  float* comp = compensated ? accum + (size_t)n * (size_t)Crow : nullptr;
   if (n > 0 && !(accum_mode & SCOUP_ACCUM_CONTINUE) &&
-      (e = cudaMemsetAsync(accum, 0, sizeof(float) * (size_t)n * (size_t)C * (compensated ? 2 : 1), st)) !=
+      (e = cudaMemsetAsync(accum, 0, sizeof(float) * (size_t)n * (size_t)Crow * (compensated ? 2 : 1), st)) !=
           cudaSuccess)
     return cuda_fail(e, "memset accum");
   if ((e = cudaMemsetAsync(ws.tile_glob, 0, sizeof(uint32_t) * ((size_t)max_tiles + 1), st)) != cudaSuccess ||
@@ -258,7 +282,7 @@ int uplift_call(const UpliftCall& c, void* workspace, size_t ws_bytes, int warp_
   const int32_t* ci = code_idx;
   const float* cv = code_val;
   int s_eff = s;
-  if (s > K && R_total > 0) {
+  if (L == 1 && s > K && R_total > 0) {
     PhaseScope ps(SCOUP_PHASE_CODE_TOPK, st);
     if ((e = launch_code_topk(code_idx, code_val, R_total, s, K, fci, fcv, st)) != cudaSuccess)
       return cuda_fail(e, "code top-k");
@@ -283,16 +307,29 @@ int uplift_call(const UpliftCall& c, void* workspace, size_t ws_bytes, int warp_
       }
       {
         PhaseScope ps(SCOUP_PHASE_UPLIFT_TILES, st);
-        if ((e = launch_uplift_tiles(ca, ws, v & 1, region_maps + map_offsets[v], R_total, ci, cv, s_eff,
-                                     C, accum, comp, warp_w, st)) != cudaSuccess)
+        LevelCodes lc;
+        lc.L = L;
+        lc.s_tot = L == 1 ? s_eff : s_tot;
+        for (int l = 0; l < kMaxLevels; ++l) {
+          const bool on = l < L;
+          lc.rmap[l] = on ? lv[l].region_maps + map_offsets[v] : nullptr;
+          lc.ci[l] = on ? (L == 1 ? ci : lv[l].code_idx) : nullptr;
+          lc.cv[l] = on ? (L == 1 ? cv : lv[l].code_val) : nullptr;
+          lc.s[l] = on ? (L == 1 ? s_eff : lv[l].s) : 0;
+          lc.R[l] = on ? lv[l].R_total : 0;
+        }
+        if ((e = launch_uplift_tiles(ca, ws, v & 1, lc, C, Crow, accum, comp, warp_w, st)) != cudaSuccess)
           return cuda_fail(e, "uplift tiles");
       }
     }
   }
   if (topk_idx && n > 0) {
     PhaseScope ps(SCOUP_PHASE_TOPK, st);
-    if ((e = launch_topk(accum, comp, n, C, K, topk_idx, topk_val, nullptr, st)) != cudaSuccess)
-      return cuda_fail(e, "top-k");
+    for (int l = 0; l < L; ++l)
+      if ((e = launch_topk(accum + (size_t)l * C, comp ? comp + (size_t)l * C : nullptr, n, C, K,
+                           topk_idx + (size_t)l * n * K, topk_val + (size_t)l * n * K, nullptr, st, Crow)) !=
+          cudaSuccess)
+        return cuda_fail(e, "top-k");
   }
   if (hdr_out) *hdr_out = ws.hdr;
   return SCOUP_OK;
@@ -375,6 +412,23 @@ int scoup_uplift(const scoup_scene* scene, const scoup_camera* cams, int32_t V,
                  void* workspace, size_t ws_bytes, scoup_stats* stats, void* stream) {
   const UpliftCall c{scene, cams, V, region_maps, map_offsets, R_total, code_idx, code_val, s, C, K,
                      accum, accum_mode, topk_idx, topk_val};
+  const WsHeader* hdr = nullptr;
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int rc = uplift_call(c, workspace, ws_bytes, 8, &hdr, st);
+  if (rc != SCOUP_OK) return rc;
+  if (stats) return finish_with_stats(hdr, stats, st);
+  return SCOUP_OK;
+}
+
+int scoup_uplift_levels(const scoup_scene* scene, const scoup_camera* cams, int32_t V, const int64_t* map_offsets,
+                        const scoup_level* levels, int32_t L, int32_t C, int32_t K, float* accum,
+                        int32_t accum_mode, int32_t* topk_idx, float* topk_val, void* workspace, size_t ws_bytes,
+                        scoup_stats* stats, void* stream) {
+  if (L < 1 || L > kMaxLevels || !levels) return fail(SCOUP_ERR_INVALID_ARG, "L=%d outside [1, %d]", L, kMaxLevels);
+  UpliftCall c{scene, cams, V, levels[0].region_maps, map_offsets, levels[0].R_total, levels[0].code_idx,
+               levels[0].code_val, levels[0].s, C, K, accum, accum_mode, topk_idx, topk_val};
+  c.L = L;
+  c.levels = levels;
   const WsHeader* hdr = nullptr;
   const cudaStream_t st = (cudaStream_t)stream;
   const int rc = uplift_call(c, workspace, ws_bytes, 8, &hdr, st);

@@ -82,6 +82,19 @@ __device__ __forceinline__ bool box_may_hit(const ProjRec& r, float x0, float y0
   return best >= tau - (0.01f + 1e-3f * fabsf(best));
 }
 
+// Region maps and code tables of one view, one per semantic level (a single
+// level for scoup_uplift; up to three for scoup_uplift_levels).
+constexpr int kMaxLevels = 3;
+struct LevelCodes {
+  const int32_t* rmap[kMaxLevels];  // this view's region map of each level
+  const int32_t* ci[kMaxLevels];    // code tables [R, s] of each level
+  const float* cv[kMaxLevels];
+  int s[kMaxLevels];
+  int R[kMaxLevels];
+  int L;      // number of levels
+  int s_tot;  // sum of s over the levels (entries of a combined region code)
+};
+
 struct CamArgs {
   float vm[12];
   float fx, fy, cx, cy;
@@ -137,6 +150,8 @@ struct UpliftCall {
   int32_t accum_mode;
   int32_t* topk_idx;
   float* topk_val;
+  int32_t L = 0;                        // > 0: semantic levels in `levels` replace the
+  const scoup_level* levels = nullptr;  // single-level region map and code fields above
 };
 
 // Validates and enqueues one uplift on `st` without synchronising; warp_w is
@@ -157,9 +172,9 @@ cudaError_t launch_preprocess(const scoup_scene& sc, const CamArgs& cam, const U
 size_t binning_run_base_bytes(int64_t n);
 cudaError_t launch_binning(const CamArgs& cam, int64_t n, const UpliftWs& ws, int slot,
                            cudaStream_t st);
-cudaError_t launch_uplift_tiles(const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* rmap,
-                                int32_t R_total, const int32_t* code_idx, const float* code_val,
-                                int s, int C, float* accum, float* comp, int warp_w, cudaStream_t st);
+// Accumulator rows are Crow = L * C floats wide; level l owns columns [l C, (l + 1) C).
+cudaError_t launch_uplift_tiles(const CamArgs& cam, const UpliftWs& ws, int slot, const LevelCodes& lc, int C,
+                                int Crow, float* accum, float* comp, int warp_w, cudaStream_t st);
 size_t render_smem_bytes(int C, int K);
 cudaError_t launch_render_tiles(const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* topk_idx,
                                 const float* topk_val, int K, int C, float* out, float* out_T,
@@ -186,8 +201,9 @@ bool gemm_tma_available();
 cudaError_t launch_sgemm(const float* A, const float* B, bool b_transposed, float* out, int64_t M, int N, int K,
                          const float* rownorm2, const float* colnorm2, cudaStream_t st);
 cudaError_t launch_row_norm2_f32(const float* X, int64_t R, int D, float* out, cudaStream_t st);
+// ld: row stride of accum / comp in floats (C for a plain [n, C] accumulator).
 cudaError_t launch_topk(const float* accum, const float* comp, int64_t n, int C, int K, int32_t* idx, float* val,
-                        float* entropy, cudaStream_t st);
+                        float* entropy, cudaStream_t st, int64_t ld = 0);
 int entropy_filter_run(const float* H, int64_t n, int64_t keep, int K, int32_t* idx, float* val, uint8_t* mask,
                        uint32_t* hist, cudaStream_t st);
 cudaError_t launch_relevancy(const float* sim, int64_t P, int ncols, int n_canon, float alpha, float* R,

@@ -23,17 +23,18 @@ __device__ __forceinline__ bool better(float v, int j, float ov, int oj) {
 
 template <int VPL>
 __global__ void __launch_bounds__(256) topk_kernel(const float* __restrict__ acc, const float* __restrict__ comp,
-                                                   int64_t n, int C, int K, int32_t* __restrict__ idx,
-                                                   float* __restrict__ val, float* __restrict__ entropy) {
+                                                   int64_t n, int C, int64_t ld, int K,
+                                                   int32_t* __restrict__ idx, float* __restrict__ val,
+                                                   float* __restrict__ entropy) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); row < n; row += warps) {
-    const float* a = acc + row * C;
+    const float* a = acc + row * ld;
     float v[VPL];
 #pragma unroll
     for (int k = 0; k < VPL; ++k) {
       const int j = lane + 32 * k;
-      v[k] = j < C ? (comp ? __fadd_rn(a[j], comp[row * C + j]) : a[j]) : 0.0f;
+      v[k] = j < C ? (comp ? __fadd_rn(a[j], comp[row * ld + j]) : a[j]) : 0.0f;
     }
     if (entropy) {
       float S = 0.0f, WL = 0.0f;
@@ -107,11 +108,11 @@ __global__ void code_topk_kernel(const int32_t* __restrict__ ci, const float* __
 }
 
 template <int VPL>
-cudaError_t launch_vpl(const float* acc, const float* comp, int64_t n, int C, int K, int32_t* idx, float* val,
-                       float* entropy, cudaStream_t st) {
+cudaError_t launch_vpl(const float* acc, const float* comp, int64_t n, int C, int64_t ld, int K, int32_t* idx,
+                       float* val, float* entropy, cudaStream_t st) {
   int64_t blocks = (n + 7) / 8;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  topk_kernel<VPL><<<(int)blocks, 256, 0, st>>>(acc, comp, n, C, K, idx, val, entropy);
+  topk_kernel<VPL><<<(int)blocks, 256, 0, st>>>(acc, comp, n, C, ld, K, idx, val, entropy);
   g_launches += 1;
   return cudaGetLastError();
 }
@@ -119,14 +120,15 @@ cudaError_t launch_vpl(const float* acc, const float* comp, int64_t n, int C, in
 }  // namespace
 
 cudaError_t launch_topk(const float* acc, const float* comp, int64_t n, int C, int K, int32_t* idx, float* val,
-                        float* entropy, cudaStream_t st) {
+                        float* entropy, cudaStream_t st, int64_t ld) {
   if (n <= 0) return cudaSuccess;
-  if (C <= 32) return launch_vpl<1>(acc, comp, n, C, K, idx, val, entropy, st);
-  if (C <= 64) return launch_vpl<2>(acc, comp, n, C, K, idx, val, entropy, st);
-  if (C <= 128) return launch_vpl<4>(acc, comp, n, C, K, idx, val, entropy, st);
-  if (C <= 256) return launch_vpl<8>(acc, comp, n, C, K, idx, val, entropy, st);
-  if (C <= 512) return launch_vpl<16>(acc, comp, n, C, K, idx, val, entropy, st);
-  return launch_vpl<32>(acc, comp, n, C, K, idx, val, entropy, st);
+  if (ld <= 0) ld = C;
+  if (C <= 32) return launch_vpl<1>(acc, comp, n, C, ld, K, idx, val, entropy, st);
+  if (C <= 64) return launch_vpl<2>(acc, comp, n, C, ld, K, idx, val, entropy, st);
+  if (C <= 128) return launch_vpl<4>(acc, comp, n, C, ld, K, idx, val, entropy, st);
+  if (C <= 256) return launch_vpl<8>(acc, comp, n, C, ld, K, idx, val, entropy, st);
+  if (C <= 512) return launch_vpl<16>(acc, comp, n, C, ld, K, idx, val, entropy, st);
+  return launch_vpl<32>(acc, comp, n, C, ld, K, idx, val, entropy, st);
 }
 
 cudaError_t launch_code_topk(const int32_t* ci, const float* cv, int64_t R, int s, int K,

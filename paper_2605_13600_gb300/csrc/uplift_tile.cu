@@ -34,6 +34,13 @@
 // global memory), together with the exact error of the product c * e
 // (fma(c, e, -c*e)).  The value of an entry is then sum + compensation.
 //
+// Semantic levels (kL = 3).  With several levels a pixel's region is the
+// tuple of its regions in every level (packed 21 bits per level, 0 = none),
+// a slot's code is the concatenation of the levels' codes with level l's
+// atoms offset by l C, and the accumulator rows hold L C columns: one
+// compositing pass scatters every level (the composite does not depend on
+// the level).
+//
 // Load balance.  After the block-wide ordering of a window, each warp walks
 // it independently (records staged per warp, no block barrier) and leaves as
 // soon as its 32 pixels are saturated; the block meets again only at the end
@@ -59,7 +66,16 @@ constexpr int kMaxS = 64;  // codes of up to kMaxS entries are staged in shared 
 constexpr int kGroup = 8;
 constexpr unsigned kFull = 0xffffffffu;
 
-template <bool kComp>
+// Region of a pixel: the region id (one level) or the packed level tuple.
+template <int kL> struct RegionKey { using T = int; };
+template <> struct RegionKey<3> { using T = unsigned long long; };
+__device__ __forceinline__ bool region_set(int r) { return r >= 0; }
+__device__ __forceinline__ bool region_set(unsigned long long r) { return r != 0ull; }
+__device__ __forceinline__ int level_region(unsigned long long key, int l) {
+  return (int)((key >> (21 * l)) & 0x1fffffull) - 1;
+}
+
+template <bool kComp, int kL>
 struct TileSmem {
   uint32_t bstart[kNB + 1];
   uint32_t bcur[kNB];
@@ -70,10 +86,10 @@ struct TileSmem {
   float part[kMaxSlots][kWin];
   float part_c[kComp ? kMaxSlots : 1][kComp ? kWin : 1];
   uint32_t nz[kMaxSlots][kWin / 32];  // window entries whose partial became non-zero
-  int slot_region[kMaxSlots];
+  typename RegionKey<kL>::T slot_region[kMaxSlots];
   int slot_idx[kMaxSlots][kMaxS];
   float slot_val[kMaxSlots][kMaxS];
-  int warp_regions[kThreads / 32][32];
+  typename RegionKey<kL>::T warp_regions[kThreads / 32][32];
   int warp_nreg[kThreads / 32];
   uint32_t hist[256];
   unsigned long long red_min, red_max;
@@ -213,14 +229,18 @@ __device__ __forceinline__ void acc_add(float* accum, float* comp, int64_t x, fl
   }
 }
 
-template <bool kComp, int kBW>
+template <bool kComp, int kBW, int kL>
 __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
     CamArgs cam, const ProjRec* __restrict__ proj, const unsigned long long* __restrict__ keys,
-    const uint32_t* __restrict__ tile_start, int slot, const int32_t* __restrict__ rmap,
-    int32_t R_total, const int32_t* __restrict__ code_idx, const float* __restrict__ code_val, int s,
-    int C, float* __restrict__ accum, float* __restrict__ comp, WsHeader* __restrict__ hdr) {
+    const uint32_t* __restrict__ tile_start, int slot, LevelCodes lc, int C, int Crow,
+    float* __restrict__ accum, float* __restrict__ comp, WsHeader* __restrict__ hdr) {
+  using RK = typename RegionKey<kL>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  TileSmem<kComp>& sm = *reinterpret_cast<TileSmem<kComp>*>(smem_raw);
+  TileSmem<kComp, kL>& sm = *reinterpret_cast<TileSmem<kComp, kL>*>(smem_raw);
+  // code entries per slot (the concatenated level codes with several levels)
+  const int s = kL == 1 ? lc.s[0] : lc.s_tot;
+  const int32_t* __restrict__ code_idx = lc.ci[0];
+  const float* __restrict__ code_val = lc.cv[0];
   const int tile = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t begin = tile_start[tile];
@@ -245,14 +265,26 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
   const int px = bxi + lane % kBW;
   const int py = byi + lane / kBW;
   const bool inside = px < cam.width && py < cam.height;
-  int region = inside ? rmap[(int64_t)py * cam.width + px] : -1;
-  if (region >= R_total) { atomicOr(&hdr->status, kStatDeviceCheck); region = -1; }
+  RK region;
+  if constexpr (kL == 1) {
+    int r = inside ? lc.rmap[0][(int64_t)py * cam.width + px] : -1;
+    if (r >= lc.R[0]) { atomicOr(&hdr->status, kStatDeviceCheck); r = -1; }
+    region = r;
+  } else {
+    unsigned long long key = 0ull;
+    for (int l = 0; l < lc.L; ++l) {
+      int r = inside ? lc.rmap[l][(int64_t)py * cam.width + px] : -1;
+      if (r >= lc.R[l]) { atomicOr(&hdr->status, kStatDeviceCheck); r = -1; }
+      if (r >= 0) key |= (unsigned long long)(r + 1) << (21 * l);
+    }
+    region = key;
+  }
   const float fpx = (float)px, fpy = (float)py;
 
   // ---- distinct regions of the tile -> slots; bucket histogram ----
   {
     const unsigned peers = __match_any_sync(kFull, region);
-    const bool leader = region >= 0 && lane == __ffs(peers) - 1;
+    const bool leader = region_set(region) && lane == __ffs(peers) - 1;
     const unsigned leaders = __ballot_sync(kFull, leader);
     if (leader) sm.warp_regions[warp][__popc(leaders & ((1u << lane) - 1u))] = region;
     if (lane == 0) sm.warp_nreg[warp] = __popc(leaders);
@@ -269,7 +301,7 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
     int ns = 0;
     for (int w = 0; w < kThreads / 32; ++w)
       for (int k = 0; k < sm.warp_nreg[w]; ++k) {
-        const int r = sm.warp_regions[w][k];
+        const RK r = sm.warp_regions[w][k];
         bool found = false;
         for (int q = 0; q < ns; ++q) found |= sm.slot_region[q] == r;
         if (!found && ns < kMaxSlots) sm.slot_region[ns++] = r;
@@ -300,11 +332,28 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
   const int nslots = sm.nslots;
   for (int k = tid; k < (s <= kMaxS ? nslots * s : 0); k += kThreads) {
     const int q = k / s, a = k - q * s;
-    const int64_t row = (int64_t)sm.slot_region[q] * s + a;
-    int j = code_idx[row];
-    if (j >= C) { atomicOr(&hdr->status, kStatDeviceCheck); j = -1; }
-    sm.slot_idx[q][a] = j;
-    sm.slot_val[q][a] = code_val[row];
+    if constexpr (kL == 1) {
+      const int64_t row = (int64_t)sm.slot_region[q] * s + a;
+      int j = code_idx[row];
+      if (j >= C) { atomicOr(&hdr->status, kStatDeviceCheck); j = -1; }
+      sm.slot_idx[q][a] = j;
+      sm.slot_val[q][a] = code_val[row];
+    } else {
+      int l = 0, e = a;  // level of entry a and its index in that level's code
+      while (l < lc.L - 1 && e >= lc.s[l]) { e -= lc.s[l]; ++l; }
+      const int r = level_region(sm.slot_region[q], l);
+      int j = -1;
+      float v = 0.0f;
+      if (r >= 0) {
+        const int64_t row = (int64_t)r * lc.s[l] + e;
+        j = lc.ci[l][row];
+        v = lc.cv[l][row];
+        if (j >= C) { atomicOr(&hdr->status, kStatDeviceCheck); j = -1; }
+        if (j >= 0) j += l * C;
+      }
+      sm.slot_idx[q][a] = j;
+      sm.slot_val[q][a] = v;
+    }
   }
   int my_slot = -1;
   for (int q = 0; q < nslots; ++q)
@@ -315,7 +364,7 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
   unsigned wslots = 0u;
   for (int q = 0; q < nslots; ++q)
     if (__any_sync(kFull, my_slot == q)) wslots |= 1u << q;
-  const bool any_unslotted = __any_sync(kFull, my_slot < 0 && region >= 0);
+  const bool any_unslotted = __any_sync(kFull, my_slot < 0 && region_set(region));
   __syncthreads();
 
   float T = 1.0f;
@@ -513,18 +562,23 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
                 part_add<kComp>(sm.part[q], sm.part_c[kComp ? q : 0], sm.nz[q], j0 + jq, S);
             }
           }
-          if (any_unslotted && has && my_slot < 0 && region >= 0) {
+          if (any_unslotted && has && my_slot < 0 && region_set(region)) {
             // more regions in this tile than slots: scatter this pixel directly
 #pragma unroll
             for (int u = 0; u < kGroup; ++u) {
               if (!(e[u] > 0.0f)) continue;
               const int64_t g = st_g[idx[u]];
-              for (int a = 0; a < s; ++a) {
-                const int64_t row = (int64_t)region * s + a;
-                const int jj = code_idx[row];
-                if (jj >= 0 && jj < C) {
-                  acc_add<kComp>(accum, comp, g * C + jj, code_val[row], e[u], 0.0f);
-                  ++n_atom;
+              for (int l = 0; l < (kL == 1 ? 1 : lc.L); ++l) {
+                int r;
+                if constexpr (kL == 1) r = region; else r = level_region(region, l);
+                if (r < 0) continue;
+                for (int a = 0; a < lc.s[l]; ++a) {
+                  const int64_t row = (int64_t)r * lc.s[l] + a;
+                  const int jj = lc.ci[l][row];
+                  if (jj >= 0 && jj < C) {
+                    acc_add<kComp>(accum, comp, g * Crow + l * C + jj, lc.cv[l][row], e[u], 0.0f);
+                    ++n_atom;
+                  }
                 }
               }
               ++n_flush;
@@ -568,7 +622,7 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
             for (int a = a0; a < s; a += lanes_per) {
               int jj;
               float cval;
-              if (s <= kMaxS) {
+              if (kL > 1 || s <= kMaxS) {
                 jj = sm.slot_idx[q][a];
                 cval = sm.slot_val[q][a];
               } else {
@@ -577,7 +631,7 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
                 cval = code_val[row];
                 if (jj >= C) { atomicOr(&hdr->status, kStatDeviceCheck); jj = -1; }
               }
-              if (jj >= 0) { acc_add<kComp>(accum, comp, g * C + jj, cval, v, vc); ++n_atom; }
+              if (jj >= 0) { acc_add<kComp>(accum, comp, g * Crow + jj, cval, v, vc); ++n_atom; }
             }
           }
         }
@@ -621,45 +675,41 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
   }
 }
 
-}  // namespace
-
-template <bool kComp, int kBW>
-cudaError_t launch_tiles_t(const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* rmap,
-                           int32_t R_total, const int32_t* code_idx, const float* code_val, int s, int C,
+template <bool kComp, int kBW, int kL>
+cudaError_t launch_tiles_t(const CamArgs& cam, const UpliftWs& ws, int slot, const LevelCodes& lc, int C, int Crow,
                            float* accum, float* comp, cudaStream_t st) {
   const int ntiles = cam.gx * cam.gy;
-  const size_t smem = sizeof(TileSmem<kComp>);
-  cudaError_t err = cudaFuncSetAttribute(uplift_tile_kernel<kComp, kBW>,
+  const size_t smem = sizeof(TileSmem<kComp, kL>);
+  cudaError_t err = cudaFuncSetAttribute(uplift_tile_kernel<kComp, kBW, kL>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  uplift_tile_kernel<kComp, kBW><<<ntiles, kThreads, smem, st>>>(cam, ws.proj, ws.keys, ws.tile_start, slot,
-                                                                 rmap, R_total, code_idx, code_val, s, C, accum,
-                                                                 comp, ws.hdr);
+  uplift_tile_kernel<kComp, kBW, kL><<<ntiles, kThreads, smem, st>>>(cam, ws.proj, ws.keys, ws.tile_start, slot, lc,
+                                                                     C, Crow, accum, comp, ws.hdr);
   g_launches += 1;
   return cudaGetLastError();
 }
 
 template <bool kComp>
-cudaError_t launch_tiles_shape(int warp_w, const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* rmap,
-                               int32_t R_total, const int32_t* code_idx, const float* code_val, int s, int C,
-                               float* accum, float* comp, cudaStream_t st) {
+cudaError_t launch_tiles_shape(int warp_w, const CamArgs& cam, const UpliftWs& ws, int slot, const LevelCodes& lc,
+                               int C, int Crow, float* accum, float* comp, cudaStream_t st) {
+  if (lc.L > 1) return launch_tiles_t<kComp, 8, 3>(cam, ws, slot, lc, C, Crow, accum, comp, st);
   switch (warp_w) {
-    case 16: return launch_tiles_t<kComp, 16>(cam, ws, slot, rmap, R_total, code_idx, code_val, s, C, accum, comp, st);
-    case 4: return launch_tiles_t<kComp, 4>(cam, ws, slot, rmap, R_total, code_idx, code_val, s, C, accum, comp, st);
-    default: return launch_tiles_t<kComp, 8>(cam, ws, slot, rmap, R_total, code_idx, code_val, s, C, accum, comp, st);
+    case 16: return launch_tiles_t<kComp, 16, 1>(cam, ws, slot, lc, C, Crow, accum, comp, st);
+    case 4: return launch_tiles_t<kComp, 4, 1>(cam, ws, slot, lc, C, Crow, accum, comp, st);
+    default: return launch_tiles_t<kComp, 8, 1>(cam, ws, slot, lc, C, Crow, accum, comp, st);
   }
 }
 
-cudaError_t launch_uplift_tiles(const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* rmap,
-                                int32_t R_total, const int32_t* code_idx, const float* code_val,
-                                int s, int C, float* accum, float* comp, int warp_w, cudaStream_t st) {
-  static_assert(sizeof(TileSmem<false>) <= 55 * 1024, "4 CTAs per SM");
-  static_assert(sizeof(TileSmem<true>) <= 74 * 1024, "3 CTAs per SM");
+}  // namespace
+
+cudaError_t launch_uplift_tiles(const CamArgs& cam, const UpliftWs& ws, int slot, const LevelCodes& lc, int C,
+                                int Crow, float* accum, float* comp, int warp_w, cudaStream_t st) {
+  static_assert(sizeof(TileSmem<false, 1>) <= 55 * 1024, "4 CTAs per SM");
+  static_assert(sizeof(TileSmem<false, 3>) <= 55 * 1024, "4 CTAs per SM");
+  static_assert(sizeof(TileSmem<true, 3>) <= 74 * 1024, "3 CTAs per SM");
   if (cam.gx * cam.gy <= 0) return cudaSuccess;
-  if (comp)
-    return launch_tiles_shape<true>(warp_w, cam, ws, slot, rmap, R_total, code_idx, code_val, s, C, accum, comp, st);
-  return launch_tiles_shape<false>(warp_w, cam, ws, slot, rmap, R_total, code_idx, code_val, s, C, accum, nullptr,
-                                   st);
+  if (comp) return launch_tiles_shape<true>(warp_w, cam, ws, slot, lc, C, Crow, accum, comp, st);
+  return launch_tiles_shape<false>(warp_w, cam, ws, slot, lc, C, Crow, accum, nullptr, st);
 }
 
 }  // namespace scoup

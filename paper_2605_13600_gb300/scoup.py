@@ -13,7 +13,7 @@ from typing import Optional, Sequence
 import numpy as np
 
 from . import _lib
-from ._lib import (SCOUP_ACCUM_COMPENSATED, SCOUP_ACCUM_CONTINUE, SCOUP_BATCH_EAGER, BatchItem, Camera,
+from ._lib import (SCOUP_ACCUM_COMPENSATED, SCOUP_ACCUM_CONTINUE, SCOUP_BATCH_EAGER, BatchItem, Camera, Level,
                    PlanInfo, Scene, ScoupError, Stats, check, load)
 
 
@@ -443,6 +443,57 @@ class Uplift:
         return self.accum
 
 
+class LevelUplift:
+    """L semantic levels (workloads sharing scene, cameras and map offsets) uplifted
+    in one pass through scoup_uplift_levels.  accum is [n, L*C] (level l in
+    columns l*C..); topk_idx / topk_val are [L, n, K]."""
+
+    def __init__(self, wls, device: str = "cuda", compensated: bool = False, dup_capacity: Optional[int] = None):
+        import torch
+        dev = torch.device(device)
+        self.wls = list(wls)
+        self.L = len(self.wls)
+        base = self.wls[0]
+        self.base = Uplift(base, device=device, dup_capacity=dup_capacity, topk=False)
+        self.C, self.K = int(base.C), int(base.K)
+        n = base.scene.n
+        self.compensated = bool(compensated)
+        self.maps, self.ci, self.cv = [], [], []
+        self.levels = (Level * self.L)()
+        for l, wl in enumerate(self.wls):
+            m = torch.as_tensor(wl.region_maps, device=dev).contiguous()
+            ci = torch.as_tensor(wl.code_idx, device=dev).contiguous()
+            cv = torch.as_tensor(wl.code_val, device=dev).contiguous()
+            self.maps.append(m)
+            self.ci.append(ci)
+            self.cv.append(cv)
+            self.levels[l].region_maps, self.levels[l].R_total = _ptr(m), int(wl.code_idx.shape[0])
+            self.levels[l].code_idx, self.levels[l].code_val, self.levels[l].s = _ptr(ci), _ptr(cv), int(wl.s)
+        shape = (2, n, self.L * self.C) if compensated else (n, self.L * self.C)
+        self.accum = torch.empty(shape, dtype=torch.float32, device=dev)
+        self.topk_idx = torch.empty((self.L, n, self.K), dtype=torch.int32, device=dev)
+        self.topk_val = torch.empty((self.L, n, self.K), dtype=torch.float32, device=dev)
+
+    def run(self, stats: bool = True, topk: bool = True, views=None, stream=None):
+        b = self.base
+        cams = b.cams if views is None else [b.cams[v] for v in views]
+        offs = np.ascontiguousarray((b.map_offsets if views is None else b.map_offsets[list(views)])[:max(1, len(cams))])
+        ca = camera_array(cams)
+        st = Stats()
+        mode = SCOUP_ACCUM_COMPENSATED if self.compensated else 0
+        check(load().scoup_uplift_levels(ct.byref(b.scene), ct.cast(ca, ct.c_void_p), len(cams),
+                                         offs.ctypes.data_as(ct.c_void_p), ct.cast(self.levels, ct.c_void_p),
+                                         self.L, self.C, self.K, _ptr(self.accum), mode,
+                                         _ptr(self.topk_idx) if topk else None,
+                                         _ptr(self.topk_val) if topk else None, _ptr(b.workspace),
+                                         b.workspace.numel(), ct.byref(st) if stats else None, _stream(stream)))
+        return st.as_dict() if stats else None
+
+    def level_accum(self, l: int):
+        a = self.accum[0] + self.accum[1] if self.compensated else self.accum
+        return a[:, l * self.C:(l + 1) * self.C]
+
+
 class BatchedUplift:
     """Many uplift workloads (scenes with their own views) run as one batch:
     a plan with per-lane workspaces, an optional autotuning pass and a CUDA
@@ -544,4 +595,4 @@ __all__ = ["ScoupError", "SCOUP_ACCUM_CONTINUE", "SCOUP_ACCUM_COMPENSATED", "sce
            "scoup_render", "scoup_render_backward", "Render", "Uplift",
            "scoup_decode_workspace_size", "scoup_decode", "scoup_similarity_workspace_size",
            "scoup_similarity", "scoup_decode_fp32", "scoup_similarity_fp32", "BatchedUplift",
-           "SCOUP_BATCH_EAGER", "scoup_topk_entropy", "scoup_entropy_filter", "scoup_relevancy"]
+           "SCOUP_BATCH_EAGER", "LevelUplift", "scoup_topk_entropy", "scoup_entropy_filter", "scoup_relevancy"]

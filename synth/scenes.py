@@ -33,7 +33,7 @@ __all__ = [
     "gaussians", "look_at", "camera_at", "fibonacci_cameras", "band_cameras",
     "voronoi_map", "region_codes", "sparse_topk_codes", "unit_rows",
     "tiny_workload", "uplift_cfg1", "uplift_cfg2", "uplift_cfg3_scene",
-    "render_cfg4", "render_cfg5", "dense_feature_codes",
+    "render_cfg4", "render_cfg5", "dense_feature_codes", "level_workloads",
 ]
 
 
@@ -247,6 +247,31 @@ def dense_feature_codes(wl: "UpliftWorkload", D: int = 512, seed: int = 7) -> "U
     out = UpliftWorkload(f"{wl.name}_dense{D}", wl.scene, wl.cams, wl.region_maps, wl.map_offsets,
                          ci, cv, D + 1, D + 1, D + 1, wl.regions_per_view)
     out.region_features = feats
+    return out
+
+
+def level_workloads(base: "UpliftWorkload", R_levels=(8, 32, 128), seed: int = 11,
+                    device: str = "cpu") -> List["UpliftWorkload"]:
+    """Semantic levels over the scene and views of `base` (coarse to fine, like
+    SAM's whole / part / subpart masks): the finest level partitions every
+    view into R_levels[-1] Voronoi regions; level l merges them into
+    R_levels[l] groups (fine local id * R_l // R_fine), so the levels nest.
+    Each level has its own Dirichlet codes (base C, s, K)."""
+    rng = np.random.default_rng(seed)
+    R_fine = int(R_levels[-1])
+    seeds = _draw_seeds(rng, base.cams, [R_fine] * len(base.cams))
+    local = [voronoi_map(sd, c.width, c.height, device=device).reshape(-1) for sd, c in zip(seeds, base.cams)]
+    offs = np.zeros(len(base.cams) + 1, np.int64)
+    for v, c in enumerate(base.cams):
+        offs[v + 1] = offs[v] + c.width * c.height
+    out = []
+    for l, R in enumerate(R_levels):
+        R = int(R)
+        maps = np.concatenate([(m.astype(np.int64) * R // R_fine + v * R).astype(np.int32)
+                               for v, m in enumerate(local)]) if local else np.zeros(0, np.int32)
+        ci, cv = region_codes(rng, R * len(base.cams), base.C, base.s)
+        out.append(UpliftWorkload(f"{base.name}_level{l}", base.scene, base.cams, maps, offs, ci, cv,
+                                  base.C, base.s, base.K, [R] * len(base.cams)))
     return out
 
 

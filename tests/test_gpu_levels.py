@@ -1,0 +1,83 @@
+"""Semantic levels uplifted in one pass (scoup_uplift_levels) vs the FP64
+oracle run once per level (the paper uplifts its three SAM levels as
+independent runs; one rasterisation serves all of them)."""
+import numpy as np
+import pytest
+
+import synth
+from parity import check_accum, check_topk
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_13600_gb300 import build
+    build.build()
+    import paper_2605_13600_gb300 as gb
+    return gb
+
+
+def _check_levels(gb, oracle_lib, wls, compensated=False, tag=""):
+    lu = gb.LevelUplift(wls, compensated=compensated)
+    st = lu.run()
+    assert st["status"] == 0, (tag, st)
+    total = 0
+    for l, wl in enumerate(wls):
+        acc, risk, cnt = oracle_lib.uplift(wl)
+        info = check_accum(lu.level_accum(l).cpu().numpy(), acc, risk)
+        assert info["n_bad"] == 0, (tag, l, info)
+        tk = check_topk(lu.topk_idx[l].cpu().numpy(), lu.topk_val[l].cpu().numpy(), acc, risk, wl.K)
+        assert tk["n_problems"] == 0, (tag, l, tk)
+        total = cnt["contributions"]
+    # contributions are counted once per pass (the composite is shared by the levels)
+    assert abs(st["contributions"] - total) <= 2 * cnt["at_risk"]
+    return lu
+
+
+def test_three_nested_levels(gb, oracle_lib):
+    base = synth.tiny_workload(501, n=4000, width=160, height=120, V=4, R=8, C=64, s=4, K=4, layout="blobs")
+    wls = synth.level_workloads(base, R_levels=(6, 24, 96), seed=3)
+    _check_levels(gb, oracle_lib, wls, tag="nested")
+
+
+def test_two_levels_and_compensated(gb, oracle_lib):
+    base = synth.tiny_workload(502, n=2500, width=96, height=72, V=3, R=8, C=32, s=3, K=3, layout="blobs")
+    wls = synth.level_workloads(base, R_levels=(4, 40), seed=4)
+    _check_levels(gb, oracle_lib, wls, compensated=True, tag="two levels, compensated")
+
+
+def test_independent_levels_overflow_slots(gb, oracle_lib):
+    """Levels that do not nest: tiles hold more distinct region tuples than
+    slots, so some pixels take the direct scatter path."""
+    base = synth.tiny_workload(503, n=3000, width=128, height=96, V=3, R=8, C=64, s=4, K=4, layout="blobs")
+    wls = [synth.level_workloads(base, R_levels=(R,), seed=10 + i)[0] for i, R in enumerate((30, 60, 120))]
+    _check_levels(gb, oracle_lib, wls, tag="independent")
+
+
+def test_levels_match_separate_uplifts(gb):
+    import torch
+    base = synth.tiny_workload(504, n=2000, width=96, height=80, V=3, R=8, C=32, s=4, K=4)
+    wls = synth.level_workloads(base, R_levels=(5, 20, 60), seed=6)
+    lu = gb.LevelUplift(wls)
+    lu.run()
+    for l, wl in enumerate(wls):
+        up = gb.Uplift(wl)
+        up.run()
+        torch.testing.assert_close(lu.level_accum(l), up.accum, rtol=2e-5, atol=1e-6)
+
+
+def test_levels_argument_checks(gb):
+    from paper_2605_13600_gb300._lib import ScoupError
+    base = synth.tiny_workload(505, n=200, width=48, height=40, V=2, R=4, C=16, s=3, K=3)
+    wls = synth.level_workloads(base, R_levels=(2, 4), seed=1)
+    bad = synth.UpliftWorkload("s_above_K", base.scene, base.cams, wls[1].region_maps, wls[1].map_offsets,
+                               np.tile(np.arange(5, dtype=np.int32), (wls[1].code_idx.shape[0], 1)),
+                               np.full((wls[1].code_idx.shape[0], 5), 0.2, np.float32), 16, 5, 3,
+                               wls[1].regions_per_view)
+    lu = gb.LevelUplift([wls[0], bad])
+    with pytest.raises(ScoupError):
+        lu.run()
