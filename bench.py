@@ -49,6 +49,8 @@ def parse_args():
                     help="views of the 1920x1080 render + decode measurement (0 = skip)")
     ap.add_argument("--dense-views", type=int, default=20,
                     help="views of the dense (D=512) vs sparse uplift comparison (0 = skip)")
+    ap.add_argument("--level-views", type=int, default=20,
+                    help="views of the three-level one-pass vs separate-pass comparison (0 = skip)")
     ap.add_argument("--batch-scenes", type=int, default=16,
                     help="scenes of the batched-uplift measurement (0 = skip)")
     ap.add_argument("--decode-rows", type=int, default=0,
@@ -369,6 +371,10 @@ def run_gb300(args, dist):
     if args.dense_views > 0:
         dn = dense_leg(args, dist, wl, up, dev)
 
+    lv = None
+    if args.level_views > 0:
+        lv = levels_leg(args, dist, dev)
+
     bt = None
     if args.batch_scenes > 0:
         del up
@@ -392,6 +398,7 @@ def run_gb300(args, dist):
             "stats": {k: st0[k] for k in ("visible", "duplicates", "flushes", "atomics")},
             "render_decode": rd,
             "dense_vs_sparse": dn,
+            "levels": lv,
             "batched": bt,
         }
         print(json.dumps(line), flush=True)
@@ -531,6 +538,46 @@ def dense_leg(args, dist, wl, up, dev):
     torch.cuda.empty_cache()
     return {"views": len(views), "workload": WORKLOAD, "accumulate_only": True, **out,
             "time_ratio_dense_over_sparse": out["dense_d512"]["ms"] / out["sparse_s8"]["ms"]}
+
+
+def levels_leg(args, dist, dev):
+    """Secondary measurement: three nested semantic levels (50 / 100 / 200
+    regions per view, C = 256, s = 8, K = 8 each) over the 1M Gaussians, as one
+    scoup_uplift_levels pass vs three scoup_uplift passes (both with Top-K)."""
+    import torch
+
+    import synth
+    import paper_2605_13600_gb300 as gb
+
+    base = synth.uplift_cfg2(device=str(dev), V=args.level_views)
+    wls = synth.level_workloads(base, R_levels=(50, 100, 200), seed=11, device=str(dev))
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        dist.barrier()
+        ev0.record(stream)
+        for _ in range(2):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return dist.max(ev0.elapsed_time(ev1) / 1e3 / 2)
+
+    lu = gb.LevelUplift(wls, device=str(dev))
+    st = lu.run(stats=True)
+    if st["status"] != 0:
+        raise RuntimeError("levels status")
+    t_one = timed(lambda: lu.run(stats=False))
+    del lu
+    ups = [gb.Uplift(wl, device=str(dev)) for wl in wls]
+    t_sep = timed(lambda: [u.run(stats=False) for u in ups])
+    del ups
+    torch.cuda.empty_cache()
+    return {"views": args.level_views, "levels": [50, 100, 200], "contributions_per_level": st["contributions"],
+            "one_pass_ms": t_one * 1e3, "separate_passes_ms": t_sep * 1e3, "speedup": t_sep / t_one,
+            "level_contributions_per_s_one_pass": dist.world * 3 * st["contributions"] / t_one}
 
 
 def batched_leg(args, dist, dev):

@@ -161,7 +161,10 @@ typedef struct scoup_level {
  *            ([2, n, L*C] with SCOUP_ACCUM_COMPENSATED).
  *  topk_idx, topk_val  DEVICE [L, n, K] or NULL.
  * Limits as for scoup_uplift, and per level s <= K, sum of s <= 64,
- * R_total < 2^21 - 1.  Workspace and stats as for scoup_uplift. */
+ * R_total < 2^21 - 1.  Workspace and stats as for scoup_uplift.
+ * Rendering all levels at once is scoup_render with C' = L*C, K' = L*K and
+ * each Gaussian's codes of level l concatenated with atom ids offset by l*C:
+ * out_codes[p][l*C + j] is level l's rendered code. */
 int scoup_uplift_levels(const scoup_scene* scene, const scoup_camera* cams, int32_t V, const int64_t* map_offsets,
                         const scoup_level* levels, int32_t L, int32_t C, int32_t K, float* accum,
                         int32_t accum_mode, int32_t* topk_idx, float* topk_val, void* workspace, size_t ws_bytes,

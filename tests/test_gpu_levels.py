@@ -81,3 +81,24 @@ def test_levels_argument_checks(gb):
     lu = gb.LevelUplift([wls[0], bad])
     with pytest.raises(ScoupError):
         lu.run()
+
+
+def test_render_levels_at_once(gb, oracle_lib):
+    """One scoup_render over the levels' codes (atom ids offset by l*C) gives
+    every level's rendered codes in its own column block."""
+    base = synth.tiny_workload(506, n=1500, width=64, height=48, V=1, R=6, C=16, s=3, K=3, layout="blobs")
+    rng = np.random.default_rng(7)
+    L, C, K, n = 3, 16, 3, base.scene.n
+    idx_l, val_l = zip(*[synth.sparse_topk_codes(rng, n, C, K) for _ in range(L)])
+    idx = np.concatenate([np.where(i >= 0, i + l * C, -1) for l, i in enumerate(idx_l)], axis=1).astype(np.int32)
+    val = np.concatenate(val_l, axis=1).astype(np.float32)
+    r = gb.Render(base.scene, idx, val, L * C, [base.cams[0]])
+    (W, T, _), st = r.run(0)
+    Wg = W.cpu().numpy()
+    for l in range(L):
+        Wo, To, risk, _ = oracle_lib.render(base.scene, idx_l[l].astype(np.int32), val_l[l].astype(np.float64), C,
+                                            base.cams[0])
+        err = np.abs(Wg[..., l * C:(l + 1) * C].astype(np.float64) - Wo)
+        tol = 1e-4 * np.abs(Wo) + 1e-6 * np.abs(Wo).max(axis=-1, keepdims=True) + 1e-7
+        tol = np.where(risk[..., None], 1e-2 + tol, tol)
+        assert (err <= tol).all()
