@@ -84,7 +84,11 @@ const char* scoup_last_error(void);
 
 /* Bytes of workspace for scoup_uplift on scenes of up to n Gaussians, views
  * of up to max_width x max_height pixels and up to dup_capacity
- * (Gaussian, tile) pairs per view.  Returns 0 on invalid arguments. */
+ * (Gaussian, tile) pairs per view.  scoup_uplift runs even and odd views in
+ * two pipelines (the second on a stream the library owns, joined back into
+ * the caller's stream) when the workspace holds two sets of per-view buffers;
+ * this size provides them; a workspace too small for two runs one.
+ * Returns 0 on invalid arguments. */
 size_t scoup_uplift_workspace_size(int64_t n, int32_t max_width, int32_t max_height,
                                    int64_t dup_capacity);
 

@@ -82,25 +82,39 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 int tiles_of(int w, int h) { return ((w + kTile - 1) / kTile) * ((h + kTile - 1) / kTile); }
 
-// Fixed part of the uplift workspace (everything but the key lists).
-size_t uplift_fixed_bytes(int64_t n, int max_tiles, int64_t code_rows_k) {
+// Workspace = shared part (header, Morton-ordered scene copy, codes) + one
+// per-view part for each view pipeline (records, depth, rectangles, tile
+// counters) + the key lists, split evenly between the pipelines.
+size_t shared_bytes(int64_t n, int64_t code_rows_k) {
   const size_t un = (size_t)n;
   size_t b = align_up(sizeof(WsHeader));
   b += 2 * align_up(sizeof(float) * 3 * un);              // spatially ordered means, scales
   b += align_up(sizeof(float) * 4 * un);                  // quats
   b += 4 * align_up(sizeof(float) * un);                  // opacity, tau, orig, cell
   b += align_up(reorder_scratch_bytes());
-  b += align_up(sizeof(ProjRec) * un);                    // proj
-  b += align_up(sizeof(uint32_t) * un);                   // depth
-  b += align_up(sizeof(ushort4) * un);                    // rect
-  b += 4 * align_up(sizeof(uint32_t) * ((size_t)max_tiles + 1));
-  b += align_up(binning_run_base_bytes(n));                // binning: reserved-run offsets
   b += 2 * align_up((size_t)code_rows_k * 4);             // filtered codes (s > K)
   return b;
 }
 
-UpliftWs carve(void* ws, size_t bytes, int64_t n, int max_tiles, int64_t code_rows_k,
-               int32_t** codes_i, float** codes_v) {
+size_t lane_bytes(int64_t n, int max_tiles) {
+  const size_t un = (size_t)n;
+  size_t b = align_up(sizeof(ProjRec) * un);              // proj
+  b += align_up(sizeof(uint32_t) * un);                   // depth
+  b += align_up(sizeof(ushort4) * un);                    // rect
+  b += 4 * align_up(sizeof(uint32_t) * ((size_t)max_tiles + 1));
+  b += align_up(binning_run_base_bytes(n));               // binning: reserved-run offsets
+  return b;
+}
+
+// Fixed part of the uplift workspace (everything but the key lists) for `lanes` view pipelines.
+size_t uplift_fixed_bytes(int64_t n, int max_tiles, int64_t code_rows_k, int lanes = 1) {
+  return shared_bytes(n, code_rows_k) + (size_t)lanes * lane_bytes(n, max_tiles);
+}
+
+// Carves `lanes` view pipelines out of the workspace; out[l] share the header
+// and the scene copy.
+void carve_lanes(void* ws, size_t bytes, int64_t n, int max_tiles, int64_t code_rows_k, int lanes,
+                 int32_t** codes_i, float** codes_v, UpliftWs* out) {
   UpliftWs w;
   char* p = (char*)ws;
   size_t off = 0;
@@ -115,20 +129,44 @@ UpliftWs carve(void* ws, size_t bytes, int64_t n, int max_tiles, int64_t code_ro
   w.sp.orig = (int32_t*)take(sizeof(int32_t) * un);
   w.cell = (uint32_t*)take(sizeof(uint32_t) * un);
   w.cells_scratch = (uint32_t*)take(reorder_scratch_bytes());
-  w.proj = (ProjRec*)take(sizeof(ProjRec) * un);
-  w.depth = (uint32_t*)take(sizeof(uint32_t) * un);
-  w.rect = (ushort4*)take(sizeof(ushort4) * un);
-  w.tile_count = (uint32_t*)take(sizeof(uint32_t) * ((size_t)max_tiles + 1));
-  w.tile_glob = (uint32_t*)take(sizeof(uint32_t) * ((size_t)max_tiles + 1));
-  w.run_base = (uint32_t*)take(binning_run_base_bytes(n));
-  w.tile_start = (uint32_t*)take(sizeof(uint32_t) * ((size_t)max_tiles + 1));
-  w.tile_fill = (uint32_t*)take(sizeof(uint32_t) * ((size_t)max_tiles + 1));
   *codes_i = (int32_t*)take((size_t)code_rows_k * 4);
   *codes_v = (float*)take((size_t)code_rows_k * 4);
-  w.keys = (unsigned long long*)(p + off);
-  w.dup_capacity = bytes > off ? (int64_t)((bytes - off) / sizeof(unsigned long long)) : 0;
   w.max_tiles = max_tiles;
+  for (int l = 0; l < lanes; ++l) {
+    out[l] = w;
+    out[l].proj = (ProjRec*)take(sizeof(ProjRec) * un);
+    out[l].depth = (uint32_t*)take(sizeof(uint32_t) * un);
+    out[l].rect = (ushort4*)take(sizeof(ushort4) * un);
+    out[l].tile_count = (uint32_t*)take(sizeof(uint32_t) * ((size_t)max_tiles + 1));
+    out[l].tile_glob = (uint32_t*)take(sizeof(uint32_t) * ((size_t)max_tiles + 1));
+    out[l].run_base = (uint32_t*)take(binning_run_base_bytes(n));
+    out[l].tile_start = (uint32_t*)take(sizeof(uint32_t) * ((size_t)max_tiles + 1));
+    out[l].tile_fill = (uint32_t*)take(sizeof(uint32_t) * ((size_t)max_tiles + 1));
+  }
+  const int64_t keys_each = bytes > off ? (int64_t)((bytes - off) / sizeof(unsigned long long) / lanes) : 0;
+  for (int l = 0; l < lanes; ++l) {
+    out[l].keys = (unsigned long long*)(p + off) + (size_t)l * (size_t)keys_each;
+    out[l].dup_capacity = keys_each;
+  }
+}
+
+UpliftWs carve(void* ws, size_t bytes, int64_t n, int max_tiles, int64_t code_rows_k,
+               int32_t** codes_i, float** codes_v) {
+  UpliftWs w;
+  carve_lanes(ws, bytes, n, max_tiles, code_rows_k, 1, codes_i, codes_v, &w);
   return w;
+}
+
+// The library's second stream for the odd views of an uplift (one per host
+// thread and device, created on first use).
+cudaStream_t view_lane_stream() {
+  thread_local cudaStream_t streams[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return nullptr;
+  if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess)
+    streams[dev] = nullptr;
+  return streams[dev];
 }
 
 CamArgs cam_args(const scoup_camera& c) {
@@ -206,7 +244,7 @@ namespace scoup {
 int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
 
 int uplift_call(const UpliftCall& c, void* workspace, size_t ws_bytes, int warp_w, const WsHeader** hdr_out,
-                cudaStream_t st) {
+                cudaStream_t st, int view_lanes) {
   const scoup_scene* scene = c.scene;
   const scoup_camera* cams = c.cams;
   const int32_t V = c.V, C = c.C, K = c.K, accum_mode = c.accum_mode;
@@ -264,9 +302,14 @@ int uplift_call(const UpliftCall& c, void* workspace, size_t ws_bytes, int warp_
   if (ws_bytes < fixed)
     return fail(SCOUP_ERR_OOM, "workspace too small: %zu < %zu bytes before tile lists", ws_bytes, fixed);
 
+  // two view pipelines (even / odd views on two streams) when the workspace holds them
+  const int lanes =
+      (view_lanes >= 2 && V >= 2 && ws_bytes >= uplift_fixed_bytes(scene->n, max_tiles, code_rows_k, 2) + 64) ? 2 : 1;
   int32_t* fci = nullptr;
   float* fcv = nullptr;
-  UpliftWs ws = carve(workspace, ws_bytes, scene->n, max_tiles, code_rows_k, &fci, &fcv);
+  UpliftWs wsl[2];
+  carve_lanes(workspace, ws_bytes, scene->n, max_tiles, code_rows_k, lanes, &fci, &fcv, wsl);
+  const UpliftWs& ws = wsl[0];
   const int64_t n = scene->n;
   cudaError_t e;
   if ((e = cudaMemsetAsync(ws.hdr, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
@@ -276,9 +319,10 @@ int uplift_call(const UpliftCall& c, void* workspace, size_t ws_bytes, int warp_
       (e = cudaMemsetAsync(accum, 0, sizeof(float) * (size_t)n * (size_t)Crow * (compensated ? 2 : 1), st)) !=
           cudaSuccess)
     return cuda_fail(e, "memset accum");
-  if ((e = cudaMemsetAsync(ws.tile_glob, 0, sizeof(uint32_t) * ((size_t)max_tiles + 1), st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(ws.tile_count, 0, sizeof(uint32_t) * ((size_t)max_tiles + 1), st)) != cudaSuccess)
-    return cuda_fail(e, "memset");
+  for (int l = 0; l < lanes; ++l)
+    if ((e = cudaMemsetAsync(wsl[l].tile_glob, 0, sizeof(uint32_t) * ((size_t)max_tiles + 1), st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(wsl[l].tile_count, 0, sizeof(uint32_t) * ((size_t)max_tiles + 1), st)) != cudaSuccess)
+      return cuda_fail(e, "memset");
   const int32_t* ci = code_idx;
   const float* cv = code_val;
   int s_eff = s;
@@ -295,18 +339,37 @@ int uplift_call(const UpliftCall& c, void* workspace, size_t ws_bytes, int warp_
       PhaseScope ps(SCOUP_PHASE_TAU, st);
       if ((e = launch_reorder(*scene, ws, st)) != cudaSuccess) return cuda_fail(e, "reorder");
     }
-    for (int v = 0; v < V; ++v) {
+    // view v runs in pipeline v % lanes; the second pipeline forks from and
+    // joins back into `st` through events (graph capture follows them)
+    cudaStream_t sts[2] = {st, st};
+    cudaEvent_t fork = nullptr, join = nullptr;
+    if (lanes == 2) {
+      sts[1] = view_lane_stream();
+      if (!sts[1]) return fail(SCOUP_ERR_CUDA, "could not create the second view stream");
+      if ((e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming)) != cudaSuccess ||
+          (e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming)) != cudaSuccess ||
+          (e = cudaEventRecord(fork, st)) != cudaSuccess || (e = cudaStreamWaitEvent(sts[1], fork, 0)) != cudaSuccess) {
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+        return cuda_fail(e, "view streams");
+      }
+    }
+    int rc_views = SCOUP_OK;
+    for (int v = 0; v < V && rc_views == SCOUP_OK; ++v) {
+      const int lane = v % lanes, slot = 2 * lane + ((v / lanes) & 1);
+      const cudaStream_t vs = sts[lane];
+      const UpliftWs& wv = wsl[lane];
       const CamArgs ca = cam_args(cams[v]);
       {
-        PhaseScope ps(SCOUP_PHASE_PREPROCESS, st);
-        if ((e = launch_preprocess(*scene, ca, ws, v & 1, st)) != cudaSuccess) return cuda_fail(e, "preprocess");
+        PhaseScope ps(SCOUP_PHASE_PREPROCESS, vs);
+        if ((e = launch_preprocess(*scene, ca, wv, slot, vs)) != cudaSuccess) { rc_views = cuda_fail(e, "preprocess"); break; }
       }
       {
-        PhaseScope ps(SCOUP_PHASE_BINNING, st);
-        if ((e = launch_binning(ca, n, ws, v & 1, st)) != cudaSuccess) return cuda_fail(e, "binning");
+        PhaseScope ps(SCOUP_PHASE_BINNING, vs);
+        if ((e = launch_binning(ca, n, wv, slot, vs)) != cudaSuccess) { rc_views = cuda_fail(e, "binning"); break; }
       }
       {
-        PhaseScope ps(SCOUP_PHASE_UPLIFT_TILES, st);
+        PhaseScope ps(SCOUP_PHASE_UPLIFT_TILES, vs);
         LevelCodes lc;
         lc.L = L;
         lc.s_tot = L == 1 ? s_eff : s_tot;
@@ -318,10 +381,20 @@ int uplift_call(const UpliftCall& c, void* workspace, size_t ws_bytes, int warp_
           lc.s[l] = on ? (L == 1 ? s_eff : lv[l].s) : 0;
           lc.R[l] = on ? lv[l].R_total : 0;
         }
-        if ((e = launch_uplift_tiles(ca, ws, v & 1, lc, C, Crow, accum, comp, warp_w, st)) != cudaSuccess)
-          return cuda_fail(e, "uplift tiles");
+        if ((e = launch_uplift_tiles(ca, wv, slot, lc, C, Crow, accum, comp, warp_w, vs)) != cudaSuccess) {
+          rc_views = cuda_fail(e, "uplift tiles");
+          break;
+        }
       }
     }
+    if (lanes == 2) {
+      // join even on an error, so that a capture in progress stays well formed
+      if ((e = cudaEventRecord(join, sts[1])) != cudaSuccess || (e = cudaStreamWaitEvent(st, join, 0)) != cudaSuccess)
+        if (rc_views == SCOUP_OK) rc_views = cuda_fail(e, "view streams");
+      cudaEventDestroy(fork);
+      cudaEventDestroy(join);
+    }
+    if (rc_views != SCOUP_OK) return rc_views;
   }
   if (topk_idx && n > 0) {
     PhaseScope ps(SCOUP_PHASE_TOPK, st);
@@ -367,8 +440,8 @@ const char* scoup_last_error(void) { return g_err.c_str(); }
 size_t scoup_uplift_workspace_size(int64_t n, int32_t max_width, int32_t max_height,
                                    int64_t dup_capacity) {
   if (n < 0 || max_width <= 0 || max_height <= 0 || dup_capacity < 0) return 0;
-  return uplift_fixed_bytes(n, tiles_of(max_width, max_height), 0) +
-         sizeof(unsigned long long) * (size_t)dup_capacity;
+  return uplift_fixed_bytes(n, tiles_of(max_width, max_height), 0, 2) +
+         2 * sizeof(unsigned long long) * (size_t)dup_capacity;
 }
 
 int scoup_uplift_plan(const scoup_scene* scene, const scoup_camera* cams, int32_t V,
@@ -414,7 +487,7 @@ int scoup_uplift(const scoup_scene* scene, const scoup_camera* cams, int32_t V,
                      accum, accum_mode, topk_idx, topk_val};
   const WsHeader* hdr = nullptr;
   const cudaStream_t st = (cudaStream_t)stream;
-  const int rc = uplift_call(c, workspace, ws_bytes, 8, &hdr, st);
+  const int rc = uplift_call(c, workspace, ws_bytes, 8, &hdr, st, 2);
   if (rc != SCOUP_OK) return rc;
   if (stats) return finish_with_stats(hdr, stats, st);
   return SCOUP_OK;
@@ -431,7 +504,7 @@ int scoup_uplift_levels(const scoup_scene* scene, const scoup_camera* cams, int3
   c.levels = levels;
   const WsHeader* hdr = nullptr;
   const cudaStream_t st = (cudaStream_t)stream;
-  const int rc = uplift_call(c, workspace, ws_bytes, 8, &hdr, st);
+  const int rc = uplift_call(c, workspace, ws_bytes, 8, &hdr, st, 2);
   if (rc != SCOUP_OK) return rc;
   if (stats) return finish_with_stats(hdr, stats, st);
   return SCOUP_OK;

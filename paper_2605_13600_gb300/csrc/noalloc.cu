@@ -64,8 +64,8 @@ int scoup_uplift_noalloc(const scoup_scene* scene, const scoup_camera* cams, int
     if (cams[v].width > maxw) maxw = cams[v].width;
     if (cams[v].height > maxh) maxh = cams[v].height;
   }
-  const size_t fixed = scoup_uplift_workspace_size(scene->n, maxw, maxh, 0) +
-                       (s > K && R_total > 0 ? 2 * (size_t)R_total * (size_t)K * 4 + 512 : 0);
+  // one view pipeline: every byte after the fixed part goes to the tile lists
+  const size_t fixed = scoup::uplift_required_bytes(scene->n, cams, V, s, K, R_total, 0);
   if (fixed > scoup::kNoAllocScratchBytes) {
     char msg[200];
     snprintf(msg, sizeof(msg),
@@ -79,9 +79,12 @@ int scoup_uplift_noalloc(const scoup_scene* scene, const scoup_camera* cams, int
   if (e != cudaSuccess)
     return scoup::set_error(SCOUP_ERR_CUDA, cudaGetErrorString(e));
   scoup_stats local;
-  return scoup_uplift(scene, cams, V, region_maps, map_offsets, R_total, code_idx, code_val, s, C, K,
-                      accum, accum_mode, topk_idx, topk_val, scratch, scoup::kNoAllocScratchBytes,
-                      stats ? stats : &local, stream);
+  const scoup::UpliftCall c{scene, cams, V, region_maps, map_offsets, R_total, code_idx, code_val, s, C, K,
+                            accum, accum_mode, topk_idx, topk_val};
+  const scoup::WsHeader* hdr = nullptr;
+  const int rc = scoup::uplift_call(c, scratch, scoup::kNoAllocScratchBytes, 8, &hdr, (cudaStream_t)stream, 1);
+  if (rc != SCOUP_OK) return rc;
+  return scoup::uplift_stats(hdr, stats ? stats : &local, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -144,7 +144,7 @@ __global__ void gather_kernel(const float* __restrict__ means, const float* __re
 __global__ void init_header_kernel(WsHeader* __restrict__ hdr) {
   const int t = threadIdx.x;
   if (t < 3) { hdr->bbox[t][0] = 0xffffffffu; hdr->bbox[t][1] = 0u; }
-  if (t < 2) { hdr->drange[t][0] = 0xffffffffu; hdr->drange[t][1] = 0u; }
+  if (t < 4) { hdr->drange[t][0] = 0xffffffffu; hdr->drange[t][1] = 0u; }
 }
 
 int grid_for(int64_t n, int per_sm) {

@@ -22,11 +22,12 @@ constexpr int kStatDeviceCheck = 2;
 constexpr int kStatTimeout = 4;
 
 // Workspace header: status word, per-view depth range (double-buffered by
-// view parity), scene bounding box and counters, 256 bytes.
+// view parity in each of the two view pipelines), scene bounding box and
+// counters, 256 bytes.
 struct WsHeader {
   int32_t status;
   int32_t max_dups_view;
-  uint32_t drange[2][2];  // [view & 1] = {min, max} float bits of visible depths
+  uint32_t drange[4][2];  // [2 lane + (view & 1)] = {min, max} float bits of visible depths
   uint32_t bbox[3][2];    // order-preserving bits of the means' bounding box
   unsigned long long visible;
   unsigned long long duplicates;
@@ -35,7 +36,7 @@ struct WsHeader {
   unsigned long long flushes;
   unsigned long long atomics;
   unsigned long long listed;
-  unsigned long long reserved[19];
+  unsigned long long reserved[17];
 };
 static_assert(sizeof(WsHeader) == 256, "header size");
 
@@ -157,8 +158,10 @@ struct UpliftCall {
 // Validates and enqueues one uplift on `st` without synchronising; warp_w is
 // the tile kernel's warp pixel-block width (8, 16 or 4).  *hdr_out receives
 // the workspace header that holds the call's status and counters.
+// view_lanes = 2 runs even and odd views in two pipelines (a second stream)
+// when the workspace holds both.
 int uplift_call(const UpliftCall& c, void* workspace, size_t ws_bytes, int warp_w, const struct WsHeader** hdr_out,
-                cudaStream_t st);
+                cudaStream_t st, int view_lanes = 1);
 size_t uplift_required_bytes(int64_t n, const scoup_camera* cams, int32_t V, int32_t s, int32_t K, int32_t R_total,
                              int64_t dup_capacity);
 int uplift_stats(const struct WsHeader* dev_hdr, scoup_stats* stats, cudaStream_t st);

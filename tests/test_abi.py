@@ -44,7 +44,7 @@ def test_version_and_sizes(lib):
     assert L.scoup_uplift_workspace_size(10, 0, 10, 0) == 0
     a = L.scoup_uplift_workspace_size(1000, 160, 120, 0)
     b = L.scoup_uplift_workspace_size(1000, 160, 120, 100)
-    assert b - a == 800 and a > 1000 * 32
+    assert b - a == 2 * 800 and a > 1000 * 32  # two view pipelines, 8 bytes per pair each
 
 
 def _call_uplift(lib, **kw):
