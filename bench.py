@@ -51,6 +51,8 @@ def parse_args():
                     help="views of the dense (D=512) vs sparse uplift comparison (0 = skip)")
     ap.add_argument("--level-views", type=int, default=20,
                     help="views of the three-level one-pass vs separate-pass comparison (0 = skip)")
+    ap.add_argument("--backward-views", type=int, default=8,
+                    help="views of the differentiable-render measurement (0 = skip)")
     ap.add_argument("--batch-scenes", type=int, default=16,
                     help="scenes of the batched-uplift measurement (0 = skip)")
     ap.add_argument("--decode-rows", type=int, default=0,
@@ -371,6 +373,10 @@ def run_gb300(args, dist):
     if args.dense_views > 0:
         dn = dense_leg(args, dist, wl, up, dev)
 
+    bw = None
+    if args.backward_views > 0:
+        bw = backward_leg(args, dist, dev)
+
     lv = None
     if args.level_views > 0:
         lv = levels_leg(args, dist, dev)
@@ -399,6 +405,7 @@ def run_gb300(args, dist):
             "render_decode": rd,
             "dense_vs_sparse": dn,
             "levels": lv,
+            "render_backward": bw,
             "batched": bt,
         }
         print(json.dumps(line), flush=True)
@@ -538,6 +545,62 @@ def dense_leg(args, dist, wl, up, dev):
     torch.cuda.empty_cache()
     return {"views": len(views), "workload": WORKLOAD, "accumulate_only": True, **out,
             "time_ratio_dense_over_sparse": out["dense_d512"]["ms"] / out["sparse_s8"]["ms"]}
+
+
+def backward_leg(args, dist, dev):
+    """Secondary measurement: the differentiable sparse render (500k Gaussians,
+    800x600 views, K = 8 of C = 256): per view the forward render and the
+    hand-written backward to the Top-K values and opacities, for a seeded
+    upstream gradient dL/dWhat.  MPix/s of forward + backward."""
+    import torch
+
+    import synth
+    import paper_2605_13600_gb300 as gb
+
+    rw = synth.render_cfg5()
+    cams = rw.cams[:max(1, args.backward_views)]
+    ren = gb.Render(rw.scene, rw.topk_idx, rw.topk_val, rw.C, cams, device=str(dev))
+    H, W = cams[0].height, cams[0].width
+    out = ren.outputs(cams[0])
+    gen = torch.Generator(device=dev).manual_seed(5)
+    g = torch.randn((H, W, rw.C), generator=gen, device=dev) * 1e-3
+    d_val = torch.zeros_like(ren.topk_val)
+    d_op = torch.zeros_like(ren.opacity)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+
+    def view(v):
+        cam = cams[v]
+        gb.scoup_render(ren.scene, ren.topk_idx, ren.topk_val, ren.K, ren.C, cam, out[0], out[1], out[2],
+                        ren.workspace, stats=False)
+        gb.scoup_render_backward(ren.scene, ren.topk_idx, ren.topk_val, ren.K, ren.C, cam, g, d_val, d_op,
+                                 ren.workspace)
+
+    for _ in range(max(2, args.warmup)):
+        view(0)
+    torch.cuda.synchronize()
+    dist.barrier()
+    ev[0].record(stream)
+    for v in range(len(cams)):
+        view(v)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    t = dist.max(ev[0].elapsed_time(ev[1]) / 1e3)
+    gb.scoup_profile_enable(True)
+    for v in range(len(cams)):
+        view(v)
+    torch.cuda.synchronize()
+    prof = gb.scoup_profile_read()
+    gb.scoup_profile_enable(False)
+    st = gb.scoup_read_stats(ren.workspace)
+    if st["status"] != 0:
+        raise RuntimeError("render backward status")
+    P = H * W
+    return {"metric": "render forward+backward pixels/s", "value": dist.world * len(cams) * P / t / 1e6,
+            "unit": "MPix/s", "workload": rw.name, "views_timed": len(cams), "pixels_per_view": P,
+            "C": rw.C, "K": rw.K, "ms_per_view": t * 1e3 / len(cams),
+            "phase_ms_per_view": {k: prof[k][0] / len(cams) for k in ("render", "render_bwd") if k in prof},
+            "gradient": "seeded N(0, 1e-3) dL/dWhat"}
 
 
 def levels_leg(args, dist, dev):
