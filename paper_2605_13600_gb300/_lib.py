@@ -120,6 +120,7 @@ PROTOS = {
     "scoup_plan_stats": (ct.c_int, [P, P, P]),
     "scoup_plan_info_get": (ct.c_int, [P, ct.POINTER(PlanInfo)]),
     "scoup_plan_destroy": (ct.c_int, [P]),
+    "scoup_selftest_gemm_timeout": (ct.c_int, [P, SZ, P]),
     "scoup_profile_enable": (ct.c_int, [I32]),
     "scoup_profile_read": (ct.c_int, [P, P, I32]),
     "scoup_launch_count": (I64, []),

@@ -805,6 +805,14 @@ int scoup_relevancy(const float* sim, int64_t P, int32_t ncols, int32_t n_canon,
   return e == cudaSuccess ? SCOUP_OK : cuda_fail(e, "relevancy");
 }
 
+int scoup_selftest_gemm_timeout(void* workspace, size_t ws_bytes, void* stream) {
+  if (!gemm_tma_available()) return fail(SCOUP_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+  const int rc = gemm_timeout_selftest(workspace, ws_bytes, (cudaStream_t)stream);
+  if (rc == SCOUP_ERR_TIMEOUT) return fail(rc, "tensor-core pipeline wait ran out (self-test, expected)");
+  if (rc != SCOUP_OK) return fail(rc, "self-test could not run (workspace must hold 49408 bytes, 256-byte aligned)");
+  return fail(SCOUP_ERR_DEVICE_CHECK, "self-test: the stalled pipeline did not report a timeout");
+}
+
 int scoup_read_stats(const void* workspace, size_t ws_bytes, scoup_stats* stats, void* stream) {
   if (!workspace || ws_bytes < sizeof(WsHeader)) return fail(SCOUP_ERR_INVALID_ARG, "bad workspace");
   if (!stats) return fail(SCOUP_ERR_INVALID_ARG, "stats is NULL");

@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_bf16_kernel(const __grid
   if (warp == 0 && lane == 0) {
     // ---- TMA producer ----
     int it = 0;
-    for (int u = blockIdx.x; u < units && !sm.abort; u += gridDim.x) {
+    for (int u = blockIdx.x; u < units && !sm.abort && !ep.stall_loads; u += gridDim.x) {
       const int m0 = (u / n_tiles) * BM, n0 = (u % n_tiles) * BN;
       for (int kb = 0; kb < kt; ++kb, ++it) {
         const int s = it % kStages;
@@ -386,5 +386,36 @@ cudaError_t launch_row_norm_bf16(const void* X, int64_t R, int D, float* out, in
 }
 
 bool gemm_tma_available() { return encode_fn() != nullptr; }
+
+// Runs a 128 x 64 x 64 GEMM whose producer issues no loads: the MMA and
+// epilogue warps' bounded waits run out, the kernel records kStatTimeout and
+// frees its TMEM, and the context stays usable.  Returns the device status.
+int gemm_timeout_selftest(void* workspace, size_t ws_bytes, cudaStream_t st) {
+  const size_t need = 256 + 3 * (size_t)128 * 64 * 2;
+  if (!workspace || ws_bytes < need || ((uintptr_t)workspace & 255u)) return SCOUP_ERR_INVALID_ARG;
+  char* w = (char*)workspace;
+  int* status = (int*)w;
+  void* A = w + 256;
+  void* B = (char*)A + 128 * 64 * 2;
+  void* out = (char*)B + 128 * 64 * 2;
+  if (cudaMemsetAsync(w, 0, need, st) != cudaSuccess) return SCOUP_ERR_CUDA;
+  GemmEpi ep;
+  ep.M = 128;
+  ep.N = 64;
+  ep.K = 64;
+  ep.mode = kOutBF16;
+  ep.out = out;
+  ep.ldo = 64;
+  ep.rownorm2 = nullptr;
+  ep.colnorm = nullptr;
+  ep.status = status;
+  ep.stall_loads = 1;
+  if (launch_gemm_bf16(A, B, ep, st) != cudaSuccess) return SCOUP_ERR_CUDA;
+  int h = 0;
+  if (cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return SCOUP_ERR_CUDA;
+  return (h & kStatTimeout) ? SCOUP_ERR_TIMEOUT : SCOUP_OK;
+}
 
 }  // namespace scoup

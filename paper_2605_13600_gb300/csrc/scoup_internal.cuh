@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "../../include/scoup.h"
+#include "../../include/scoup_selftest.h"
 
 #include <atomic>
 
@@ -195,12 +196,14 @@ struct GemmEpi {
   float* rownorm2;       // kOutBF16: accumulated squared row norms (may be null); kOutCos: input
   const float* colnorm;  // kOutCos: column norms
   int* status;
+  int stall_loads = 0;   // self-test only: the producer issues no loads, so the bounded waits run out
 };
 cudaError_t launch_gemm_bf16(const void* A, const void* Bt, const GemmEpi& ep, cudaStream_t st);
 cudaError_t launch_f32_to_bf16(const float* x, void* y, int64_t n, cudaStream_t st);
 cudaError_t launch_transpose_bf16(const float* B, void* Bt, int Cdim, int D, cudaStream_t st);
 cudaError_t launch_row_norm_bf16(const void* X, int64_t R, int D, float* out, int squared, cudaStream_t st);
 bool gemm_tma_available();
+int gemm_timeout_selftest(void* workspace, size_t ws_bytes, cudaStream_t st);
 cudaError_t launch_sgemm(const float* A, const float* B, bool b_transposed, float* out, int64_t M, int N, int K,
                          const float* rownorm2, const float* colnorm2, cudaStream_t st);
 cudaError_t launch_row_norm2_f32(const float* X, int64_t R, int D, float* out, cudaStream_t st);

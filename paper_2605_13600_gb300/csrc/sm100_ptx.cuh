@@ -43,11 +43,27 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Non-blocking test of the phase with the given parity.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 // Bounded wait: returns false after max_iters failed polls (the caller then
-// records an error and leaves instead of spinning forever).
+// records an error and leaves instead of spinning forever).  Polls with the
+// non-blocking test (a blocking try_wait may hold for a system-dependent time
+// per poll), backing off with nanosleep after the first 64 polls, so the
+// bound is max_iters x (a poll + at most 128 ns).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t max_iters) {
   for (uint32_t i = 0; i < max_iters; ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_test_wait(bar, parity)) return true;
     if (i > 64) __nanosleep(64);
   }
   return false;

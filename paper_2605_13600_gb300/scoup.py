@@ -357,6 +357,16 @@ def scoup_relevancy(sim, n_canon: int, R, alpha: float = 10.0, stream=None) -> N
     check(load().scoup_relevancy(_ptr(sim), P, ncols, int(n_canon), float(alpha), _ptr(R), _stream(stream)))
 
 
+def scoup_selftest_gemm_timeout(stream=None) -> tuple:
+    """Self-test of the tensor-core pipeline's bounded waits: (status code, message).
+    SCOUP_ERR_TIMEOUT is the expected result."""
+    import torch
+    ws = torch.empty(49408, dtype=torch.uint8, device="cuda")
+    rc = load().scoup_selftest_gemm_timeout(_ptr(ws), ws.numel(), _stream(stream))
+    msg = load().scoup_last_error()
+    return int(rc), (msg.decode() if msg else "")
+
+
 def scoup_read_stats(workspace, stream=None) -> dict:
     st = Stats()
     check(load().scoup_read_stats(_ptr(workspace), workspace.numel(), ct.byref(st), _stream(stream)))
@@ -595,4 +605,4 @@ __all__ = ["ScoupError", "SCOUP_ACCUM_CONTINUE", "SCOUP_ACCUM_COMPENSATED", "sce
            "scoup_render", "scoup_render_backward", "Render", "Uplift",
            "scoup_decode_workspace_size", "scoup_decode", "scoup_similarity_workspace_size",
            "scoup_similarity", "scoup_decode_fp32", "scoup_similarity_fp32", "BatchedUplift",
-           "SCOUP_BATCH_EAGER", "LevelUplift", "scoup_topk_entropy", "scoup_entropy_filter", "scoup_relevancy"]
+           "SCOUP_BATCH_EAGER", "LevelUplift", "scoup_selftest_gemm_timeout", "scoup_topk_entropy", "scoup_entropy_filter", "scoup_relevancy"]
