@@ -80,9 +80,8 @@ struct TileSmem {
   uint32_t bstart[kNB + 1];
   uint32_t bcur[kNB];
   unsigned long long win[kWin];
-  float4 stage_a[kThreads / 32][32];
-  float4 stage_b[kThreads / 32][32];
-  int stage_g[kThreads / 32][32];
+  float4 rec_a[kWin];  // the window's projected records, loaded once per window
+  float4 rec_b[kWin];
   float part[kMaxSlots][kWin];
   float part_c[kComp ? kMaxSlots : 1][kComp ? kWin : 1];
   uint32_t nz[kMaxSlots][kWin / 32];  // window entries whose partial became non-zero
@@ -491,21 +490,26 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
     }
 
     // ---- composite the window: every warp walks it on its own ----
-    // Each lane stages one of the next 32 records and tests it against the
-    // warp's 8x4 pixel block (box_may_hit); the warp then composites only the
-    // Gaussians that can reach one of its pixels, in window order.
+    // The CTA loads the window's records into shared memory once (one per
+    // thread, all loads in flight together).  Each lane then tests one of the
+    // next 32 records against the warp's pixel block (box_may_hit); the warp
+    // composites only the Gaussians that can reach one of its pixels, in
+    // window order.
+    for (int j = tid; j < m; j += kThreads) {
+      const ProjRec pr = proj[(int)(sm.win[j] & 0xffffffffull)];
+      sm.rec_a[j] = pr.a;
+      sm.rec_b[j] = pr.b;
+    }
+    __syncthreads();
     bool warp_done = __all_sync(kFull, done);
-    float4* st_a = sm.stage_a[warp];
-    float4* st_b = sm.stage_b[warp];
-    int* st_g = sm.stage_g[warp];
+    const float4* st_a = sm.rec_a;
+    const float4* st_b = sm.rec_b;
     for (int j0 = 0; j0 < m && !warp_done; j0 += 32) {
       bool rel = false;
       if (j0 + lane < m) {
-        const int g = (int)(sm.win[j0 + lane] & 0xffffffffull);
-        const ProjRec pr = proj[g];
-        st_a[lane] = pr.a;
-        st_b[lane] = pr.b;
-        st_g[lane] = g;
+        ProjRec pr;
+        pr.a = st_a[j0 + lane];
+        pr.b = st_b[j0 + lane];
         rel = box_may_hit(pr, bx0, by0, (float)kBW, (float)kBH);
       }
       unsigned rmask = __ballot_sync(kFull, rel);
@@ -522,8 +526,8 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
         for (int u = 0; u < kGroup; ++u) {
           // branch-free: every lane evaluates, inactive lanes discard the result
           const int q = idx[u] < 0 ? 0 : idx[u];
-          const float4 a = st_a[q];
-          const float4 b = st_b[q];
+          const float4 a = st_a[j0 + q];
+          const float4 b = st_b[j0 + q];
           const bool live = idx[u] >= 0 && !done;
           const float dx = a.x - fpx, dy = a.y - fpy;
           // power = dx*(qa*dx + qb*dy) + (qc*dy)*dy: products rounded, two fused sums
@@ -567,7 +571,7 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
 #pragma unroll
             for (int u = 0; u < kGroup; ++u) {
               if (!(e[u] > 0.0f)) continue;
-              const int64_t g = st_g[idx[u]];
+              const int64_t g = (int64_t)(sm.win[j0 + idx[u]] & 0xffffffffull);
               for (int l = 0; l < (kL == 1 ? 1 : lc.L); ++l) {
                 int r;
                 if constexpr (kL == 1) r = region; else r = level_region(region, l);
