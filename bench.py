@@ -429,7 +429,7 @@ def render_decode_leg(args, dist, wl, up, dev, pk):
     H, W = cams[0].height, cams[0].width
     P = H * W
     D, Q = rw.codebook.shape[1], rw.text.shape[0]
-    out = ren.outputs(cams[0])
+    out = ren.outputs(cams[0], dtype=torch.bfloat16)  # bf16 codes: the decode's input type
     codebook = torch.from_numpy(rw.codebook).to(dev)
     text = torch.from_numpy(rw.text).to(dev)
     feats = torch.empty((P, D), dtype=torch.bfloat16, device=dev)
@@ -474,7 +474,7 @@ def render_decode_leg(args, dist, wl, up, dev, pk):
         raise RuntimeError("decode/similarity device status")
 
     # the decode GEMM alone: bf16 codes in, bf16 features out (one launch + a 256x512 transpose)
-    codes_bf16 = out[0].view(P, wl.C).to(torch.bfloat16)
+    codes_bf16 = out[0].view(P, wl.C)
     for _ in range(3):
         gb.scoup_decode(codes_bf16, codebook, feats, n2, workspace=dws)
     torch.cuda.synchronize()
@@ -487,7 +487,6 @@ def render_decode_leg(args, dist, wl, up, dev, pk):
     t_gemm = ev0.elapsed_time(ev1) / 1e3 / reps
     flops = 2.0 * P * wl.C * D
     gemm_bytes = 2.0 * P * wl.C + 2.0 * P * D
-    del codes_bf16
     evaluated = sum(s["evaluated_pairs"] for s in stats) / len(stats)
     contrib = sum(s["contributions"] for s in stats) / len(stats)
     return {

@@ -192,7 +192,11 @@ int scoup_read_stats(const void* workspace, size_t ws_bytes, scoup_stats* stats,
  * to back order with the same compositing as scoup_uplift (Eq. 2), where
  * w^_i is Gaussian i's K-sparse code (topk_idx[i][k] < C or -1 padding,
  * topk_val[i][k]).  The result is the dense, unnormalised C-vector per pixel.
- *  out_codes  float32 [H, W, C] row-major (every pixel written).
+ *  out_codes  [H, W, C] row-major (every pixel written): float32 with
+ *             out_dtype 0, bf16 (round to nearest even) with out_dtype 1 --
+ *             the input scoup_decode takes without conversion.  A pixel whose
+ *             list spans w windows of 256 entries is rounded to bf16 after
+ *             each window: relative error at most w 2^-8 (bf16 unit roundoff).
  *  out_T      float32 [H, W] final transmittance, or NULL.
  *  out_last   int32 [H, W]: number of front-to-back list entries up to and
  *             including the last contributor of the pixel, or NULL.
@@ -201,8 +205,8 @@ int scoup_read_stats(const void* workspace, size_t ws_bytes, scoup_stats* stats,
  *  stats      HOST or NULL; when given, the call synchronises `stream`.
  * Limits: 1 <= K <= C <= 1024. */
 int scoup_render(const scoup_scene* scene, const int32_t* topk_idx, const float* topk_val, int32_t K,
-                 int32_t C, const scoup_camera* cam, float* out_codes, float* out_T, int32_t* out_last,
-                 void* workspace, size_t ws_bytes, scoup_stats* stats, void* stream);
+                 int32_t C, const scoup_camera* cam, void* out_codes, int32_t out_dtype, float* out_T,
+                 int32_t* out_last, void* workspace, size_t ws_bytes, scoup_stats* stats, void* stream);
 
 /* Gradient through scoup_render (derived from Eq. 2 and Eq. 7) for a loss
  * whose gradient with respect to the rendered codes is dL_dcodes (float32

@@ -95,7 +95,7 @@ PROTOS = {
     "scoup_topk": (ct.c_int, [P, I64, I32, I32, P, P, P]),
     "scoup_uplift_levels": (ct.c_int, [ct.POINTER(Scene), P, I32, P, P, I32, I32, I32, P, I32, P, P, P, SZ,
                                        ct.POINTER(Stats), P]),
-    "scoup_render": (ct.c_int, [ct.POINTER(Scene), P, P, I32, I32, ct.POINTER(Camera), P, P, P, P, SZ,
+    "scoup_render": (ct.c_int, [ct.POINTER(Scene), P, P, I32, I32, ct.POINTER(Camera), P, I32, P, P, P, SZ,
                                 ct.POINTER(Stats), P]),
     "scoup_render_backward": (ct.c_int, [ct.POINTER(Scene), P, P, I32, I32, ct.POINTER(Camera), P, P, P, P,
                                          SZ, ct.POINTER(Stats), P]),

@@ -511,8 +511,8 @@ int scoup_uplift_levels(const scoup_scene* scene, const scoup_camera* cams, int3
 }
 
 int scoup_render(const scoup_scene* scene, const int32_t* topk_idx, const float* topk_val, int32_t K,
-                 int32_t C, const scoup_camera* cam, float* out_codes, float* out_T, int32_t* out_last,
-                 void* workspace, size_t ws_bytes, scoup_stats* stats, void* stream) {
+                 int32_t C, const scoup_camera* cam, void* out_codes, int32_t out_dtype, float* out_T,
+                 int32_t* out_last, void* workspace, size_t ws_bytes, scoup_stats* stats, void* stream) {
   int rc = check_scene(scene);
   if (rc) return rc;
   int max_tiles = 1;
@@ -520,6 +520,7 @@ int scoup_render(const scoup_scene* scene, const int32_t* topk_idx, const float*
   if (C < 1 || C > 1024) return fail(SCOUP_ERR_INVALID_ARG, "C=%d outside [1, 1024]", C);
   if (K < 1 || K > C) return fail(SCOUP_ERR_INVALID_ARG, "K=%d outside [1, C=%d]", K, C);
   if (!out_codes) return fail(SCOUP_ERR_INVALID_ARG, "out_codes is NULL");
+  if (out_dtype != 0 && out_dtype != 1) return fail(SCOUP_ERR_INVALID_ARG, "out_dtype must be 0 (f32) or 1 (bf16)");
   if (scene->n > 0 && (!topk_idx || !topk_val)) return fail(SCOUP_ERR_INVALID_ARG, "Top-K arrays are NULL");
   if (!workspace) return fail(SCOUP_ERR_INVALID_ARG, "workspace is NULL");
   if (render_smem_bytes(C, K) > 227 * 1024)
@@ -552,7 +553,7 @@ int scoup_render(const scoup_scene* scene, const int32_t* topk_idx, const float*
   }
   {
     PhaseScope ps(SCOUP_PHASE_RENDER, st);
-    if ((e = launch_render_tiles(ca, ws, 0, topk_idx, topk_val, K, C, out_codes, out_T, out_last, st)) !=
+    if ((e = launch_render_tiles(ca, ws, 0, topk_idx, topk_val, K, C, out_codes, out_dtype, out_T, out_last, st)) !=
         cudaSuccess)
       return cuda_fail(e, "render tiles");
   }

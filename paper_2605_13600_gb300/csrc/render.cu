@@ -17,7 +17,10 @@
 // lanes of a warp read consecutive words) whenever they fit, so the
 // per-contribution reads never leave the SM.  A pixel's row is written once
 // per window (coalesced); a pixel still open at the end of a window keeps its
-// partial row in the output and resumes from it in the next window.
+// partial row in the output and resumes from it in the next window.  With
+// bf16 output the row is rounded on every write, so a pixel spanning w
+// windows carries at most w roundings (relative error <= w 2^-8).
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include "tile_order.cuh"
@@ -129,9 +132,15 @@ __device__ __forceinline__ bool walk_pixel(RenderSmem& sm, int m, int wbase, flo
   return false;
 }
 
-__device__ __forceinline__ void write_row(float* __restrict__ out_row, const float* acc, int C) {
+__device__ __forceinline__ void write_row(void* __restrict__ out, int64_t pix, bool bf16, const float* acc, int C) {
   const int lane = threadIdx.x & 31;
-  for (int c = lane; c < C; c += 32) out_row[c] = acc[c] + acc[C + 16 + c];
+  if (bf16) {
+    __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(out) + pix * C;
+    for (int c = lane; c < C; c += 32) o[c] = __float2bfloat16_rn(acc[c] + acc[C + 16 + c]);
+  } else {
+    float* o = reinterpret_cast<float*>(out) + pix * C;
+    for (int c = lane; c < C; c += 32) o[c] = acc[c] + acc[C + 16 + c];
+  }
 }
 
 // 4 CTAs per SM (64 registers): the walk is latency-bound and occupancy pays
@@ -140,7 +149,7 @@ template <bool kStaged>
 __global__ void __launch_bounds__(kRThreads, 4) render_tile_kernel(
     CamArgs cam, const ProjRec* __restrict__ proj, const unsigned long long* __restrict__ keys,
     const uint32_t* __restrict__ tile_start, int slot, const int32_t* __restrict__ topk_idx,
-    const float* __restrict__ topk_val, int K, int C, float* __restrict__ out, float* __restrict__ out_T,
+    const float* __restrict__ topk_val, int K, int C, void* __restrict__ out, int out_bf16, float* __restrict__ out_T,
     int32_t* __restrict__ out_last, WsHeader* __restrict__ hdr) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RenderSmem& sm = *reinterpret_cast<RenderSmem*>(smem_raw);
@@ -196,11 +205,16 @@ __global__ void __launch_bounds__(kRThreads, 4) render_tile_kernel(
       if (p >= kTilePixels) break;
       if (sm.done[p]) continue;
       const int px = tx * kTile + (p & (kTile - 1)), py = ty * kTile + (p >> 4);
-      float* row = out + ((int64_t)py * cam.width + px) * C;
+      const int64_t pix = (int64_t)py * cam.width + px;
       if (first_window) {
         for (int c = lane; c < C; c += 32) { acc[c] = 0.0f; acc[C + 16 + c] = 0.0f; }
       } else {
-        for (int c = lane; c < C; c += 32) { acc[c] = row[c]; acc[C + 16 + c] = 0.0f; }  // partial row of an earlier window
+        // partial row of an earlier window
+        for (int c = lane; c < C; c += 32) {
+          acc[c] = out_bf16 ? __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(out)[pix * C + c])
+                            : reinterpret_cast<const float*>(out)[pix * C + c];
+          acc[C + 16 + c] = 0.0f;
+        }
       }
       __syncwarp();
       float T = sm.T[p];
@@ -208,7 +222,7 @@ __global__ void __launch_bounds__(kRThreads, 4) render_tile_kernel(
       const bool fin = m > 0 && walk_pixel<kStaged>(sm, m, wbase, (float)px, (float)py, T, last, acc, topk_idx,
                                                     topk_val, sc, K, C, n_eval, n_contrib);
       __syncwarp();
-      write_row(row, acc, C);
+      write_row(out, pix, out_bf16 != 0, acc, C);
       if (lane == 0) {
         sm.T[p] = T;
         sm.last[p] = last;
@@ -249,7 +263,7 @@ size_t render_smem_bytes(int C, int K) {
 }
 
 cudaError_t launch_render_tiles(const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* topk_idx,
-                                const float* topk_val, int K, int C, float* out, float* out_T,
+                                const float* topk_val, int K, int C, void* out, int out_bf16, float* out_T,
                                 int32_t* out_last, cudaStream_t st) {
   const int ntiles = cam.gx * cam.gy;
   if (ntiles <= 0) return cudaSuccess;
@@ -260,10 +274,10 @@ cudaError_t launch_render_tiles(const CamArgs& cam, const UpliftWs& ws, int slot
   if (err != cudaSuccess) return err;
   if (staged)
     render_tile_kernel<true><<<ntiles, kRThreads, smem, st>>>(cam, ws.proj, ws.keys, ws.tile_start, slot, topk_idx,
-                                                              topk_val, K, C, out, out_T, out_last, ws.hdr);
+                                                              topk_val, K, C, out, out_bf16, out_T, out_last, ws.hdr);
   else
     render_tile_kernel<false><<<ntiles, kRThreads, smem, st>>>(cam, ws.proj, ws.keys, ws.tile_start, slot,
-                                                               topk_idx, topk_val, K, C, out, out_T, out_last,
+                                                               topk_idx, topk_val, K, C, out, out_bf16, out_T, out_last,
                                                                ws.hdr);
   g_launches += 1;
   return cudaGetLastError();

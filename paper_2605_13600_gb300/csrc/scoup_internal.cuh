@@ -181,7 +181,7 @@ cudaError_t launch_uplift_tiles(const CamArgs& cam, const UpliftWs& ws, int slot
                                 int Crow, float* accum, float* comp, int warp_w, cudaStream_t st);
 size_t render_smem_bytes(int C, int K);
 cudaError_t launch_render_tiles(const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* topk_idx,
-                                const float* topk_val, int K, int C, float* out, float* out_T,
+                                const float* topk_val, int K, int C, void* out, int out_bf16, float* out_T,
                                 int32_t* out_last, cudaStream_t st);
 size_t render_bwd_smem_bytes(int C, int K);
 cudaError_t launch_render_bwd(const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* topk_idx,

@@ -152,18 +152,21 @@ def scoup_topk(accum, K: int, topk_idx, topk_val, stream=None) -> None:
 
 def scoup_render(scene: Scene, topk_idx, topk_val, K: int, C: int, cam, out_codes, out_T, out_last,
                  workspace, stats: bool = True, stream=None):
-    """Eq. 7 for one view into out_codes [H, W, C] (float32); returns stats when stats=True."""
+    """Eq. 7 for one view into out_codes [H, W, C] (float32 or bfloat16); returns stats when stats=True."""
     import torch
     _need(topk_idx, torch.int32, "topk_idx")
     _need(topk_val, torch.float32, "topk_val")
-    _need(out_codes, torch.float32, "out_codes")
+    if out_codes.dtype not in (torch.float32, torch.bfloat16):
+        raise TypeError("out_codes must be float32 or bfloat16")
+    _need(out_codes, out_codes.dtype, "out_codes")
     _need(out_T, torch.float32, "out_T")
     _need(out_last, torch.int32, "out_last")
     _need(workspace, torch.uint8, "workspace")
     ca = camera_array([cam])
     st = Stats()
     check(load().scoup_render(ct.byref(scene), _ptr(topk_idx), _ptr(topk_val), int(K), int(C),
-                              ct.cast(ca, ct.POINTER(Camera)), _ptr(out_codes), _ptr(out_T), _ptr(out_last),
+                              ct.cast(ca, ct.POINTER(Camera)), _ptr(out_codes),
+                              1 if out_codes.dtype == torch.bfloat16 else 0, _ptr(out_T), _ptr(out_last),
                               _ptr(workspace), workspace.numel(), ct.byref(st) if stats else None,
                               _stream(stream)))
     return st.as_dict() if stats else None
@@ -216,10 +219,10 @@ class Render:
                                      dtype=torch.uint8, device=dev)
         self.device = dev
 
-    def outputs(self, cam):
+    def outputs(self, cam, dtype=None):
         import torch
         H, W = cam.height, cam.width
-        return (torch.empty((H, W, self.C), dtype=torch.float32, device=self.device),
+        return (torch.empty((H, W, self.C), dtype=dtype or torch.float32, device=self.device),
                 torch.empty((H, W), dtype=torch.float32, device=self.device),
                 torch.empty((H, W), dtype=torch.int32, device=self.device))
 

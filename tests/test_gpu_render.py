@@ -99,3 +99,56 @@ def test_render_uplifted_codes(gb, oracle_lib, cfg1, cfg1_oracle):
         Wg, Tg, lastg, st, Wo, To, risk, cnt = _render_pair(gb, oracle_lib, cfg1.scene, idx, val, cfg1.C,
                                                            cfg1.cams[v])
         check_render(Wg, Tg, Wo, To, risk)
+
+
+@pytest.mark.parametrize("case", ["random", "long_lists"])
+def test_render_bf16_output(gb, oracle_lib, case):
+    """bf16 output: the FP32 row rounded once per window the pixel spans
+    (relative error at most windows x 2^-8 on top of the FP32 tolerance)."""
+    import torch
+    if case == "random":
+        wl = synth.tiny_workload(57, n=3000, width=130, height=70, V=1, log_scale_mean=-3.0)
+        C, K = 256, 8
+    else:
+        wl = synth.tiny_workload(56, n=6000, width=48, height=32, V=1, log_scale_mean=-2.0)
+        wl.scene.opacity[:] = np.minimum(wl.scene.opacity, 0.06)
+        C, K = 32, 4
+    rng = np.random.default_rng(57)
+    idx, val = synth.sparse_topk_codes(rng, wl.scene.n, C, K)
+    r = gb.Render(wl.scene, idx, val, C, [wl.cams[0]])
+    (W32, T32, last), _ = r.run(0)
+    outb = r.outputs(wl.cams[0], dtype=torch.bfloat16)
+    (Wb, Tb, lastb), st = r.run(0, out=outb)
+    assert st["status"] == 0
+    Wo, To, risk, _ = oracle_lib.render(wl.scene, idx, val.astype(np.float64), C, wl.cams[0])
+    windows = np.ceil(np.maximum(last.cpu().numpy(), 1) / 256.0)[..., None] + 1.0
+    err = np.abs(Wb.float().cpu().numpy().astype(np.float64) - Wo)
+    scale = np.abs(Wo).max(axis=-1, keepdims=True)
+    tol = windows * 2.0 ** -8 * np.abs(Wo) + 1e-4 * np.abs(Wo) + 1e-6 * scale + 1e-7
+    tol = np.where(risk[..., None], 1e-2 + tol, tol)
+    assert (err <= tol).all(), float((err - tol).max())
+    # transmittance and counts do not depend on the output type
+    assert torch.equal(Tb, T32) and torch.equal(lastb, last)
+
+
+def test_render_bf16_feeds_decode(gb):
+    """bf16 rendered codes go to the decode without conversion (codes_dtype 1):
+    the result equals decoding the same values handed over as float32 (which
+    the decode rounds to the same bf16 numbers)."""
+    import torch
+    wl = synth.tiny_workload(58, n=2000, width=64, height=48, V=1)
+    rng = np.random.default_rng(58)
+    C, K, D = 64, 4, 32
+    idx, val = synth.sparse_topk_codes(rng, wl.scene.n, C, K)
+    B = torch.from_numpy(synth.unit_rows(rng, C, D)).cuda()
+    r = gb.Render(wl.scene, idx, val, C, [wl.cams[0]])
+    outb = r.outputs(wl.cams[0], dtype=torch.bfloat16)
+    (Wb, _, _), _ = r.run(0, out=outb)
+    P = wl.cams[0].width * wl.cams[0].height
+    f_direct = torch.empty((P, D), dtype=torch.float32, device="cuda")
+    f_conv = torch.empty((P, D), dtype=torch.float32, device="cuda")
+    gb.scoup_decode(Wb.view(P, C), B, f_direct)
+    gb.scoup_decode(Wb.view(P, C).float().contiguous(), B, f_conv)
+    torch.cuda.synchronize()
+    assert torch.equal(f_direct, f_conv)
+    assert f_direct.abs().sum() > 0
