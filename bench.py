@@ -299,12 +299,14 @@ def run_gb300(args, dist):
     pk = peaks()
     V = len(up.cams)
     contrib_per_launch = contrib / V
-    # FP32-pipe work every accepted Gaussian-pixel pair needs under Eq. 2 (a lower
-    # bound for any implementation): exponent 2 subtractions + 3 products + 2 fused
-    # sums, 2 threshold compares, exp argument scale, alpha = o*exp, min with 0.99,
-    # 1 - alpha, T(1 - alpha), stop compare, e = alpha*T  -> 16 ops (the exp itself
-    # runs on the SFU and is not counted)
-    ops = 16.0 * contrib_per_launch
+    evaluated_per_launch = st0["evaluated_pairs"] / V
+    # FP32-pipe work of Eq. 2 for every evaluated Gaussian-pixel pair, accepted
+    # or not (a lower bound for any implementation; the exp runs on the SFU and
+    # is not counted, nor e = alpha T of the accepted pairs): exponent 2
+    # subtractions + 3 products + 2 fused sums, 2 threshold compares, exp
+    # argument scale, alpha = o exp, min with 0.99, 1 - alpha, T (1 - alpha),
+    # stop compare -> 15 operations
+    ops = 15.0 * evaluated_per_launch
     alu_peak = 152 * 128 * pk["sm_max_mhz"] * 1e6  # FP32 lanes x max SM clock
     achieved = ops / per_launch_s
     npx = up.cams[0].width * up.cams[0].height
@@ -320,6 +322,7 @@ def run_gb300(args, dist):
                              "achieved_gbs": bytes_launch / per_launch_s / 1e9,
                              "peak_gbs": pk["hbm_gbs"],
                              "frac": bytes_launch / per_launch_s / 1e9 / pk["hbm_gbs"]},
+                "ops_per_launch": ops, "op_count": "15 FP32 ops per evaluated pair (exp on the SFU not counted)",
                 "peak_source": pk["source"] + " (HBM); FP32 lanes x max SM clock (ALU)"}
 
     # end to end through the public API with host buffers
