@@ -4,7 +4,8 @@
 // pixel (unnormalised), plus the final transmittance and the list position of
 // the last contributor (for the backward pass).
 //
-// One CTA per 16x16 tile.  The tile's key list is ordered window by window
+// This is the SIMT form, used for code rows wider than the tensor-core
+// kernel takes (render_mma.cu).  One CTA per 16x16 tile.  The tile's key list is ordered window by window
 // exactly as in the uplift (tile_order.cuh) and the window's records are
 // staged in shared memory.  Each warp then takes pixels one at a time from a
 // shared counter and walks the window 32 Gaussians per round: every lane
@@ -22,6 +23,7 @@
 // windows carries at most w roundings (relative error <= w 2^-8).
 #include <cuda_bf16.h>
 #include <math.h>
+#include <stdlib.h>
 
 #include "tile_order.cuh"
 
@@ -257,7 +259,15 @@ size_t staged_bytes(int K) { return (size_t)K * ROrder::kWin * (sizeof(float) + 
 
 bool render_stages(int K) { return staged_bytes(K) <= kStageMaxBytes; }
 
+// The tensor-core kernel (render_mma.cu) takes every shape it supports;
+// SCOUP_RENDER_SIMT=1 in the environment selects this kernel instead.
+bool render_uses_mma(int C, int K) {
+  const char* f = getenv("SCOUP_RENDER_SIMT");
+  return render_mma_supported(C, K) && !(f && f[0] == '1');
+}
+
 size_t render_smem_bytes(int C, int K) {
+  if (render_uses_mma(C, K)) return render_mma_smem_bytes();
   return sizeof(RenderSmem) + sizeof(float) * (size_t)kRWarps * (size_t)(2 * C + 16) +
          (render_stages(K) ? staged_bytes(K) : 0);
 }
@@ -265,6 +275,8 @@ size_t render_smem_bytes(int C, int K) {
 cudaError_t launch_render_tiles(const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* topk_idx,
                                 const float* topk_val, int K, int C, void* out, int out_bf16, float* out_T,
                                 int32_t* out_last, cudaStream_t st) {
+  if (render_uses_mma(C, K))
+    return launch_render_mma(cam, ws, slot, topk_idx, topk_val, K, C, out, out_bf16, out_T, out_last, st);
   const int ntiles = cam.gx * cam.gy;
   if (ntiles <= 0) return cudaSuccess;
   const size_t smem = render_smem_bytes(C, K);

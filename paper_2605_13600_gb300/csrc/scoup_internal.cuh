@@ -180,6 +180,12 @@ cudaError_t launch_binning(const CamArgs& cam, int64_t n, const UpliftWs& ws, in
 cudaError_t launch_uplift_tiles(const CamArgs& cam, const UpliftWs& ws, int slot, const LevelCodes& lc, int C,
                                 int Crow, float* accum, float* comp, int warp_w, cudaStream_t st);
 size_t render_smem_bytes(int C, int K);
+bool render_uses_mma(int C, int K);
+bool render_mma_supported(int C, int K);
+size_t render_mma_smem_bytes();
+cudaError_t launch_render_mma(const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* topk_idx,
+                              const float* topk_val, int K, int C, void* out, int out_bf16, float* out_T,
+                              int32_t* out_last, cudaStream_t st);
 cudaError_t launch_render_tiles(const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* topk_idx,
                                 const float* topk_val, int K, int C, void* out, int out_bf16, float* out_T,
                                 int32_t* out_last, cudaStream_t st);

@@ -180,6 +180,19 @@ __device__ __forceinline__ uint64_t smem_desc_k128(uint32_t saddr) {
   return d;
 }
 
+// Shared-memory matrix descriptor of a K-major tile without swizzling, built
+// from 8-row x 16-byte core matrices: lbo = byte distance between core
+// matrices adjacent along K, sbo = byte distance between adjacent 8-row
+// groups; tile base 16-byte aligned.
+__device__ __forceinline__ uint64_t smem_desc_kmajor_none(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3fffu);        // start address
+  d |= (uint64_t)((lbo >> 4) & 0x3fffu) << 16;    // leading byte offset
+  d |= (uint64_t)((sbo >> 4) & 0x3fffu) << 32;    // stride byte offset
+  d |= (uint64_t)1u << 46;                        // descriptor version (tcgen05)
+  return d;                                       // layout bits 61-63 = 0: no swizzle
+}
+
 // Instruction descriptor, kind::f16: f32 accumulate, bf16 A and B, both
 // K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {

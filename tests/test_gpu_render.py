@@ -2,8 +2,10 @@
 
 Per pixel the dense C-vector, the final transmittance and the contribution
 count are compared on seeded scenes with ragged image sizes, a one-hot round
-trip, long tile lists (several windows), and Top-K codes produced by the GPU
-uplift itself.
+trip, long tile lists (several windows), and Top-K codes from the oracle's
+uplift.  Code rows up to 256 wide (Top-K up to 16) take the tensor-core
+kernel; wider rows, and any shape with SCOUP_RENDER_SIMT=1, the SIMT kernel,
+which is checked here on the same cases.
 """
 import numpy as np
 import pytest
@@ -66,8 +68,16 @@ def test_render_random_codes(gb, oracle_lib, seed, W, H, n, C, K, lsm):
     assert (lastg >= 0).all()
 
 
-def test_render_one_hot_round_trip(gb, oracle_lib):
-    """Every Gaussian coded (j, 1): What(p) = (1 - T_final(p)) onehot_j."""
+@pytest.mark.parametrize("kernel", ["tensor", "simt"])
+def test_render_one_hot_round_trip(gb, oracle_lib, monkeypatch, kernel):
+    """Every Gaussian coded (j, 1): What(p) = (1 - T_final(p)) onehot_j.
+
+    The SIMT kernel sums the weights in FP32 in list order (2e-6).  The
+    tensor-core kernel splits each weight into two bf16 parts, which keep it
+    to 2^-18 relative, and sums the products in FP32 inside the MMA: the
+    bound adds 2^-16 of the sum (1 - T)."""
+    if kernel == "simt":
+        monkeypatch.setenv("SCOUP_RENDER_SIMT", "1")
     wl = synth.tiny_workload(55, n=800, width=72, height=40, V=1, log_scale_mean=-2.6)
     n = wl.scene.n
     idx = np.full((n, 2), -1, np.int32)
@@ -75,7 +85,8 @@ def test_render_one_hot_round_trip(gb, oracle_lib):
     val = np.zeros((n, 2), np.float32)
     val[:, 0] = 1.0
     Wg, Tg, *_ = _render_pair(gb, oracle_lib, wl.scene, idx, val, 12, wl.cams[0])
-    np.testing.assert_allclose(Wg[..., 5], 1.0 - Tg, atol=2e-6)
+    atol = 2e-6 + (2.0 ** -16 * (1.0 - Tg) if kernel == "tensor" else 0.0)
+    assert (np.abs(Wg[..., 5] - (1.0 - Tg)) <= atol).all()
     assert np.abs(np.delete(Wg, 5, axis=-1)).max() == 0.0
 
 
@@ -152,3 +163,45 @@ def test_render_bf16_feeds_decode(gb):
     torch.cuda.synchronize()
     assert torch.equal(f_direct, f_conv)
     assert f_direct.abs().sum() > 0
+
+
+@pytest.mark.parametrize("seed,W,H,n,C,K,lsm", [
+    (52, 64, 48, 1500, 64, 4, -2.8),
+    (54, 130, 70, 3000, 256, 8, -3.0),
+])
+def test_render_simt_kernel(gb, oracle_lib, monkeypatch, seed, W, H, n, C, K, lsm):
+    """The SIMT kernel, selected by SCOUP_RENDER_SIMT=1, on the random-code cases."""
+    monkeypatch.setenv("SCOUP_RENDER_SIMT", "1")
+    test_render_random_codes(gb, oracle_lib, seed, W, H, n, C, K, lsm)
+
+
+def test_render_wide_rows_and_largest_k(gb, oracle_lib):
+    """C = 320 (wider than the tensor-core kernel takes: SIMT kernel) and
+    C = 256 with K = 16 (the largest Top-K the tensor-core kernel stages)."""
+    wl = synth.tiny_workload(59, n=2500, width=80, height=56, V=1, log_scale_mean=-2.8)
+    rng = np.random.default_rng(59)
+    for C, K in ((320, 8), (256, 16)):
+        idx, val = synth.sparse_topk_codes(rng, wl.scene.n, C, K)
+        Wg, Tg, lastg, st, Wo, To, risk, cnt = _render_pair(gb, oracle_lib, wl.scene, idx, val, C, wl.cams[0])
+        check_render(Wg, Tg, Wo, To, risk)
+        assert abs(st["contributions"] - cnt["contributions"]) <= 2 * risk.sum()
+
+
+def test_render_repeated_atoms(gb, oracle_lib):
+    """A code naming one atom twice adds both values (Eq. 7 over the sparse
+    vector), and atom ids outside [0, C) or -1 add nothing."""
+    wl = synth.tiny_workload(60, n=1200, width=64, height=40, V=1, log_scale_mean=-2.6)
+    rng = np.random.default_rng(60)
+    C, K = 48, 6
+    idx, val = synth.sparse_topk_codes(rng, wl.scene.n, C, K)
+    idx[::3, 1] = idx[::3, 0]            # repeated atom
+    idx[::5, 2] = idx[::5, 0]
+    val[::4, 3] = -val[::4, 3]           # a negative coefficient
+    idx[::11, 4] = -1
+    val[::11, 4] = 0.0
+    Wg, Tg, lastg, st, Wo, To, risk, cnt = _render_pair(gb, oracle_lib, wl.scene, idx, val, C, wl.cams[0])
+    err = np.abs(Wg.astype(np.float64) - Wo)
+    mag, *_ = oracle_lib.render(wl.scene, idx, np.abs(val).astype(np.float64), C, wl.cams[0])
+    tol = 1e-4 * mag + 1e-6 * mag.max(axis=-1, keepdims=True) + 1e-7
+    tol = np.where(risk[..., None], 1e-2 + tol, tol)
+    assert (err <= tol).all(), float((err - tol).max())
