@@ -90,44 +90,65 @@ __device__ __forceinline__ void split_bf16x2(float x, float y, uint32_t& hi, uin
 // Walks the thread's pixel over window positions j0 .. j0 + 31 and writes its
 // row of E (hi and lo parts, zero where a Gaussian does not contribute);
 // returns whether any weight of the row is nonzero.
+// Gaussians that cannot pass the alpha test at any pixel of the warp's 16 x 2
+// block (box_may_hit) are skipped, 8 at a time when none of 8 can.
 __device__ __forceinline__ bool walk_chunk(const RenderMmaSmem& sm, int j0, int m, int wbase, float fpx, float fpy,
-                                           float& T, int& last, bool& done, unsigned& n_eval, unsigned& n_contrib,
-                                           unsigned char* e_hi, unsigned char* e_lo, int row) {
-  if (__all_sync(0xffffffffu, done)) {
-#pragma unroll
-    for (int g = 0; g < kChunk / 8; ++g) {
-      *reinterpret_cast<uint4*>(e_hi + core_off(row, g * 8)) = make_uint4(0u, 0u, 0u, 0u);
-      *reinterpret_cast<uint4*>(e_lo + core_off(row, g * 8)) = make_uint4(0u, 0u, 0u, 0u);
+                                           float bx0, float by0, float& T, int& last, bool& done, unsigned& n_eval,
+                                           unsigned& n_contrib, unsigned char* e_hi, unsigned char* e_lo, int row) {
+  unsigned rel = 0u;
+  if (!__all_sync(0xffffffffu, done)) {
+    const int jl = j0 + (int)(threadIdx.x & 31);
+    bool r = false;
+    if (jl < m) {
+      ProjRec pr;
+      pr.a = sm.rec_a[jl];
+      pr.b = sm.rec_b[jl];
+      r = box_may_hit(pr, bx0, by0, (float)kTile, 2.0f);
     }
-    return false;
+    rel = __ballot_sync(0xffffffffu, r);
   }
   bool any = false;
 #pragma unroll
   for (int g = 0; g < kChunk / 8; ++g) {
-    float ev[8];
+    const unsigned rel8 = (rel >> (8 * g)) & 0xffu;
+    if (rel8 == 0u) {  // warp-uniform
+      *reinterpret_cast<uint4*>(e_hi + core_off(row, g * 8)) = make_uint4(0u, 0u, 0u, 0u);
+      *reinterpret_cast<uint4*>(e_lo + core_off(row, g * 8)) = make_uint4(0u, 0u, 0u, 0u);
+      continue;
+    }
+    // independent per Gaussian: exponent, alpha test and alpha (8 chains in
+    // flight).  Positions past the window hold records that never pass (tau =
+    // +inf), and a Gaussian outside the warp's box cannot pass either, so
+    // alpha > 0 exactly when the Gaussian passes the alpha test here.
+    float al[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int j = j0 + g * 8 + u;
-      const bool live = !done && j < m;
-      const int jj = j < m ? j : 0;
-      const float4 a = sm.rec_a[jj];
-      const float4 b = sm.rec_b[jj];
+      const float4 a = sm.rec_a[j];
+      const float4 b = sm.rec_b[j];
       const float dx = a.x - fpx, dy = a.y - fpy;
       const float power = fmaf(dx, fmaf(a.z, dx, __fmul_rn(a.w, dy)), __fmul_rn(__fmul_rn(b.x, dy), dy));
-      const bool accept = live && power <= 0.0f && power >= b.z;
-      const float alpha = accept ? fminf(0.99f, b.y * __expf(power)) : 0.0f;
-      const float test = T * (1.0f - alpha);
-      const bool stop = accept && test < 1e-4f;
-      const bool take = accept && !stop;
-      ev[u] = take ? alpha * T : 0.0f;
-      n_eval += live ? 1u : 0u;
-      n_contrib += take ? 1u : 0u;
-      if (take) {
-        T = test;
-        last = wbase + j + 1;
-      }
+      al[u] = (power <= 0.0f && power >= b.z) ? fminf(0.99f, b.y * __expf(power)) : 0.0f;
+    }
+    // serial front to back: transmittance, T-stop, weights
+    float ev[8];
+    const bool open0 = !done;
+    int ustop = 8;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const float test = T * (1.0f - al[u]);
+      const bool act = !done && al[u] > 0.0f;
+      const bool stop = act && test < 1e-4f;
+      const bool tk = act && !stop;
+      ev[u] = tk ? al[u] * T : 0.0f;
+      T = tk ? test : T;
+      if (tk) last = wbase + j0 + g * 8 + u + 1;
+      n_contrib += tk ? 1u : 0u;
+      if (stop) ustop = u;
       done = done || stop;
     }
+    // examined: the group's Gaussians in the warp's box while the pixel was open, up to the stop
+    if (open0) n_eval += __popc(rel8 & ((2u << ustop) - 1u));
     uint4 hi, lo;
     split_bf16x2(ev[0], ev[1], hi.x, lo.x);
     split_bf16x2(ev[2], ev[3], hi.y, lo.y);
@@ -215,7 +236,7 @@ __global__ void __launch_bounds__(kMThreads, 1) render_mma_kernel(
   bool done = !inside;
   const OrderBuckets bk = order_buckets<MOrder>(hdr, slot);
   ptx::tc_fence_before();
-  order_init(sm.ord, tkeys, n, bk);  // ends with a barrier: TMEM address and mbarriers are visible
+  order_init<MOrder, 16>(sm.ord, tkeys, n, bk);  // ends with a barrier: TMEM address and mbarriers are visible
   ptx::tc_fence_after();
   const uint32_t tmem = sm.tmem;
 
@@ -228,19 +249,48 @@ __global__ void __launch_bounds__(kMThreads, 1) render_mma_kernel(
   int chunk = 0, wbase = 0;
   OrderState ost;
   while (!all_done && !aborted) {
-    const int m = n > 0 ? order_next_window(sm.ord, tkeys, n, bk, ost, hdr) : 0;
+    const int m = n > 0 ? order_next_window<MOrder, 16>(sm.ord, tkeys, n, bk, ost, hdr) : 0;
     if (m <= 0) break;  // list exhausted, or an inconsistency (status already set)
-    for (int j = tid; j < m; j += kMThreads) {
-      const ProjRec pr = proj[(int)(sm.ord.win[j] & 0xffffffffull)];
-      sm.rec_a[j] = pr.a;
-      sm.rec_b[j] = pr.b;
+    // records of the window; the positions up to the next chunk boundary get
+    // a record no pixel accepts (tau = +inf)
+    for (int j = tid; j < ((m + kChunk - 1) & ~(kChunk - 1)); j += kMThreads) {
+      if (j < m) {
+        const ProjRec pr = proj[(int)(sm.ord.win[j] & 0xffffffffull)];
+        sm.rec_a[j] = pr.a;
+        sm.rec_b[j] = pr.b;
+      } else {
+        sm.rec_a[j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        sm.rec_b[j] = make_float4(0.0f, 0.0f, INFINITY, 0.0f);
+      }
     }
-    for (int t = tid; t < m * K; t += kMThreads) {
-      const int j = t / K, k = t - j * K;
+    // one thread per Gaussian stages its whole code row (all loads in flight together)
+    for (int j = tid; j < m; j += kMThreads) {
       const int64_t g = (int64_t)(sm.ord.win[j] & 0xffffffffull);
-      const int atom = topk_idx[g * K + k];
-      sm.code_idx[k * MOrder::kWin + j] = (short)(atom >= 0 && atom < C ? atom : -1);
-      sm.code_val[k * MOrder::kWin + j] = topk_val[g * K + k];
+      int32_t ai[kMaxK];
+      float av[kMaxK];
+      if ((K & 3) == 0) {
+#pragma unroll
+        for (int k4 = 0; k4 < kMaxK / 4; ++k4)
+          if (4 * k4 < K) {
+            const int4 a = reinterpret_cast<const int4*>(topk_idx + g * K)[k4];
+            const float4 v = reinterpret_cast<const float4*>(topk_val + g * K)[k4];
+            ai[4 * k4] = a.x; ai[4 * k4 + 1] = a.y; ai[4 * k4 + 2] = a.z; ai[4 * k4 + 3] = a.w;
+            av[4 * k4] = v.x; av[4 * k4 + 1] = v.y; av[4 * k4 + 2] = v.z; av[4 * k4 + 3] = v.w;
+          }
+      } else {
+#pragma unroll
+        for (int k = 0; k < kMaxK; ++k)
+          if (k < K) {
+            ai[k] = topk_idx[g * K + k];
+            av[k] = topk_val[g * K + k];
+          }
+      }
+#pragma unroll
+      for (int k = 0; k < kMaxK; ++k)
+        if (k < K) {
+          sm.code_idx[k * MOrder::kWin + j] = (short)(ai[k] >= 0 && ai[k] < C ? ai[k] : -1);
+          sm.code_val[k * MOrder::kWin + j] = av[k];
+        }
     }
     __syncthreads();
     for (int j0 = 0; j0 < m; j0 += kChunk, ++chunk) {
@@ -265,8 +315,9 @@ __global__ void __launch_bounds__(kMThreads, 1) render_mma_kernel(
           reinterpret_cast<uint4*>(cb.w[t])[i - t * n16] = make_uint4(0u, 0u, 0u, 0u);
         }
       }
-      const bool any = walk_chunk(sm, j0, m, wbase, (float)px, (float)py, T, last, done, n_eval, n_contrib,
-                                  cb.e[0][half], cb.e[1][half], row);
+      const bool any = walk_chunk(sm, j0, m, wbase, (float)px, (float)py, (float)(tx * kTile),
+                                  (float)(ty * kTile + 2 * warp), T, last, done, n_eval, n_contrib, cb.e[0][half],
+                                  cb.e[1][half], row);
       const unsigned wany = __ballot_sync(0xffffffffu, any);
       if (lane == 0) sm.any_e[warp] = wany != 0u;
       __syncthreads();

@@ -13,6 +13,11 @@
 
 namespace scoup {
 
+// Key loads a thread keeps in flight in the list passes (kLB, a template
+// parameter of order_init and order_next_window): 4 by default, more where
+// registers allow.
+constexpr int kLoadBatch = 4;
+
 template <int kWin_, int kLogNB_>
 struct OrderSmem {
   static constexpr int kWin = kWin_;
@@ -59,12 +64,24 @@ __device__ OrderBuckets order_buckets(const WsHeader* hdr, int slot) {
 
 // Histogram + exclusive scan into sm.bstart (block-wide; blockDim.x threads,
 // a multiple of 32 dividing kNB).
-template <class S>
+template <class S, int kLB = kLoadBatch>
 __device__ void order_init(S& sm, const unsigned long long* __restrict__ keys, int n, const OrderBuckets& bk) {
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
   for (int b = tid; b < S::kNB; b += nt) sm.bcur[b] = 0u;
   __syncthreads();
-  for (int i = tid; i < n; i += nt) atomicAdd(&sm.bcur[bk(keys[i])], 1u);
+  // kLB keys per thread are loaded before their atomics, so each
+  // thread has that many global loads in flight at once
+  for (int i0 = tid; i0 < n; i0 += kLB * nt) {
+    unsigned long long kk[kLB];
+#pragma unroll
+    for (int u = 0; u < kLB; ++u) {
+      const int i = i0 + u * nt;
+      kk[u] = i < n ? keys[i] : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < kLB; ++u)
+      if (i0 + u * nt < n) atomicAdd(&sm.bcur[bk(kk[u])], 1u);
+  }
   __syncthreads();
   const int per = S::kNB / nt;
   uint32_t sum = 0;
@@ -149,7 +166,7 @@ __device__ unsigned long long order_select(S& sm, const unsigned long long* __re
 // Next window, sorted front to back into sm.win[0..m).  Returns m, or 0 when
 // the list is exhausted, or -1 on an internal inconsistency (status set).
 // Block-uniform; every thread of the CTA must call it.
-template <class S>
+template <class S, int kLB = kLoadBatch>
 __device__ int order_next_window(S& sm, const unsigned long long* __restrict__ keys, int n,
                                  const OrderBuckets& bk, OrderState& st, WsHeader* hdr) {
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -198,12 +215,20 @@ __device__ int order_next_window(S& sm, const unsigned long long* __restrict__ k
     m = (int)(sm.bstart[b1] - base);
     for (int b = st.b0 + tid; b < b1; b += nt) sm.bcur[b] = sm.bstart[b] - base;
     __syncthreads();
-    for (int i = tid; i < n; i += nt) {
-      const unsigned long long k = keys[i];
-      const int b = bk(k);
-      if (b >= st.b0 && b < b1) {
-        const uint32_t pos = atomicAdd(&sm.bcur[b], 1u);
-        if (pos < (uint32_t)kWin) sm.win[pos] = k;
+    for (int i0 = tid; i0 < n; i0 += kLB * nt) {
+      unsigned long long kk[kLB];
+#pragma unroll
+      for (int u = 0; u < kLB; ++u) {
+        const int i = i0 + u * nt;
+        kk[u] = i < n ? keys[i] : 0ull;
+      }
+#pragma unroll
+      for (int u = 0; u < kLB; ++u) {
+        const int b = bk(kk[u]);
+        if (i0 + u * nt < n && b >= st.b0 && b < b1) {
+          const uint32_t pos = atomicAdd(&sm.bcur[b], 1u);
+          if (pos < (uint32_t)kWin) sm.win[pos] = kk[u];
+        }
       }
     }
     __syncthreads();
