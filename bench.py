@@ -476,6 +476,23 @@ def render_decode_leg(args, dist, wl, up, dev, pk):
     if gb.scoup_read_stats(dws)["status"] != 0 or gb.scoup_read_stats(sws)["status"] != 0:
         raise RuntimeError("decode/similarity device status")
 
+    # the same views through the one-call form (scoup_render_decode_fused) + similarity
+    def view_fused(v):
+        ren.run_decode(v, codebook, feats, n2, stats=False)
+        gb.scoup_similarity(feats, text, sim, feat_norm2=n2, workspace=sws)
+
+    for _ in range(3):
+        view_fused(0)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for v in range(len(cams)):
+        view_fused(v)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_fused = ev0.elapsed_time(ev1) / 1e3
+    if ren.run_decode(0, codebook, feats, n2, stats=True)["status"] != 0:
+        raise RuntimeError("fused render+decode status")
+
     # the decode GEMM alone: bf16 codes in, bf16 features out (one launch + a 256x512 transpose)
     codes_bf16 = out[0].view(P, wl.C)
     for _ in range(3):
@@ -498,6 +515,9 @@ def render_decode_leg(args, dist, wl, up, dev, pk):
         "C": wl.C, "D": D, "Q": Q, "K": wl.K,
         "codes": "Top-K of the uplift measured above",
         "ms_per_view": t * 1e3 / len(cams), "phase_ms_per_view": phase_ms,
+        "fused_call": {"form": "scoup_render_decode_fused + scoup_similarity",
+                       "value": len(cams) * P / t_fused / 1e6, "unit": "MPix/s",
+                       "ms_per_view": t_fused * 1e3 / len(cams)},
         "render_evaluated_pairs_per_view": evaluated, "render_contributions_per_view": contrib,
         # the decode GEMM moves more bytes than its FLOPs need time for at these
         # shapes (t_hbm = 2(C + D) B/pixel / BW > t_tensor = 2 C D / peak), so its

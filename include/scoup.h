@@ -194,9 +194,14 @@ int scoup_read_stats(const void* workspace, size_t ws_bytes, scoup_stats* stats,
  * topk_val[i][k]).  The result is the dense, unnormalised C-vector per pixel.
  *  out_codes  [H, W, C] row-major (every pixel written): float32 with
  *             out_dtype 0, bf16 (round to nearest even) with out_dtype 1 --
- *             the input scoup_decode takes without conversion.  A pixel whose
- *             list spans w windows of 256 entries is rounded to bf16 after
- *             each window: relative error at most w 2^-8 (bf16 unit roundoff).
+ *             the input scoup_decode takes without conversion.
+ * Two kernels compute it.  For C <= 256 and K <= 16 the tile's codes are a
+ * tensor-core contraction accumulated in FP32 (each weight and coefficient
+ * carried as two bf16 parts: about 3 * 2^-18 relative error per product) and
+ * rounded to the output type once.  Wider rows (or SCOUP_RENDER_SIMT=1 in the
+ * environment) take the SIMT kernel, which sums in FP32 in list order and,
+ * with bf16 output, rounds after each window of 256 list entries (a pixel
+ * spanning w windows: relative error at most w 2^-8, bf16 unit roundoff).
  *  out_T      float32 [H, W] final transmittance, or NULL.
  *  out_last   int32 [H, W]: number of front-to-back list entries up to and
  *             including the last contributor of the pixel, or NULL.
@@ -207,6 +212,38 @@ int scoup_read_stats(const void* workspace, size_t ws_bytes, scoup_stats* stats,
 int scoup_render(const scoup_scene* scene, const int32_t* topk_idx, const float* topk_val, int32_t K,
                  int32_t C, const scoup_camera* cam, void* out_codes, int32_t out_dtype, float* out_T,
                  int32_t* out_last, void* workspace, size_t ws_bytes, scoup_stats* stats, void* stream);
+
+/* Workspace bytes for scoup_render_decode_fused on views of width x height:
+ * the decode workspace, the view's bf16 rendered codes and a render
+ * workspace (scoup_uplift_workspace_size with the same n, size and
+ * dup_capacity).  Returns 0 on invalid arguments. */
+size_t scoup_render_decode_workspace_size(int64_t n, int32_t width, int32_t height, int32_t C, int32_t D,
+                                          int64_t dup_capacity);
+
+/* Eq. 7 then Eq. 8 in one call: renders the view (scoup_render with bf16
+ * codes) into the workspace and decodes those codes with the codebook
+ * (scoup_decode with codes_dtype 1) on the same stream.  The results equal
+ * the two separate calls bit for bit (the same kernels on the same values);
+ * the rendered codes never reach a caller array.
+ *  codebook    DEVICE float32 [C, D] row-major.
+ *  features    DEVICE [H * W, D] row-major, float32 (out_dtype 0) or bf16
+ *              (out_dtype 1), 16-byte aligned; feat_norm2 as in scoup_decode.
+ *  out_T, out_last as in scoup_render (or NULL).
+ *  workspace   DEVICE, >= scoup_render_decode_workspace_size(...) bytes.
+ *  stats       HOST or NULL: the render's counters and the first nonzero
+ *              status of either stage; when given, the call synchronises.
+ * Limits: those of both calls (1 <= K <= C <= 1024, C a multiple of 8;
+ * D a multiple of 16).  Why two kernels and not one: at C = 256 a tile's
+ * FP32 codes take all 512 TMEM columns of the SM, the decode's 256 x 512
+ * FP32 result would need as many again, and the bf16 code tile the decode
+ * reads (128 KB) plus codebook stages leave no shared memory for the next
+ * tile's walk, so a fused kernel would run the decode with the SM's walkers
+ * idle; the separate persistent GEMM streams at 84% of the HBM copy rate. */
+int scoup_render_decode_fused(const scoup_scene* scene, const int32_t* topk_idx, const float* topk_val, int32_t K,
+                              int32_t C, const scoup_camera* cam, const float* codebook, int32_t D,
+                              void* features, int32_t out_dtype, float* feat_norm2, float* out_T,
+                              int32_t* out_last, void* workspace, size_t ws_bytes, scoup_stats* stats,
+                              void* stream);
 
 /* Gradient through scoup_render (derived from Eq. 2 and Eq. 7) for a loss
  * whose gradient with respect to the rendered codes is dL_dcodes (float32

@@ -102,6 +102,9 @@ PROTOS = {
     "scoup_read_stats": (ct.c_int, [P, SZ, ct.POINTER(Stats), P]),
     "scoup_decode_workspace_size": (SZ, [I64, I32, I32]),
     "scoup_decode": (ct.c_int, [P, I32, I64, I32, P, I32, P, I32, P, P, SZ, P]),
+    "scoup_render_decode_workspace_size": (SZ, [I64, I32, I32, I32, I32, I64]),
+    "scoup_render_decode_fused": (ct.c_int, [ct.POINTER(Scene), P, P, I32, I32, ct.POINTER(Camera), P, I32, P, I32,
+                                             P, P, P, P, SZ, ct.POINTER(Stats), P]),
     "scoup_similarity_workspace_size": (SZ, [I64, I32, I32]),
     "scoup_similarity": (ct.c_int, [P, I64, I32, P, P, I32, P, P, SZ, P]),
     "scoup_decode_fp32": (ct.c_int, [P, I64, I32, P, I32, P, P]),

@@ -679,6 +679,52 @@ int scoup_decode(const void* codes, int32_t codes_dtype, int64_t P, int32_t C, c
   return SCOUP_OK;
 }
 
+size_t scoup_render_decode_workspace_size(int64_t n, int32_t width, int32_t height, int32_t C, int32_t D,
+                                          int64_t dup_capacity) {
+  if (n < 0 || width <= 0 || height <= 0 || C <= 0 || D <= 0 || dup_capacity < 0) return 0;
+  const int64_t P = (int64_t)width * height;
+  const size_t dec = scoup_decode_workspace_size(P, C, D);
+  const size_t up = scoup_uplift_workspace_size(n, width, height, dup_capacity);
+  if (!dec || !up) return 0;
+  return align_up(dec) + align_up((size_t)P * C * 2) + up;
+}
+
+// Workspace: [decode workspace][bf16 rendered codes, P x C][render workspace (the rest)].
+int scoup_render_decode_fused(const scoup_scene* scene, const int32_t* topk_idx, const float* topk_val, int32_t K,
+                              int32_t C, const scoup_camera* cam, const float* codebook, int32_t D, void* features,
+                              int32_t out_dtype, float* feat_norm2, float* out_T, int32_t* out_last, void* workspace,
+                              size_t ws_bytes, scoup_stats* stats, void* stream) {
+  if (!cam) return fail(SCOUP_ERR_INVALID_ARG, "cam is NULL");
+  if (cam->width <= 0 || cam->height <= 0)
+    return fail(SCOUP_ERR_INVALID_ARG, "camera size %dx%d", cam->width, cam->height);
+  if (C < 8 || C % 8 || C > 1024) return fail(SCOUP_ERR_INVALID_ARG, "C=%d must be a multiple of 8 in [8, 1024]", C);
+  if (D < 16 || D % 16) return fail(SCOUP_ERR_INVALID_ARG, "D=%d must be a positive multiple of 16", D);
+  if (!workspace) return fail(SCOUP_ERR_INVALID_ARG, "workspace is NULL");
+  const int64_t P = (int64_t)cam->width * cam->height;
+  const size_t dec = align_up(scoup_decode_workspace_size(P, C, D));
+  const size_t wb = align_up((size_t)P * C * 2);
+  if (ws_bytes < dec + wb) return fail(SCOUP_ERR_OOM, "workspace too small: %zu < %zu bytes before the render's", ws_bytes, dec + wb);
+  char* w = (char*)workspace;
+  void* What = w + dec;
+  char* rws = w + dec + wb;
+  int rc = scoup_render(scene, topk_idx, topk_val, K, C, cam, What, 1, out_T, out_last, rws, ws_bytes - dec - wb,
+                        nullptr, stream);
+  if (rc) return rc;
+  rc = scoup_decode(What, 1, P, C, codebook, D, features, out_dtype, feat_norm2, w, dec, stream);
+  if (rc) return rc;
+  if (stats) {
+    scoup_stats ds;
+    const int r_render = finish_with_stats((const WsHeader*)rws, stats, (cudaStream_t)stream);
+    if (r_render) return r_render;
+    const int r_decode = finish_with_stats((const WsHeader*)w, &ds, (cudaStream_t)stream);
+    if (r_decode) {
+      stats->status = ds.status;
+      return r_decode;
+    }
+  }
+  return SCOUP_OK;
+}
+
 size_t scoup_similarity_workspace_size(int64_t P, int32_t D, int32_t Q) {
   if (P < 0 || D <= 0 || Q <= 0) return 0;
   return align_up(sizeof(WsHeader)) + align_up((size_t)Q * D * 2) + align_up((size_t)Q * 4) + align_up((size_t)P * 4);

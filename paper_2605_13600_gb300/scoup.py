@@ -218,6 +218,8 @@ class Render:
         self.workspace = torch.empty(scoup_uplift_workspace_size(n, maxw, maxh, dup_capacity),
                                      dtype=torch.uint8, device=dev)
         self.device = dev
+        self.n, self.maxw, self.maxh, self.dup_capacity = n, maxw, maxh, dup_capacity
+        self._fused_ws = None
 
     def outputs(self, cam, dtype=None):
         import torch
@@ -232,6 +234,19 @@ class Render:
         st = scoup_render(self.scene, self.topk_idx, self.topk_val, self.K, self.C, cam, out[0], out[1],
                           out[2], self.workspace, stats=stats, stream=stream)
         return out, st
+
+    def run_decode(self, v: int, codebook, features, feat_norm2=None, out_T=None, out_last=None,
+                   stats: bool = True, stream=None):
+        """View v rendered and decoded in one call (scoup_render_decode_fused):
+        features [H * W, D] (float32 or bfloat16) = bf16(What) @ codebook."""
+        import torch
+        D = int(codebook.shape[1])
+        need = scoup_render_decode_workspace_size(self.n, self.maxw, self.maxh, self.C, D, self.dup_capacity)
+        if self._fused_ws is None or self._fused_ws.numel() < need:
+            self._fused_ws = torch.empty(need, dtype=torch.uint8, device=self.device)
+        return scoup_render_decode_fused(self.scene, self.topk_idx, self.topk_val, self.K, self.C, self.cams[v],
+                                         codebook, features, feat_norm2, out_T, out_last, self._fused_ws,
+                                         stats=stats, stream=stream)
 
 
 def scoup_decode_workspace_size(P: int, C: int, D: int) -> int:
@@ -265,6 +280,38 @@ def scoup_decode(codes, codebook, features, feat_norm2=None, workspace=None, str
                               _ptr(features), 1 if features.dtype == torch.bfloat16 else 0, _ptr(feat_norm2),
                               _ptr(workspace), workspace.numel(), _stream(stream)))
     return workspace
+
+
+def scoup_render_decode_workspace_size(n: int, width: int, height: int, C: int, D: int, dup_capacity: int) -> int:
+    return int(load().scoup_render_decode_workspace_size(n, width, height, C, D, dup_capacity))
+
+
+def scoup_render_decode_fused(scene: Scene, topk_idx, topk_val, K: int, C: int, cam, codebook, features,
+                              feat_norm2, out_T, out_last, workspace, stats: bool = True, stream=None):
+    """Eq. 7 then Eq. 8 for one view in one call: features [H * W, D] = bf16(What) @ codebook.
+    out_T / out_last / feat_norm2 may be None.  Returns stats when stats=True."""
+    import torch
+    _need(topk_idx, torch.int32, "topk_idx")
+    _need(topk_val, torch.float32, "topk_val")
+    _need(codebook, torch.float32, "codebook")
+    if features.dtype not in (torch.float32, torch.bfloat16):
+        raise TypeError("features must be float32 or bfloat16")
+    _need(features, features.dtype, "features")
+    _need(feat_norm2, torch.float32, "feat_norm2")
+    _need(out_T, torch.float32, "out_T")
+    _need(out_last, torch.int32, "out_last")
+    _need(workspace, torch.uint8, "workspace")
+    D = int(codebook.shape[1])
+    if int(codebook.shape[0]) != int(C) or tuple(features.shape) != (cam.width * cam.height, D):
+        raise ValueError("shape mismatch")
+    ca = camera_array([cam])
+    st = Stats()
+    check(load().scoup_render_decode_fused(ct.byref(scene), _ptr(topk_idx), _ptr(topk_val), int(K), int(C),
+                                           ct.cast(ca, ct.POINTER(Camera)), _ptr(codebook), D, _ptr(features),
+                                           1 if features.dtype == torch.bfloat16 else 0, _ptr(feat_norm2),
+                                           _ptr(out_T), _ptr(out_last), _ptr(workspace), workspace.numel(),
+                                           ct.byref(st) if stats else None, _stream(stream)))
+    return st.as_dict() if stats else None
 
 
 def scoup_similarity_workspace_size(P: int, D: int, Q: int) -> int:
@@ -608,4 +655,5 @@ __all__ = ["ScoupError", "SCOUP_ACCUM_CONTINUE", "SCOUP_ACCUM_COMPENSATED", "sce
            "scoup_render", "scoup_render_backward", "Render", "Uplift",
            "scoup_decode_workspace_size", "scoup_decode", "scoup_similarity_workspace_size",
            "scoup_similarity", "scoup_decode_fp32", "scoup_similarity_fp32", "BatchedUplift",
-           "SCOUP_BATCH_EAGER", "LevelUplift", "scoup_selftest_gemm_timeout", "scoup_topk_entropy", "scoup_entropy_filter", "scoup_relevancy"]
+           "SCOUP_BATCH_EAGER", "LevelUplift", "scoup_selftest_gemm_timeout", "scoup_topk_entropy", "scoup_entropy_filter", "scoup_relevancy",
+           "scoup_render_decode_workspace_size", "scoup_render_decode_fused"]

@@ -86,3 +86,28 @@ def test_topk_rejects_bad_arguments(lib):
     assert L.scoup_topk(fake, 10, 8, 9, fake, fake, None) == lib.SCOUP_ERR_INVALID_ARG
     assert L.scoup_topk(None, 10, 8, 2, fake, fake, None) == lib.SCOUP_ERR_INVALID_ARG
     assert L.scoup_topk(fake, -1, 8, 2, fake, fake, None) == lib.SCOUP_ERR_INVALID_ARG
+
+
+def test_render_decode_fused_sizes_and_checks(lib):
+    """Workspace layout of scoup_render_decode_fused (decode workspace, bf16
+    codes, render workspace) and its host-side argument checks."""
+    L = lib.load()
+    n, W, H, C, D, dup = 1000, 160, 120, 64, 128, 500
+    P = W * H
+    al = lambda x: (x + 255) // 256 * 256
+    want = al(L.scoup_decode_workspace_size(P, C, D)) + al(P * C * 2) + L.scoup_uplift_workspace_size(n, W, H, dup)
+    assert L.scoup_render_decode_workspace_size(n, W, H, C, D, dup) == want
+    assert L.scoup_render_decode_workspace_size(n, 0, H, C, D, dup) == 0
+    assert L.scoup_render_decode_workspace_size(n, W, H, C, 0, dup) == 0
+    sc = lib.Scene()
+    sc.n = 4
+    fake = ct.c_void_p(0x10000)  # never dereferenced: validation fails first
+    sc.means = sc.scales = sc.quats = sc.opacity = fake
+    cams = (lib.Camera * 1)()
+    cams[0].fx = cams[0].fy = 100.0
+    cams[0].width, cams[0].height = W, H
+    for kw, frag in (({"C": 12}, "C=12"), ({"D": 40}, "D=40"), ({"ws_bytes": 1024}, "workspace too small")):
+        rc = L.scoup_render_decode_fused(ct.byref(sc), fake, fake, 4, kw.get("C", C), ct.cast(cams, ct.POINTER(lib.Camera)),
+                                         fake, kw.get("D", D), fake, 1, None, None, None, fake,
+                                         kw.get("ws_bytes", 1 << 30), None, None)
+        assert rc != 0 and frag in L.scoup_last_error().decode(), (kw, L.scoup_last_error())

@@ -205,3 +205,58 @@ def test_render_repeated_atoms(gb, oracle_lib):
     tol = 1e-4 * mag + 1e-6 * mag.max(axis=-1, keepdims=True) + 1e-7
     tol = np.where(risk[..., None], 1e-2 + tol, tol)
     assert (err <= tol).all(), float((err - tol).max())
+
+
+@pytest.mark.parametrize("out_dtype", ["bf16", "f32"])
+def test_render_decode_fused(gb, oracle_lib, out_dtype):
+    """scoup_render_decode_fused (Eq. 7 then Eq. 8 in one call) equals
+    scoup_render with bf16 codes followed by scoup_decode bit for bit, and
+    the oracle's decode of the oracle's render within the bf16 operand bound:
+    |F - F_o| <= (2u + u^2 + 2e-4) sum_c |W_c| |B_cd| (+ u |F_o| for bf16
+    features), u = 2^-8, 2e-4 covering the rendered codes' own tolerance."""
+    import torch
+    wl = synth.tiny_workload(61, n=2500, width=96, height=64, V=1, log_scale_mean=-2.8)
+    rng = np.random.default_rng(61)
+    C, K, D = 64, 8, 128
+    idx, val = synth.sparse_topk_codes(rng, wl.scene.n, C, K)
+    Bn = synth.unit_rows(rng, C, D)
+    B = torch.from_numpy(Bn).cuda()
+    cam = wl.cams[0]
+    P = cam.width * cam.height
+    fdt = torch.bfloat16 if out_dtype == "bf16" else torch.float32
+    r = gb.Render(wl.scene, idx, val, C, [cam])
+    Wb, T1, last1 = r.outputs(cam, dtype=torch.bfloat16)
+    r.run(0, out=(Wb, T1, last1))
+    f1 = torch.empty((P, D), dtype=fdt, device="cuda")
+    n1 = torch.zeros((P,), dtype=torch.float32, device="cuda") if out_dtype == "bf16" else None
+    gb.scoup_decode(Wb.view(P, C), B, f1, n1)
+    f2 = torch.empty_like(f1)
+    n2 = torch.zeros_like(n1) if n1 is not None else None
+    T2, last2 = torch.empty_like(T1), torch.empty_like(last1)
+    st = r.run_decode(0, B, f2, n2, T2, last2)
+    torch.cuda.synchronize()
+    assert st["status"] == 0 and st["contributions"] > 0
+    assert torch.equal(f1, f2) and torch.equal(T1, T2) and torch.equal(last1, last2)
+    if n1 is not None:
+        assert torch.equal(n1, n2)
+    Wo, To, risk, _ = oracle_lib.render(wl.scene, idx, val.astype(np.float64), C, cam)
+    Fo = oracle_lib.decode(Wo.reshape(P, C), Bn)
+    mag = np.abs(Wo.reshape(P, C)) @ np.abs(Bn.astype(np.float64))
+    u = 2.0 ** -8
+    bound = (2 * u + u * u + 2e-4) * mag + (u * np.abs(Fo) if out_dtype == "bf16" else 0.0) + 1e-6
+    ok = ~risk.reshape(P)
+    err = np.abs(f2.float().cpu().numpy().astype(np.float64) - Fo)
+    assert (err[ok] <= bound[ok]).all(), float((err - bound)[ok].max())
+
+
+def test_render_decode_fused_argument_checks(gb):
+    import torch
+    from paper_2605_13600_gb300._lib import ScoupError
+    wl = synth.tiny_workload(62, n=300, width=40, height=24, V=1)
+    rng = np.random.default_rng(62)
+    idx, val = synth.sparse_topk_codes(rng, wl.scene.n, 12, 3)
+    r = gb.Render(wl.scene, idx, val, 12, [wl.cams[0]])
+    B = torch.from_numpy(synth.unit_rows(rng, 12, 32)).cuda()
+    f = torch.empty((40 * 24, 32), dtype=torch.bfloat16, device="cuda")
+    with pytest.raises(ScoupError):  # C = 12 is not a multiple of 8 (the decode's limit)
+        r.run_decode(0, B, f)
