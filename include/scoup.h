@@ -238,7 +238,7 @@ size_t scoup_render_decode_workspace_size(int64_t n, int32_t width, int32_t heig
  * FP32 result would need as many again, and the bf16 code tile the decode
  * reads (128 KB) plus codebook stages leave no shared memory for the next
  * tile's walk, so a fused kernel would run the decode with the SM's walkers
- * idle; the separate persistent GEMM streams at 84% of the HBM copy rate. */
+ * idle; the separate persistent GEMM streams above 80% of the HBM copy rate. */
 int scoup_render_decode_fused(const scoup_scene* scene, const int32_t* topk_idx, const float* topk_val, int32_t K,
                               int32_t C, const scoup_camera* cam, const float* codebook, int32_t D,
                               void* features, int32_t out_dtype, float* feat_norm2, float* out_T,
