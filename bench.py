@@ -343,9 +343,13 @@ def run_gb300(args, dist):
         d2h = out_i.numel() * 4 + out_v.numel() * 4
 
         def e2e_step():
+            # scene and code table copied up front; the region maps (93% of the
+            # input bytes) are staged view by view by the library while earlier
+            # views compute (scoup_uplift_host_maps)
             for k, t in host.items():
-                getattr(up, k).copy_(t, non_blocking=True)
-            up.run(stats=False)
+                if k != "region_maps":
+                    getattr(up, k).copy_(t, non_blocking=True)
+            up.run_host_maps(host["region_maps"], stats=False)
             out_i.copy_(up.topk_idx, non_blocking=True)
             out_v.copy_(up.topk_val, non_blocking=True)
 
@@ -359,7 +363,9 @@ def run_gb300(args, dist):
         torch.cuda.synchronize()
         t_e2e = dist.max((time.perf_counter() - t0) / args.steps)
         e2e = {"value": dist.world * contrib / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "ms_per_step": t_e2e * 1e3}
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": t_e2e * 1e3,
+               "form": "pinned host inputs; scene and codes copied, region maps staged per view by "
+                       "scoup_uplift_host_maps; Top-K read back"}
 
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:

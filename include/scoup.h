@@ -146,6 +146,30 @@ int scoup_uplift(const scoup_scene* scene, const scoup_camera* cams, int32_t V,
                  float* accum, int32_t accum_mode, int32_t* topk_idx, float* topk_val,
                  void* workspace, size_t ws_bytes, scoup_stats* stats, void* stream);
 
+/* Workspace bytes for scoup_uplift_host_maps: a staging ring of 4 view maps
+ * of max_width x max_height int32 entries, then a scoup_uplift workspace
+ * (scoup_uplift_workspace_size with the same arguments).  0 on invalid
+ * arguments. */
+size_t scoup_uplift_host_maps_workspace_size(int64_t n, int32_t max_width, int32_t max_height,
+                                             int64_t dup_capacity);
+
+/* scoup_uplift with the region maps in HOST memory (pinned for the copies to
+ * run asynchronously): view v's map is copied to a ring slot in the workspace
+ * on a library copy stream while earlier views compute, and only view v's
+ * tile pass waits for it (its projection and binning do not read the map).
+ * Results equal scoup_uplift on the same maps up to the order of the FP32
+ * atomic additions (as two scoup_uplift runs do); counters are equal.  The copies
+ * follow the work already on `stream` and the call's work is joined back
+ * into it.  Single level; not for graph capture (the copy stream is not
+ * forked from a capturing stream).  Other arguments as scoup_uplift;
+ * workspace >= scoup_uplift_host_maps_workspace_size(...) bytes, sized with
+ * max_width / max_height covering every view. */
+int scoup_uplift_host_maps(const scoup_scene* scene, const scoup_camera* cams, int32_t V,
+                           const int32_t* host_region_maps, const int64_t* map_offsets, int32_t R_total,
+                           const int32_t* code_idx, const float* code_val, int32_t s, int32_t C, int32_t K,
+                           float* accum, int32_t accum_mode, int32_t* topk_idx, float* topk_val,
+                           void* workspace, size_t ws_bytes, scoup_stats* stats, void* stream);
+
 /* One semantic level of a multi-level uplift: the region maps of every view
  * (packed as for scoup_uplift, same map_offsets for all levels) and the
  * level's code table. */

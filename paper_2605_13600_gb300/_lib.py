@@ -92,6 +92,9 @@ PROTOS = {
     "scoup_uplift_plan": (ct.c_int, [ct.POINTER(Scene), P, I32, P, SZ, ct.POINTER(I64), P]),
     "scoup_uplift": (ct.c_int, [ct.POINTER(Scene), P, I32, P, P, I32, P, P, I32, I32, I32, P, I32,
                                 P, P, P, SZ, ct.POINTER(Stats), P]),
+    "scoup_uplift_host_maps_workspace_size": (SZ, [I64, I32, I32, I64]),
+    "scoup_uplift_host_maps": (ct.c_int, [ct.POINTER(Scene), P, I32, P, P, I32, P, P, I32, I32, I32, P, I32,
+                                          P, P, P, SZ, ct.POINTER(Stats), P]),
     "scoup_topk": (ct.c_int, [P, I64, I32, I32, P, P, P]),
     "scoup_uplift_levels": (ct.c_int, [ct.POINTER(Scene), P, I32, P, P, I32, I32, I32, P, I32, P, P, P, SZ,
                                        ct.POINTER(Stats), P]),

@@ -1,4 +1,5 @@
 // api.cu -- C ABI entry points: validation, workspace carve-up, launch order.
+#include <algorithm>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -169,6 +170,17 @@ cudaStream_t view_lane_stream() {
   return streams[dev];
 }
 
+// The library's stream for staging host region maps (one per device and host thread).
+cudaStream_t map_copy_stream() {
+  thread_local cudaStream_t streams[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return nullptr;
+  if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess)
+    streams[dev] = nullptr;
+  return streams[dev];
+}
+
 CamArgs cam_args(const scoup_camera& c) {
   CamArgs a;
   memcpy(a.vm, c.viewmat, sizeof(a.vm));
@@ -297,6 +309,13 @@ int uplift_call(const UpliftCall& c, void* workspace, size_t ws_bytes, int warp_
   for (int v = 0; v < V; ++v)
     if (map_offsets[v] < 0) return fail(SCOUP_ERR_INVALID_ARG, "map_offsets[%d] < 0", v);
   if (!workspace) return fail(SCOUP_ERR_INVALID_ARG, "workspace is NULL");
+  if (c.maps_on_host) {
+    if (L != 1) return fail(SCOUP_ERR_INVALID_ARG, "host region maps take a single level");
+    if (!c.map_stage) return fail(SCOUP_ERR_INVALID_ARG, "no staging ring for host region maps");
+    for (int v = 0; v < V; ++v)
+      if ((int64_t)cams[v].width * cams[v].height > c.map_stage_cap)
+        return fail(SCOUP_ERR_INVALID_ARG, "view %d is larger than the staging ring's slots", v);
+  }
   const int64_t code_rows_k = (L == 1 && s > K) ? (int64_t)R_total * K : 0;
   const size_t fixed = uplift_fixed_bytes(scene->n, max_tiles, code_rows_k);
   if (ws_bytes < fixed)
@@ -354,6 +373,32 @@ int uplift_call(const UpliftCall& c, void* workspace, size_t ws_bytes, int warp_
         return cuda_fail(e, "view streams");
       }
     }
+    // host maps: copy stream forked from `st`; ready[q] = slot q holds its
+    // view's map, used[q] = the tile kernel that read slot q has finished
+    cudaStream_t cs = nullptr;
+    cudaEvent_t cfork = nullptr, cjoin = nullptr, ready[kMapStageSlots] = {}, used[kMapStageSlots] = {};
+    auto destroy_copy_events = [&]() {
+      for (cudaEvent_t* ev : {&cfork, &cjoin}) if (*ev) cudaEventDestroy(*ev);
+      for (int q = 0; q < kMapStageSlots; ++q) {
+        if (ready[q]) cudaEventDestroy(ready[q]);
+        if (used[q]) cudaEventDestroy(used[q]);
+      }
+    };
+    if (c.maps_on_host) {
+      cs = map_copy_stream();
+      bool ok = cs != nullptr;
+      ok = ok && cudaEventCreateWithFlags(&cfork, cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&cjoin, cudaEventDisableTiming) == cudaSuccess;
+      for (int q = 0; q < kMapStageSlots && ok; ++q)
+        ok = cudaEventCreateWithFlags(&ready[q], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&used[q], cudaEventDisableTiming) == cudaSuccess;
+      ok = ok && cudaEventRecord(cfork, st) == cudaSuccess && cudaStreamWaitEvent(cs, cfork, 0) == cudaSuccess;
+      if (!ok) {
+        destroy_copy_events();
+        if (lanes == 2) { cudaEventDestroy(fork); cudaEventDestroy(join); }
+        return fail(SCOUP_ERR_CUDA, "map copy stream");
+      }
+    }
     int rc_views = SCOUP_OK;
     for (int v = 0; v < V && rc_views == SCOUP_OK; ++v) {
       const int lane = v % lanes, slot = 2 * lane + ((v / lanes) & 1);
@@ -368,6 +413,18 @@ int uplift_call(const UpliftCall& c, void* workspace, size_t ws_bytes, int warp_
         PhaseScope ps(SCOUP_PHASE_BINNING, vs);
         if ((e = launch_binning(ca, n, wv, slot, vs)) != cudaSuccess) { rc_views = cuda_fail(e, "binning"); break; }
       }
+      const int q = v % kMapStageSlots;
+      if (c.maps_on_host) {
+        // the copy waits for the tile kernel that last read slot q (view v - kMapStageSlots)
+        const size_t bytes = sizeof(int32_t) * (size_t)cams[v].width * (size_t)cams[v].height;
+        if ((v >= kMapStageSlots && (e = cudaStreamWaitEvent(cs, used[q], 0)) != cudaSuccess) ||
+            (e = cudaMemcpyAsync(c.map_stage + (size_t)q * c.map_stage_cap, region_maps + map_offsets[v], bytes,
+                                 cudaMemcpyHostToDevice, cs)) != cudaSuccess ||
+            (e = cudaEventRecord(ready[q], cs)) != cudaSuccess || (e = cudaStreamWaitEvent(vs, ready[q], 0)) != cudaSuccess) {
+          rc_views = cuda_fail(e, "region map copy");
+          break;
+        }
+      }
       {
         PhaseScope ps(SCOUP_PHASE_UPLIFT_TILES, vs);
         LevelCodes lc;
@@ -375,7 +432,9 @@ int uplift_call(const UpliftCall& c, void* workspace, size_t ws_bytes, int warp_
         lc.s_tot = L == 1 ? s_eff : s_tot;
         for (int l = 0; l < kMaxLevels; ++l) {
           const bool on = l < L;
-          lc.rmap[l] = on ? lv[l].region_maps + map_offsets[v] : nullptr;
+          lc.rmap[l] = on ? (c.maps_on_host ? c.map_stage + (size_t)q * c.map_stage_cap
+                                            : lv[l].region_maps + map_offsets[v])
+                          : nullptr;
           lc.ci[l] = on ? (L == 1 ? ci : lv[l].code_idx) : nullptr;
           lc.cv[l] = on ? (L == 1 ? cv : lv[l].code_val) : nullptr;
           lc.s[l] = on ? (L == 1 ? s_eff : lv[l].s) : 0;
@@ -386,6 +445,15 @@ int uplift_call(const UpliftCall& c, void* workspace, size_t ws_bytes, int warp_
           break;
         }
       }
+      if (c.maps_on_host && (e = cudaEventRecord(used[q], vs)) != cudaSuccess) {
+        rc_views = cuda_fail(e, "region map copy");
+        break;
+      }
+    }
+    if (c.maps_on_host) {
+      if ((e = cudaEventRecord(cjoin, cs)) != cudaSuccess || (e = cudaStreamWaitEvent(st, cjoin, 0)) != cudaSuccess)
+        if (rc_views == SCOUP_OK) rc_views = cuda_fail(e, "map copy stream");
+      destroy_copy_events();
     }
     if (lanes == 2) {
       // join even on an error, so that a capture in progress stays well formed
@@ -488,6 +556,43 @@ int scoup_uplift(const scoup_scene* scene, const scoup_camera* cams, int32_t V,
   const WsHeader* hdr = nullptr;
   const cudaStream_t st = (cudaStream_t)stream;
   const int rc = uplift_call(c, workspace, ws_bytes, 8, &hdr, st, 2);
+  if (rc != SCOUP_OK) return rc;
+  if (stats) return finish_with_stats(hdr, stats, st);
+  return SCOUP_OK;
+}
+
+size_t scoup_uplift_host_maps_workspace_size(int64_t n, int32_t max_width, int32_t max_height,
+                                             int64_t dup_capacity) {
+  const size_t up = scoup_uplift_workspace_size(n, max_width, max_height, dup_capacity);
+  if (!up) return 0;
+  return align_up(sizeof(int32_t) * kMapStageSlots * (size_t)max_width * (size_t)max_height) + up;
+}
+
+// Workspace: [staging ring of kMapStageSlots view maps][scoup_uplift workspace].
+int scoup_uplift_host_maps(const scoup_scene* scene, const scoup_camera* cams, int32_t V,
+                           const int32_t* host_region_maps, const int64_t* map_offsets, int32_t R_total,
+                           const int32_t* code_idx, const float* code_val, int32_t s, int32_t C, int32_t K,
+                           float* accum, int32_t accum_mode, int32_t* topk_idx, float* topk_val,
+                           void* workspace, size_t ws_bytes, scoup_stats* stats, void* stream) {
+  if (V < 0) return fail(SCOUP_ERR_INVALID_ARG, "V=%d < 0", V);
+  if (V > 0 && !cams) return fail(SCOUP_ERR_INVALID_ARG, "cams is NULL");
+  if (!workspace) return fail(SCOUP_ERR_INVALID_ARG, "workspace is NULL");
+  int64_t cap = 1;
+  for (int v = 0; v < V; ++v) {
+    if (cams[v].width <= 0 || cams[v].height <= 0)
+      return fail(SCOUP_ERR_INVALID_ARG, "view %d: bad size %dx%d", v, cams[v].width, cams[v].height);
+    cap = std::max(cap, (int64_t)cams[v].width * cams[v].height);
+  }
+  const size_t ring = align_up(sizeof(int32_t) * kMapStageSlots * (size_t)cap);
+  if (ws_bytes < ring) return fail(SCOUP_ERR_OOM, "workspace too small: %zu < %zu bytes of staging ring", ws_bytes, ring);
+  UpliftCall c{scene, cams, V, host_region_maps, map_offsets, R_total, code_idx, code_val, s, C, K,
+               accum, accum_mode, topk_idx, topk_val};
+  c.maps_on_host = true;
+  c.map_stage = (int32_t*)workspace;
+  c.map_stage_cap = cap;
+  const WsHeader* hdr = nullptr;
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int rc = uplift_call(c, (char*)workspace + ring, ws_bytes - ring, 8, &hdr, st, 2);
   if (rc != SCOUP_OK) return rc;
   if (stats) return finish_with_stats(hdr, stats, st);
   return SCOUP_OK;

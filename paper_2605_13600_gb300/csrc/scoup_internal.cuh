@@ -154,7 +154,14 @@ struct UpliftCall {
   float* topk_val;
   int32_t L = 0;                        // > 0: semantic levels in `levels` replace the
   const scoup_level* levels = nullptr;  // single-level region map and code fields above
+  // region_maps in HOST memory (single level): each view's map is copied into
+  // a device ring of kMapStageSlots slots of map_stage_cap entries, on a
+  // library copy stream, just ahead of the view's tile kernel
+  bool maps_on_host = false;
+  int32_t* map_stage = nullptr;
+  int64_t map_stage_cap = 0;
 };
+constexpr int kMapStageSlots = 4;
 
 // Validates and enqueues one uplift on `st` without synchronising; warp_w is
 // the tile kernel's warp pixel-block width (8, 16 or 4).  *hdr_out receives

@@ -114,6 +114,42 @@ def scoup_uplift(scene: Scene, cams: Sequence, region_maps, map_offsets, R_total
     return st.as_dict() if stats else None
 
 
+def scoup_uplift_host_maps_workspace_size(n: int, max_width: int, max_height: int, dup_capacity: int) -> int:
+    return int(load().scoup_uplift_host_maps_workspace_size(n, max_width, max_height, dup_capacity))
+
+
+def scoup_uplift_host_maps(scene: Scene, cams: Sequence, host_region_maps, map_offsets, R_total: int, code_idx,
+                           code_val, s: int, C: int, K: int, accum, accum_mode: int, topk_idx, topk_val,
+                           workspace, stats: bool = True, stream=None):
+    """scoup_uplift with the region maps in host memory (a CPU tensor, pinned
+    for asynchronous copies): each view's map is staged into the workspace
+    while earlier views compute."""
+    import torch
+    if not isinstance(host_region_maps, torch.Tensor) or host_region_maps.device.type != "cpu":
+        raise TypeError("host_region_maps must be a CPU tensor (pinned for asynchronous copies)")
+    if accum is not None and accum.numel() < scene.n * C * (2 if accum_mode & SCOUP_ACCUM_COMPENSATED else 1):
+        raise ValueError("accum is too small for n x C (x 2 when compensated)")
+    if host_region_maps.dtype != torch.int32 or not host_region_maps.is_contiguous():
+        raise TypeError("host_region_maps must be a contiguous int32 tensor")
+    _need(code_idx, torch.int32, "code_idx")
+    _need(code_val, torch.float32, "code_val")
+    _need(accum, torch.float32, "accum")
+    _need(topk_idx, torch.int32, "topk_idx")
+    _need(topk_val, torch.float32, "topk_val")
+    _need(workspace, torch.uint8, "workspace")
+    offs = np.ascontiguousarray(np.asarray(map_offsets, np.int64)[:max(1, len(cams))])
+    ca = camera_array(cams)
+    st = Stats()
+    rc = load().scoup_uplift_host_maps(ct.byref(scene), ct.cast(ca, ct.c_void_p), len(cams), _ptr(host_region_maps),
+                                       offs.ctypes.data_as(ct.c_void_p), int(R_total), _ptr(code_idx),
+                                       _ptr(code_val), int(s), int(C), int(K), _ptr(accum), int(accum_mode),
+                                       _ptr(topk_idx), _ptr(topk_val), _ptr(workspace),
+                                       0 if workspace is None else workspace.numel(),
+                                       ct.byref(st) if stats else None, _stream(stream))
+    check(rc)
+    return st.as_dict() if stats else None
+
+
 def scoup_uplift_noalloc(scene: Scene, cams: Sequence, region_maps, map_offsets, R_total: int,
                          code_idx, code_val, s: int, C: int, K: int, accum, accum_mode: int,
                          topk_idx, topk_val, stream=None) -> dict:
@@ -478,6 +514,8 @@ class Uplift:
         self.dup_capacity = dup_capacity
         self.workspace = torch.empty(scoup_uplift_workspace_size(n, maxw, maxh, dup_capacity) + extra,
                                      dtype=torch.uint8, device=dev)
+        self.maxw, self.maxh, self.extra, self.device = maxw, maxh, extra, dev
+        self._host_ws = None
         self.compensated = bool(compensated)
         self.accum = torch.empty(((2, n, self.C) if compensated else (n, self.C)), dtype=torch.float32,
                                  device=dev)
@@ -495,6 +533,23 @@ class Uplift:
                             self.code_val, self.s, self.C, self.K, self.accum, accum_mode,
                             self.topk_idx if topk else None, self.topk_val if topk else None,
                             self.workspace, stats=stats, stream=stream)
+
+    def run_host_maps(self, host_maps, stats: bool = True, accum_mode: int = 0, stream=None, topk: bool = True):
+        """One uplift with the region maps read from host memory (host_maps:
+        a pinned CPU int32 tensor laid out like region_maps): the copies of
+        the views' maps overlap the earlier views' compute."""
+        import torch
+        topk = topk and self.topk_idx is not None
+        if self._host_ws is None:
+            self._host_ws = torch.empty(scoup_uplift_host_maps_workspace_size(self.n, self.maxw, self.maxh,
+                                                                              self.dup_capacity) + self.extra,
+                                        dtype=torch.uint8, device=self.device)
+        if self.compensated:
+            accum_mode |= SCOUP_ACCUM_COMPENSATED
+        return scoup_uplift_host_maps(self.scene, self.cams, host_maps, self.map_offsets, self.R_total,
+                                      self.code_idx, self.code_val, self.s, self.C, self.K, self.accum, accum_mode,
+                                      self.topk_idx if topk else None, self.topk_val if topk else None,
+                                      self._host_ws, stats=stats, stream=stream)
 
     def accum_value(self):
         """The accumulator [n, C] (sum + compensation in the compensated form)."""
@@ -656,4 +711,5 @@ __all__ = ["ScoupError", "SCOUP_ACCUM_CONTINUE", "SCOUP_ACCUM_COMPENSATED", "sce
            "scoup_decode_workspace_size", "scoup_decode", "scoup_similarity_workspace_size",
            "scoup_similarity", "scoup_decode_fp32", "scoup_similarity_fp32", "BatchedUplift",
            "SCOUP_BATCH_EAGER", "LevelUplift", "scoup_selftest_gemm_timeout", "scoup_topk_entropy", "scoup_entropy_filter", "scoup_relevancy",
-           "scoup_render_decode_workspace_size", "scoup_render_decode_fused"]
+           "scoup_render_decode_workspace_size", "scoup_render_decode_fused",
+           "scoup_uplift_host_maps_workspace_size", "scoup_uplift_host_maps"]

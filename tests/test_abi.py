@@ -111,3 +111,25 @@ def test_render_decode_fused_sizes_and_checks(lib):
                                          fake, kw.get("D", D), fake, 1, None, None, None, fake,
                                          kw.get("ws_bytes", 1 << 30), None, None)
         assert rc != 0 and frag in L.scoup_last_error().decode(), (kw, L.scoup_last_error())
+
+
+def test_uplift_host_maps_sizes_and_checks(lib):
+    """Workspace layout of scoup_uplift_host_maps (a 4-slot staging ring of
+    view maps, then a scoup_uplift workspace) and its host-side checks."""
+    L = lib.load()
+    n, W, H, dup = 1000, 160, 120, 500
+    al = lambda x: (x + 255) // 256 * 256
+    assert L.scoup_uplift_host_maps_workspace_size(n, W, H, dup) == al(4 * W * H * 4) + L.scoup_uplift_workspace_size(n, W, H, dup)
+    assert L.scoup_uplift_host_maps_workspace_size(n, 0, H, dup) == 0
+    sc = lib.Scene()
+    sc.n = 4
+    fake = ct.c_void_p(0x10000)  # never dereferenced: validation fails first
+    sc.means = sc.scales = sc.quats = sc.opacity = fake
+    cams = (lib.Camera * 1)()
+    cams[0].fx = cams[0].fy = 100.0
+    offs = (ct.c_int64 * 1)(0)
+    for wh, ws_bytes, frag in (((0, 10), 1 << 30, "bad size"), ((W, H), 1024, "staging ring")):
+        cams[0].width, cams[0].height = wh
+        rc = L.scoup_uplift_host_maps(ct.byref(sc), ct.cast(cams, ct.c_void_p), 1, fake, ct.cast(offs, ct.c_void_p),
+                                      4, fake, fake, 2, 8, 2, fake, 0, fake, fake, fake, ws_bytes, None, None)
+        assert rc != 0 and frag in L.scoup_last_error().decode(), (wh, L.scoup_last_error())

@@ -197,3 +197,43 @@ def test_cfg2_full_size_sampled_rows(gb, oracle_lib):
     tk = check_topk(up.topk_idx.cpu().numpy()[rows], up.topk_val.cpu().numpy()[rows], acc, risk, wl.K)
     assert tk["n_problems"] == 0, tk
     print("cfg2 sampled", info, st)
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_region_maps(gb, oracle_lib, cfg1, cfg1_oracle, pinned):
+    """scoup_uplift_host_maps: cfg1's 8 views staged from host memory through a
+    4-slot device ring (every slot reused) against the oracle, and against
+    scoup_uplift on device maps (equal counters and Top-K; accumulators equal
+    up to the order of FP32 atomic additions)."""
+    import torch
+    up = gb.Uplift(cfg1)
+    st_dev = up.run()
+    acc_dev = up.accum.clone()
+    idx_dev = up.topk_idx.clone()
+    host = torch.as_tensor(np.asarray(cfg1.region_maps, np.int32)).contiguous()
+    if pinned:
+        host = host.pin_memory()
+    st = up.run_host_maps(host)
+    assert st["status"] == 0
+    for k in ("visible", "duplicates", "evaluated_pairs", "contributions"):
+        assert st[k] == st_dev[k], k
+    info = check_accum(up.accum.cpu().numpy(), cfg1_oracle["acc"], cfg1_oracle["risk"])
+    assert info["n_bad"] == 0, info
+    tk = check_topk(up.topk_idx.cpu().numpy(), up.topk_val.cpu().numpy(), cfg1_oracle["acc"], cfg1_oracle["risk"],
+                    cfg1.K)
+    assert tk["n_problems"] == 0, tk
+    np.testing.assert_allclose(up.accum.cpu().numpy(), acc_dev.cpu().numpy(), rtol=2e-6, atol=1e-7)
+    assert (up.topk_idx != idx_dev).sum().item() <= 4
+
+
+def test_host_region_maps_ragged_views(gb, oracle_lib):
+    """Nine views (the ring wraps twice) of a ragged-size scene, host maps."""
+    import torch
+    wl = synth.tiny_workload(36, n=1500, width=70, height=45, V=9, R=12, C=32, s=4, K=4, log_scale_mean=-2.7)
+    up = gb.Uplift(wl)
+    st = up.run_host_maps(torch.as_tensor(np.asarray(wl.region_maps, np.int32)).contiguous().pin_memory())
+    assert st["status"] == 0
+    acc, risk, cnt = oracle_lib.uplift(wl)
+    info = check_accum(up.accum.cpu().numpy(), acc, risk)
+    assert info["n_bad"] == 0, info
+    assert abs(st["contributions"] - cnt["contributions"]) <= 2 * cnt["at_risk"]
