@@ -221,7 +221,7 @@ int scoup_read_stats(const void* workspace, size_t ws_bytes, scoup_stats* stats,
  *             the input scoup_decode takes without conversion.
  * Two kernels compute it.  For C <= 256 and K <= 16 the tile's codes are a
  * tensor-core contraction accumulated in FP32 (each weight and coefficient
- * carried as two bf16 parts: about 3 * 2^-18 relative error per product) and
+ * carried as two bf16 parts: at most about 3 * 2^-16 relative error per product) and
  * rounded to the output type once.  Wider rows (or SCOUP_RENDER_SIMT=1 in the
  * environment) take the SIMT kernel, which sums in FP32 in list order and,
  * with bf16 output, rounds after each window of 256 list entries (a pixel

@@ -15,8 +15,10 @@
 // alpha test and T-stop rule of the uplift) and writes its row of E; the CTA
 // expands the chunk's codes into W.  The bf16 operands are split, e = e_hi +
 // e_lo and w = w_hi + w_lo (each part rounded to bf16), and three MMAs add
-// E_hi W_hi + E_hi W_lo + E_lo W_hi: the dropped and rounded parts leave a
-// relative error of about 3 * 2^-18 per product before FP32 accumulation.
+// E_hi W_hi + E_hi W_lo + E_lo W_hi.  With u = 2^-8 (bf16 unit roundoff)
+// each split leaves u^2 of its value and the dropped E_lo W_lo is below u^2
+// of the product: at most about 3 u^2 = 3 * 2^-16 (4.6e-5) relative per
+// product before FP32 accumulation.
 // Chunk buffers are double-buffered, so the walk of one chunk overlaps the
 // MMAs of the previous one.  A chunk in which a pixel half has no weight
 // issues no MMA for that half.

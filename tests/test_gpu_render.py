@@ -74,8 +74,9 @@ def test_render_one_hot_round_trip(gb, oracle_lib, monkeypatch, kernel):
 
     The SIMT kernel sums the weights in FP32 in list order (2e-6).  The
     tensor-core kernel splits each weight into two bf16 parts, which keep it
-    to 2^-18 relative, and sums the products in FP32 inside the MMA: the
-    bound adds 2^-16 of the sum (1 - T)."""
+    to u^2 = 2^-16 relative (u = 2^-8; the code value 1 is exact in bf16),
+    and sums the products in FP32 inside the MMA: the bound adds 2^-16 of the
+    sum (1 - T)."""
     if kernel == "simt":
         monkeypatch.setenv("SCOUP_RENDER_SIMT", "1")
     wl = synth.tiny_workload(55, n=800, width=72, height=40, V=1, log_scale_mean=-2.6)
