@@ -176,3 +176,37 @@ def test_decode_then_similarity_pipeline():
     assert (err[live] <= bound[live]).all()
     assert err[live].mean() <= 2e-3
     assert (got[~live] == 0).all()
+
+
+def test_decode_full_size_sampled_rows():
+    """The decode at the benchmark's size (2,073,600 rows = one 1920 x 1080
+    view, C = 256, D = 512, bf16 codes in, bf16 features out, one launch)
+    on seeded 8-sparse code rows: 256 sampled rows against the oracle on the
+    unrounded inputs with the operand-rounding bound of the module header."""
+    import paper_2605_13600_gb300 as gb
+    from paper_2605_13600_gb300 import build
+    build.build()
+    P, C, D, nnz = 1920 * 1080, 256, 512, 8
+    rng = np.random.default_rng(402)
+    idx = rng.integers(0, C, size=(P, nnz)).astype(np.int64)
+    val = (rng.random((P, nnz), dtype=np.float32) / nnz).astype(np.float32)
+    B = unit_rows(rng, C, D)
+    dev = torch.device("cuda:0")
+    W = torch.zeros((P, C), dtype=torch.float32, device=dev)
+    W.scatter_add_(1, torch.from_numpy(idx).to(dev), torch.from_numpy(val).to(dev))  # repeated atoms add up
+    Wb = W.to(torch.bfloat16)
+    F = torch.empty((P, D), dtype=torch.bfloat16, device=dev)
+    n2 = torch.zeros((P,), dtype=torch.float32, device=dev)
+    gb.scoup_decode(Wb, torch.from_numpy(B).to(dev), F, n2)
+    torch.cuda.synchronize()
+    rows = np.concatenate([[0, 1, P - 2, P - 1], rng.integers(0, P, 252)])
+    Wr = np.zeros((rows.size, C))
+    for q, p in enumerate(rows):
+        np.add.at(Wr[q], idx[p], val[p].astype(np.float64))
+    ref = oracle.decode(Wr, B)
+    got = F[torch.from_numpy(rows).to(dev)].float().cpu().numpy().astype(np.float64)
+    mag = np.abs(Wr) @ np.abs(B.astype(np.float64))
+    bound = (2 * U_BF16 + U_BF16 ** 2) * mag + 2.0 ** -22 * C * mag + U_BF16 * np.abs(ref) + 1e-12
+    assert (np.abs(got - ref) <= bound).all(), float(np.max(np.abs(got - ref) - bound))
+    np.testing.assert_allclose(n2[torch.from_numpy(rows).to(dev)].cpu().numpy(),
+                               (got ** 2).sum(1), rtol=1e-5, atol=1e-12)

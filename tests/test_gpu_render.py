@@ -261,3 +261,43 @@ def test_render_decode_fused_argument_checks(gb):
     f = torch.empty((40 * 24, 32), dtype=torch.bfloat16, device="cuda")
     with pytest.raises(ScoupError):  # C = 12 is not a multiple of 8 (the decode's limit)
         r.run_decode(0, B, f)
+
+
+def test_cfg4_full_size_sampled_pixels(gb, oracle_lib):
+    """The 1920 x 1080 render of the 1M-Gaussian scene (C = 256, K = 8: the
+    benchmark's render configuration, seeded random K-sparse codes) at 48
+    sampled pixels (the four corners and 44 random ones): What(p) and T_final
+    against the oracle's front-to-back list of each pixel, Eq. 7 summed in
+    FP64.  A pixel whose stop decision flips (T off by more than 1e-3
+    relative) is at risk; at most two of the 48 may be."""
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+    wl = synth.render_cfg4(n_views=1)
+    cam = wl.cams[0]
+    r = gb.Render(wl.scene, wl.topk_idx, wl.topk_val, wl.C, [cam])
+    (W, T, last), st = r.run(0)
+    assert st["status"] == 0
+    rng = np.random.default_rng(401)
+    pts = [(0, 0), (cam.width - 1, cam.height - 1), (cam.width - 1, 0), (0, cam.height - 1)]
+    pts += [(int(x), int(y)) for x, y in zip(rng.integers(0, cam.width, 44), rng.integers(0, cam.height, 44))]
+    xs = torch.tensor([p[0] for p in pts], device=W.device)
+    ys = torch.tensor([p[1] for p in pts], device=W.device)
+    Wg = W[ys, xs].double().cpu().numpy()
+    Tg = T[ys, xs].double().cpu().numpy()
+    with ThreadPoolExecutor(16) as ex:  # the oracle's C code runs without the GIL
+        lists = list(ex.map(lambda p: oracle_lib.pixel_list(wl.scene, cam, p[0], p[1]), pts))
+    flips = 0
+    for k, (gids, e, _, To) in enumerate(lists):
+        if abs(Tg[k] - To) > 1e-3 * max(To, 1e-4) + 1e-6:
+            flips += 1
+            continue
+        wo = np.zeros(wl.C)
+        for g, ee in zip(gids, e):
+            for a in range(wl.K):
+                j = int(wl.topk_idx[g, a])
+                if j >= 0:
+                    wo[j] += float(wl.topk_val[g, a]) * ee
+        tol = 1e-4 * np.abs(wo) + 1e-6 * np.abs(wo).max() + 1e-7
+        assert (np.abs(Wg[k] - wo) <= tol).all(), (pts[k], float(np.max(np.abs(Wg[k] - wo) - tol)))
+        assert abs(Tg[k] - To) <= 1e-5 + 1e-4 * To
+    assert flips <= 2
