@@ -81,3 +81,33 @@ def test_autograd_function(gb, oracle_lib):
     dv_o, do_o = oracle_lib.render_backward(scene, idx, val.astype(np.float64), 24, cam, g)
     _compare(tv.grad.cpu().numpy(), dv_o, "d_val")
     _compare(op.grad.cpu().numpy(), do_o, "d_opacity")
+
+
+def test_cfg5_full_size_backward(gb, oracle_lib):
+    """The benchmark's backward configuration (500k Gaussians, an 800 x 600
+    view, C = 256, K = 8; seeded N(0, 1) gradient, zero at pixels whose stop
+    decision is at risk) against the oracle's FP64 backward of the whole
+    view.  d_val sums many signed FP32 terms: its bound adds 1e-5 of the sum
+    of the terms' magnitudes, which the oracle gives exactly as d_val of |g|."""
+    import torch
+    wl = synth.render_cfg5()
+    cam = wl.cams[0]
+    n, C, K = wl.scene.n, wl.C, wl.K
+    idx, val = wl.topk_idx, wl.topk_val
+    rng = np.random.default_rng(501)
+    g = rng.standard_normal((cam.height, cam.width, C), dtype=np.float32)
+    _, _, risk, _ = oracle_lib.render(wl.scene, idx, val.astype(np.float64), C, cam)
+    g[risk] = 0.0
+    r = gb.Render(wl.scene, idx, val, C, [cam])
+    d_val = torch.zeros((n, K), dtype=torch.float32, device="cuda")
+    d_op = torch.zeros(n, dtype=torch.float32, device="cuda")
+    gb.scoup_render_backward(r.scene, r.topk_idx, r.topk_val, K, C, cam, torch.as_tensor(g, device="cuda"),
+                             d_val, d_op, r.workspace)
+    g64 = g.astype(np.float64)
+    dv_o, do_o = oracle_lib.render_backward(wl.scene, idx, val.astype(np.float64), C, cam, g64)
+    dv_mag, _ = oracle_lib.render_backward(wl.scene, idx, np.abs(val).astype(np.float64), C, cam, np.abs(g64))
+    dv_g = d_val.cpu().numpy()
+    tol = 2e-4 * np.abs(dv_o) + 2e-5 * np.abs(dv_o).max() + 1e-5 * dv_mag
+    assert (np.abs(dv_g - dv_o) <= tol).all(), float(np.max(np.abs(dv_g - dv_o) - tol))
+    _compare(d_op.cpu().numpy(), do_o, "d_opacity")
+    assert np.abs(dv_o).max() > 0 and np.abs(do_o).max() > 0
