@@ -122,3 +122,25 @@ def test_batch_with_empty_scenes(gb, oracle_lib):
     assert bu.accum[1].numel() == 0
     assert (bu.accum[2] == 0).all() and (bu.topk_idx[2] == -1).all()
     bu.close()
+
+
+def test_cfg3_full_size_scenes_sampled_rows(gb, oracle_lib):
+    """Two scenes of the 16-scene batch at full size (342k Gaussians x 58
+    views at 680 x 508 and 229k x 72 views at 832 x 622, C = 256, s = K = 8)
+    in one autotuned batched graph; 8 seeded rows per scene against the oracle."""
+    import torch
+    wls = [synth.uplift_cfg3_scene(b, device="cuda") for b in (9, 6)]
+    bu = gb.BatchedUplift(wls)
+    bu.autotune(sample_views=2)
+    bu.run()
+    stats = bu.stats()
+    for b, wl in enumerate(wls):
+        assert stats[b]["status"] == 0, (b, stats[b])
+        rows = np.sort(np.random.default_rng(9 + b).choice(wl.scene.n, 8, replace=False))
+        acc, risk, cnt = oracle_lib.uplift(wl, rows=rows)
+        ga = bu.accum_value(b)[torch.as_tensor(rows, device="cuda")].cpu().numpy()
+        info = check_accum(ga, acc, risk)
+        assert info["n_bad"] == 0, (b, info)
+        tk = check_topk(bu.topk_idx[b].cpu().numpy()[rows], bu.topk_val[b].cpu().numpy()[rows], acc, risk, wl.K)
+        assert tk["n_problems"] == 0, (b, tk)
+    bu.close()
