@@ -198,7 +198,25 @@ def oracle_sample(budget_s: float, max_views: int = 16, device: str = "cpu"):
         done_views += 1
         if elapsed >= budget_s:
             break
-    return contrib / elapsed, done_views, threads, elapsed
+    # one view on one thread: the oracle's single-core rate
+    t0 = time.perf_counter()
+    _, _, cnt = oracle.uplift(wl, views=[0], nthreads=1)
+    single = cnt["contributions"] / (time.perf_counter() - t0)
+    return contrib / elapsed, done_views, threads, elapsed, single
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), or the platform's processor string."""
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.processor() or platform.machine()
 
 
 def run_reference(args, dist):
@@ -369,10 +387,12 @@ def run_gb300(args, dist):
 
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
-        v, nv, threads, el = oracle_sample(args.cpu_seconds, device=str(dev))
+        v, nv, threads, el, single = oracle_sample(args.cpu_seconds, device=str(dev))
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"views 0..{nv - 1} of 200 of the same workload (all 1M Gaussians, 988x731), "
-                         f"FP64 oracle, {el:.1f} s"}
+                         f"FP64 oracle, {el:.1f} s",
+               "cpu_model": cpu_model(),
+               "single_thread": {"value": single, "unit": UNIT, "sample": "view 0 on one thread"}}
 
     rd = None
     if args.render_views > 0:
