@@ -44,6 +44,8 @@ def parse_args():
     ap.add_argument("--views", type=int, default=200, help="views of the workload (default: all 200)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-entropy", action="store_true",
+                    help="skip the Top-K + entropy and entropy-filter measurement")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU oracle sample budget")
     ap.add_argument("--render-views", type=int, default=8,
                     help="views of the 1920x1080 render + decode measurement (0 = skip)")
@@ -394,6 +396,8 @@ def run_gb300(args, dist):
                "cpu_model": cpu_model(),
                "single_thread": {"value": single, "unit": UNIT, "sample": "view 0 on one thread"}}
 
+    ent = entropy_leg(args, up, pk) if not args.no_entropy else None
+
     rd = None
     if args.render_views > 0:
         rd = render_decode_leg(args, dist, wl, up, dev, pk)
@@ -431,6 +435,7 @@ def run_gb300(args, dist):
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk, "phase_ms_per_step": step_ms,
             "stats": {k: st0[k] for k in ("visible", "duplicates", "flushes", "atomics")},
+            "entropy": ent,
             "render_decode": rd,
             "dense_vs_sparse": dn,
             "levels": lv,
@@ -519,6 +524,19 @@ def render_decode_leg(args, dist, wl, up, dev, pk):
     if ren.run_decode(0, codebook, feats, n2, stats=True)["status"] != 0:
         raise RuntimeError("fused render+decode status")
 
+    # relevancy (App. B, Eq. 9) of 28 queries against 4 canonical phrases from the last view's similarities
+    Rel = torch.empty((P, Q - 4), dtype=torch.float32, device=dev)
+    for _ in range(3):
+        gb.scoup_relevancy(sim, 4, Rel)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(10):
+        gb.scoup_relevancy(sim, 4, Rel)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_rel = ev0.elapsed_time(ev1) / 1e3 / 10
+    rel_bytes = 4.0 * P * Q + 4.0 * P * (Q - 4)
+
     # the decode GEMM alone: bf16 codes in, bf16 features out (one launch + a 256x512 transpose)
     codes_bf16 = out[0].view(P, wl.C)
     for _ in range(3):
@@ -541,6 +559,9 @@ def render_decode_leg(args, dist, wl, up, dev, pk):
         "C": wl.C, "D": D, "Q": Q, "K": wl.K,
         "codes": "Top-K of the uplift measured above",
         "ms_per_view": t * 1e3 / len(cams), "phase_ms_per_view": phase_ms,
+        "relevancy": {"ms_per_view": t_rel * 1e3, "queries": Q - 4, "canonical": 4, "bound": "hbm",
+                      "achieved": rel_bytes / t_rel / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                      "frac": rel_bytes / t_rel / 1e9 / pk["hbm_gbs"]},
         "fused_call": {"form": "scoup_render_decode_fused + scoup_similarity",
                        "value": len(cams) * P / t_fused / 1e6, "unit": "MPix/s",
                        "ms_per_view": t_fused * 1e3 / len(cams)},
@@ -555,6 +576,61 @@ def render_decode_leg(args, dist, wl, up, dev, pk):
                             "tensor_view": {"achieved_tflops": flops / t_gemm / 1e12, "peak_tflops": pk["bf16_tflops"],
                                             "frac": flops / t_gemm / 1e12 / pk["bf16_tflops"]},
                             "peak_source": pk["source"] + " (HBM copy; bf16 burst)"},
+    }
+
+
+def entropy_leg(args, up, pk):
+    """Top-K with the coefficient entropy fused in, and the entropy filter,
+    at full size on the accumulator the uplift just produced (1M x 256)."""
+    import torch
+
+    import paper_2605_13600_gb300 as gb
+    n, C = up.accum.shape[-2], up.accum.shape[-1]
+    K = up.K
+    acc = up.accum if up.accum.dim() == 2 else up.accum[0]
+    dev = acc.device
+    idx = torch.empty((n, K), dtype=torch.int32, device=dev)
+    val = torch.empty((n, K), dtype=torch.float32, device=dev)
+    H = torch.empty((n,), dtype=torch.float32, device=dev)
+    mask = torch.empty((n,), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=10):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(reps):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / 1e3 / reps
+
+    t_topk = timed(lambda: gb.scoup_topk(acc, K, idx, val))
+    t_ent = timed(lambda: gb.scoup_topk_entropy(acc, K, idx, val, H))
+    # the filter synchronises (one host-read histogram per radix pass): host-timed
+    from paper_2605_13600_gb300._lib import load
+    ws = torch.empty(int(load().scoup_entropy_filter_workspace_size()), dtype=torch.uint8, device=dev)
+    gb.scoup_entropy_filter(H, n // 2, idx, val, mask, workspace=ws)
+    t0 = time.perf_counter()
+    reps = 5
+    for _ in range(reps):
+        gb.scoup_entropy_filter(H, n // 2, idx, val, mask, workspace=ws)
+    torch.cuda.synchronize()
+    t_filter = (time.perf_counter() - t0) / reps
+    kept = int(mask.sum().item())
+    nbytes = 4.0 * n * C + 8.0 * n * K
+    return {
+        "rows": n, "C": C, "K": K,
+        "topk_ms": t_topk * 1e3,
+        "topk_entropy_ms": t_ent * 1e3,
+        "topk_entropy_roofline": {"bound": "hbm", "achieved": (nbytes + 4.0 * n) / t_ent / 1e9,
+                                  "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                  "frac": (nbytes + 4.0 * n) / t_ent / 1e9 / pk["hbm_gbs"],
+                                  "algorithmic_bytes": nbytes + 4.0 * n},
+        "entropy_filter_ms": t_filter * 1e3, "entropy_filter_keep": n // 2, "entropy_filter_kept": kept,
+        "entropy_filter_form": "8 radix-select passes over the entropies (host reads each digit histogram)",
     }
 
 

@@ -311,7 +311,7 @@ int scoup_entropy_filter(const float* entropy, int64_t n, int64_t keep, int32_t 
  *   R[p][q] = min_k exp(a s_q) / (exp(a s_q) + exp(a s_k))
  * from the similarities sim [P, ncols] (scoup_similarity output) whose first
  * n_canon columns are the canonical phrases and the other ncols - n_canon the
- * queries; a = alpha (10 in the paper).  R DEVICE float32 [P, ncols - n_canon].
+ * queries; a = alpha > 0 (10 in the paper).  R DEVICE float32 [P, ncols - n_canon].
  * Asynchronous. */
 int scoup_relevancy(const float* sim, int64_t P, int32_t ncols, int32_t n_canon, float alpha, float* R,
                     void* stream);

@@ -951,6 +951,7 @@ int scoup_relevancy(const float* sim, int64_t P, int32_t ncols, int32_t n_canon,
                     void* stream) {
   if (P < 0) return fail(SCOUP_ERR_INVALID_ARG, "P < 0");
   if (n_canon < 1 || ncols <= n_canon) return fail(SCOUP_ERR_INVALID_ARG, "need 1 <= n_canon < ncols");
+  if (!(alpha > 0.0f) || alpha > 3.0e38f) return fail(SCOUP_ERR_INVALID_ARG, "alpha must be positive and finite");
   if (P > 0 && (!sim || !R)) return fail(SCOUP_ERR_INVALID_ARG, "NULL array");
   PhaseScope ps(SCOUP_PHASE_SIMILARITY, (cudaStream_t)stream);
   cudaError_t e = launch_relevancy(sim, P, ncols, n_canon, alpha, R, (cudaStream_t)stream);

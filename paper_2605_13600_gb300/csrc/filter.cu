@@ -52,18 +52,23 @@ __global__ void filter_kernel(const float* __restrict__ H, int64_t n, unsigned l
   }
 }
 
+// One warp per similarity row: lane q (and q + 32, ...) takes query q.
+// 1 / (1 + e^{a (s_k - s_q)}) decreases in s_k (a > 0), so the minimum over
+// the canonical phrases is the term of the largest canonical similarity:
+// one exponential per output, the same value as the minimum of all terms.
 __global__ void relevancy_kernel(const float* __restrict__ sim, int64_t P, int ncols, int n_canon, float alpha,
                                  float* __restrict__ R) {
   const int nq = ncols - n_canon;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < P * nq;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p = t / nq;
-    const int q = (int)(t - p * nq);
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < P; p += warps) {
     const float* row = sim + p * ncols;
-    const float sq = row[n_canon + q];
-    float r = 1.0f;
-    for (int k = 0; k < n_canon; ++k) r = fminf(r, 1.0f / (1.0f + expf(alpha * (row[k] - sq))));
-    R[t] = r;
+    float smax = -INFINITY;
+    for (int k = 0; k < n_canon; ++k) smax = fmaxf(smax, row[k]);
+    for (int q = lane; q < nq; q += 32) {
+      const float sq = row[n_canon + q];
+      R[p * nq + q] = n_canon > 0 ? fminf(1.0f, 1.0f / (1.0f + expf(alpha * (smax - sq)))) : 1.0f;
+    }
   }
 }
 
@@ -107,7 +112,7 @@ int entropy_filter_run(const float* H, int64_t n, int64_t keep, int K, int32_t* 
 cudaError_t launch_relevancy(const float* sim, int64_t P, int ncols, int n_canon, float alpha, float* R,
                              cudaStream_t st) {
   if (P <= 0 || ncols <= n_canon) return cudaSuccess;
-  relevancy_kernel<<<grid_for(P * (ncols - n_canon)), 256, 0, st>>>(sim, P, ncols, n_canon, alpha, R);
+  relevancy_kernel<<<grid_for(P * 32), 256, 0, st>>>(sim, P, ncols, n_canon, alpha, R);  // a warp per row
   g_launches += 1;
   return cudaGetLastError();
 }
