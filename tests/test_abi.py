@@ -133,3 +133,15 @@ def test_uplift_host_maps_sizes_and_checks(lib):
         rc = L.scoup_uplift_host_maps(ct.byref(sc), ct.cast(cams, ct.c_void_p), 1, fake, ct.cast(offs, ct.c_void_p),
                                       4, fake, fake, 2, 8, 2, fake, 0, fake, fake, fake, ws_bytes, None, None)
         assert rc != 0 and frag in L.scoup_last_error().decode(), (wh, L.scoup_last_error())
+
+
+def test_relevancy_rejects_bad_alpha(lib):
+    """Eq. 9's minimum over canonical phrases is taken at the largest canonical
+    similarity, which needs alpha > 0: zero, negative and non-finite alphas
+    are refused before any launch."""
+    L = lib.load()
+    fake = ct.c_void_p(0x10000)
+    for a in (0.0, -1.0, float("inf"), float("nan")):
+        assert L.scoup_relevancy(fake, 10, 8, 2, a, fake, None) != 0
+        assert "alpha" in L.scoup_last_error().decode()
+    assert L.scoup_relevancy(fake, 10, 2, 2, 10.0, fake, None) != 0  # no query column
