@@ -61,3 +61,30 @@ def test_two_gloo_ranks():
     assert res[0][0] == res[1][0] == 6.0
     # the reference arm prints nothing and does no work on rank 1
     assert res[1][1] == ""
+
+
+def test_reference_arm_json_line():
+    """The reference arm on rank 0 (one warm-up and one timed view of the
+    1M-Gaussian workload through the FP64 oracle on the host cores) prints
+    one JSON line carrying the fields the contract names."""
+    import json
+    import types
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class OneRank:
+        rank, world = 0, 1
+
+    out = io.StringIO()
+    with redirect_stdout(out):
+        bench.run_reference(types.SimpleNamespace(warmup=1, steps=1, gpus=1), OneRank())
+    lines = [l for l in out.getvalue().splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"] == bench.WORKLOAD
