@@ -1,0 +1,35 @@
+"""Argument checks of the Python binding (no GPU: every case below is refused
+before the library is called)."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2605_13600_gb300 as gb
+
+
+def test_host_maps_must_be_a_cpu_int32_tensor():
+    scene = gb.Scene() if hasattr(gb, "Scene") else None
+    cams = []
+    for bad in (np.zeros(4, np.int32), torch.zeros(4, dtype=torch.float32), torch.zeros(8, dtype=torch.int32)[::2]):
+        with pytest.raises(TypeError):
+            gb.scoup_uplift_host_maps(scene, cams, bad, [0], 1, None, None, 1, 8, 1, None, 0, None, None, None)
+
+
+def test_cuda_arrays_are_required():
+    cpu = torch.zeros((4, 8), dtype=torch.float32)
+    with pytest.raises(ValueError, match="CUDA"):
+        gb.scoup_topk(cpu, 2, torch.zeros((4, 2), dtype=torch.int32), torch.zeros((4, 2)))
+    with pytest.raises(TypeError):
+        gb.scoup_topk(cpu.double(), 2, None, None)
+
+
+def test_relevancy_shape_check():
+    sim = torch.zeros((6, 10), dtype=torch.float32)
+    with pytest.raises((ValueError, TypeError)):
+        gb.scoup_relevancy(sim, 4, torch.zeros((6, 5), dtype=torch.float32))
+
+
+def test_render_decode_fused_checks_types():
+    f = torch.zeros((4, 16), dtype=torch.float16)
+    with pytest.raises((TypeError, ValueError)):
+        gb.scoup_render_decode_fused(None, None, None, 1, 8, None, torch.zeros((8, 16)), f, None, None, None, None)
