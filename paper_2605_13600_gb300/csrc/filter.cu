@@ -56,18 +56,41 @@ __global__ void filter_kernel(const float* __restrict__ H, int64_t n, unsigned l
 // 1 / (1 + e^{a (s_k - s_q)}) decreases in s_k (a > 0), so the minimum over
 // the canonical phrases is the term of the largest canonical similarity:
 // one exponential per output, the same value as the minimum of all terms.
+// Rows of at most 32 columns are read four at a time, one coalesced word per
+// lane and row (the loads of the four rows in flight together); the
+// canonical maximum and each query's value come by shuffles.
+constexpr int kRelRows = 4;
+
 __global__ void relevancy_kernel(const float* __restrict__ sim, int64_t P, int ncols, int n_canon, float alpha,
                                  float* __restrict__ R) {
   const int nq = ncols - n_canon;
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < P; p += warps) {
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (ncols <= 32) {
+    for (int64_t p0 = gw * kRelRows; p0 < P; p0 += warps * kRelRows) {
+      float v[kRelRows];
+#pragma unroll
+      for (int u = 0; u < kRelRows; ++u)
+        v[u] = (p0 + u < P && lane < ncols) ? sim[(p0 + u) * ncols + lane] : -INFINITY;
+#pragma unroll
+      for (int u = 0; u < kRelRows; ++u) {
+        float c = lane < n_canon ? v[u] : -INFINITY;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) c = fmaxf(c, __shfl_xor_sync(0xffffffffu, c, off));
+        const float sq = __shfl_sync(0xffffffffu, v[u], min(n_canon + lane, 31));
+        if (p0 + u < P && lane < nq) R[(p0 + u) * nq + lane] = fminf(1.0f, 1.0f / (1.0f + expf(alpha * (c - sq))));
+      }
+    }
+    return;
+  }
+  for (int64_t p = gw; p < P; p += warps) {
     const float* row = sim + p * ncols;
     float smax = -INFINITY;
     for (int k = 0; k < n_canon; ++k) smax = fmaxf(smax, row[k]);
     for (int q = lane; q < nq; q += 32) {
       const float sq = row[n_canon + q];
-      R[p * nq + q] = n_canon > 0 ? fminf(1.0f, 1.0f / (1.0f + expf(alpha * (smax - sq)))) : 1.0f;
+      R[p * nq + q] = fminf(1.0f, 1.0f / (1.0f + expf(alpha * (smax - sq))));
     }
   }
 }

@@ -125,3 +125,19 @@ def test_relevancy_pipeline_bf16(gb, oracle_lib):
     err = np.abs(R.cpu().numpy() - want)
     # dR/ds <= alpha / 4 per similarity; two similarities per term, each within the bf16 bound
     assert err.max() <= 1e-2 and err.mean() <= 1e-3
+
+
+@pytest.mark.parametrize("n_canon,nq", [(1, 31), (2, 43), (4, 28)])
+def test_relevancy_row_widths(gb, oracle_lib, n_canon, nq):
+    """Rows of at most 32 columns (read by shuffles) and wider rows (the
+    general loop), one or several canonical phrases, a ragged row count."""
+    import torch
+    rng = np.random.default_rng(100 + nq)
+    P = 1237
+    sim = rng.uniform(-1, 1, (P, n_canon + nq)).astype(np.float32)
+    R = torch.empty((P, nq), dtype=torch.float32, device="cuda")
+    gb.scoup_relevancy(torch.from_numpy(sim).cuda(), n_canon, R, alpha=10.0)
+    torch.cuda.synchronize()
+    s64 = sim.astype(np.float64)
+    want = np.stack([oracle_lib.relevancy(s64[:, n_canon + q], s64[:, :n_canon], 10.0) for q in range(nq)], axis=1)
+    assert np.abs(R.cpu().numpy() - want).max() <= 2e-6
