@@ -484,7 +484,9 @@ int scoup_similarity_fp32(const float* features, int64_t P, int32_t D, const flo
  *    (host, optional) receives the counters.
  *  - The first call on each device looks up the device address of the array
  *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    before any stream capture.  The address is kept per device and driver
+ *    context: after a device reset (a new primary context) the next call
+ *    looks it up again. 
  *  - Every call on a device shares the one array and leaves its contents
  *    behind (each call clears what must start at zero).  Calls that overlap on
  *    the GPU -- from several host threads or on several streams at once --

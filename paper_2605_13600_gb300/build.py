@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import glob
+import hashlib
 import os
 import shutil
 import subprocess
@@ -40,11 +41,28 @@ def _headers():
         os.path.join(os.path.dirname(HERE), "include", "scoup.h")]
 
 
-def _stale(target: str, deps) -> bool:
-    if not os.path.exists(target):
+def _digest(cmd, deps) -> str:
+    """SHA-256 of the compile command and the contents of every input."""
+    h = hashlib.sha256("\0".join(cmd).encode())
+    for d in deps:
+        with open(d, "rb") as f:
+            h.update(hashlib.sha256(f.read()).digest())
+    return h.hexdigest()
+
+
+def _stale(target: str, digest: str) -> bool:
+    """A target is rebuilt unless it exists and its stamp holds the digest of
+    its current inputs (file times alone miss a shipped, newer binary)."""
+    stamp = target + ".sha256"
+    if not (os.path.exists(target) and os.path.exists(stamp)):
         return True
-    t = os.path.getmtime(target)
-    return any(os.path.getmtime(d) > t for d in deps)
+    with open(stamp) as f:
+        return f.read().strip() != digest
+
+
+def _stamp(target: str, digest: str) -> None:
+    with open(target + ".sha256", "w") as f:
+        f.write(digest + "\n")
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -57,25 +75,30 @@ def build(force: bool = False, verbose: bool = False) -> str:
     for src in srcs:
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
-        if force or _stale(obj, [src] + hdrs):
-            cmd = [nvcc, *ARCH, *COMMON, *PER_FILE.get(os.path.basename(src), []), "-c", src, "-o", obj]
-            jobs.append(cmd)
+        cmd = [nvcc, *ARCH, *COMMON, *PER_FILE.get(os.path.basename(src), []), "-c", src, "-o", obj]
+        dig = _digest(cmd[1:], [src] + hdrs)
+        if force or _stale(obj, dig):
+            jobs.append((cmd, obj, dig))
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
-            results = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs))
-        for cmd, r in zip(jobs, results):
+            results = list(ex.map(lambda j: subprocess.run(j[0], capture_output=True, text=True), jobs))
+        for (cmd, obj, dig), r in zip(jobs, results):
             if verbose or r.returncode != 0:
                 sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
             if r.returncode != 0:
                 raise RuntimeError(f"nvcc failed for {cmd[-3]}")
-    if force or jobs or _stale(LIB, objs):
+            _stamp(obj, dig)
+    link = [*ARCH, "-shared"]
+    lib_dig = _digest(link, objs)
+    if force or jobs or _stale(LIB, lib_dig):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
+        cmd = [nvcc, *link, "-o", tmp, *objs]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)
             raise RuntimeError("link of libscoup.so failed")
         os.replace(tmp, LIB)
+        _stamp(LIB, lib_dig)
     return LIB
 
 

@@ -158,6 +158,22 @@ UpliftWs carve(void* ws, size_t bytes, int64_t n, int max_tiles, int64_t code_ro
   return w;
 }
 
+}  // namespace
+
+int num_sms() {
+  static std::atomic<int> cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  int n = cache[dev].load(std::memory_order_relaxed);
+  if (n <= 0) {
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    cache[dev].store(n, std::memory_order_relaxed);
+  }
+  return n;
+}
+
+namespace {
+
 // The library's second stream for the odd views of an uplift (one per host
 // thread and device, created on first use).
 cudaStream_t view_lane_stream() {

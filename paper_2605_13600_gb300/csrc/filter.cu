@@ -97,7 +97,7 @@ __global__ void relevancy_kernel(const float* __restrict__ sim, int64_t P, int n
 
 int grid_for(int64_t n) {
   int64_t b = (n + 255) / 256;
-  if (b > 152 * 8) b = 152 * 8;
+  if (b > num_sms() * 8) b = num_sms() * 8;
   return (int)(b > 0 ? b : 1);
 }
 

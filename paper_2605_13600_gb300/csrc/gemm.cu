@@ -280,16 +280,6 @@ bool make_tmap(CUtensorMap* m, const void* ptr, CUtensorMapDataType dt, int esiz
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-int num_sms() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
-  }
-  return n;
-}
-
 template <int BN>
 cudaError_t launch_bn(const void* A, const void* Bt, const GemmEpi& ep, cudaStream_t st) {
   CUtensorMap ta, tb, to;
@@ -349,7 +339,7 @@ __global__ void row_norm_bf16_kernel(const __nv_bfloat16* __restrict__ X, int64_
 
 int blocks_for(int64_t n, int per) {
   int64_t b = (n + per - 1) / per;
-  if (b > 152 * 16) b = 152 * 16;
+  if (b > num_sms() * 16) b = num_sms() * 16;
   return (int)(b > 0 ? b : 1);
 }
 

@@ -7,6 +7,7 @@
 // call.  They can still pass their inputs and outputs; the scratch this call
 // needs lives in g_uplift_scratch below, a file-scope __device__ array that
 // every GPU which loads this library holds until the process exits.
+#include <cuda.h>
 #include <stdio.h>
 
 #include <mutex>
@@ -23,20 +24,46 @@ __device__ __align__(256) unsigned char g_uplift_scratch[kNoAllocScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 void* g_scratch_addr[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};
 
-// Device address of g_uplift_scratch on the current device, looked up once
-// per device (the host-side name of the array is not a device address).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+
+// The driver's current context (through the runtime's entry-point query, so
+// the library needs no link against the driver library); null if unknown.
+CUcontext current_context() {
+  static CtxGetCurrentFn fn = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (CtxGetCurrentFn)p;
+    looked = true;
+  }
+  CUcontext c = nullptr;
+  if (fn && fn(&c) != CUDA_SUCCESS) c = nullptr;
+  return c;
+}
+
+// Device address of g_uplift_scratch on the current device (the host-side
+// name of the array is not a device address).  It is looked up once per
+// device and context: after a device reset the runtime loads the library's
+// module again in a new context, the array gets a new address, and the
+// cached one is replaced.
 cudaError_t scratch_address(void** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  const CUcontext ctx = current_context();
   std::lock_guard<std::mutex> lk(g_setup_mu);
-  if (!g_scratch_addr[dev]) {
+  if (!g_scratch_addr[dev] || !ctx || ctx != g_scratch_ctx[dev]) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_uplift_scratch);
+    e = cudaGetSymbolAddress(&p, g_uplift_scratch);  // also creates the context if there is none yet
     if (e != cudaSuccess) return e;
     g_scratch_addr[dev] = p;
+    g_scratch_ctx[dev] = current_context();
   }
   *out = g_scratch_addr[dev];
   return cudaSuccess;

@@ -177,7 +177,7 @@ cudaError_t launch_preprocess(const scoup_scene& sc, const CamArgs& cam, const U
                               int slot, cudaStream_t st) {
   if (sc.n <= 0) return cudaSuccess;
   int blocks = (int)((sc.n + 255) / 256);
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks > num_sms() * 8) blocks = num_sms() * 8;
   preprocess_kernel<<<blocks, 256, 0, st>>>(ws.sp.means, ws.sp.scales, ws.sp.quats, ws.sp.opacity,
                                             ws.sp.tau, ws.sp.orig, sc.n, cam, ws.proj, ws.depth, ws.rect,
                                             ws.hdr, slot);

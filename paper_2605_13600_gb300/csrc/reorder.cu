@@ -149,7 +149,7 @@ __global__ void init_header_kernel(WsHeader* __restrict__ hdr) {
 
 int grid_for(int64_t n, int per_sm) {
   int64_t b = (n + 255) / 256;
-  if (b > 152 * per_sm) b = 152 * per_sm;
+  if (b > num_sms() * per_sm) b = num_sms() * per_sm;
   return (int)(b > 0 ? b : 1);
 }
 

@@ -14,6 +14,10 @@ namespace scoup {
 // Kernel launches issued by the library (every launcher adds its count).
 extern std::atomic<long long> g_launches;
 
+// Streaming multiprocessors of the current device (queried once per device);
+// grid sizes of the grid-stride kernels are multiples of it.
+int num_sms();
+
 constexpr int kTile = 16;            // 16x16 pixel tiles define binning membership (3DGS)
 constexpr int kTilePixels = kTile * kTile;
 

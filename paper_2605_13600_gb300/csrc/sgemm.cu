@@ -113,7 +113,7 @@ cudaError_t launch_sgemm(const float* A, const float* B, bool b_transposed, floa
 cudaError_t launch_row_norm2_f32(const float* X, int64_t R, int D, float* out, cudaStream_t st) {
   if (R <= 0) return cudaSuccess;
   int64_t blocks = (R * 32 + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks > num_sms() * 16) blocks = num_sms() * 16;
   row_norm2_f32_kernel<<<(int)blocks, 256, 0, st>>>(X, R, D, out);
   g_launches += 1;
   return cudaGetLastError();

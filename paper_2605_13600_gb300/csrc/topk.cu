@@ -111,7 +111,7 @@ template <int VPL>
 cudaError_t launch_vpl(const float* acc, const float* comp, int64_t n, int C, int64_t ld, int K, int32_t* idx,
                        float* val, float* entropy, cudaStream_t st) {
   int64_t blocks = (n + 7) / 8;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks > num_sms() * 16) blocks = num_sms() * 16;
   topk_kernel<VPL><<<(int)blocks, 256, 0, st>>>(acc, comp, n, C, ld, K, idx, val, entropy);
   g_launches += 1;
   return cudaGetLastError();
@@ -135,7 +135,7 @@ cudaError_t launch_code_topk(const int32_t* ci, const float* cv, int64_t R, int 
                              int32_t* ci_out, float* cv_out, cudaStream_t st) {
   if (R <= 0) return cudaSuccess;
   int64_t blocks = (R + 255) / 256;
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks > num_sms() * 8) blocks = num_sms() * 8;
   code_topk_kernel<<<(int)blocks, 256, 0, st>>>(ci, cv, R, s, K, ci_out, cv_out);
   g_launches += 1;
   return cudaGetLastError();

@@ -579,6 +579,7 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
                 for (int a = 0; a < lc.s[l]; ++a) {
                   const int64_t row = (int64_t)r * lc.s[l] + a;
                   const int jj = lc.ci[l][row];
+                  if (jj >= C) atomicOr(&hdr->status, kStatDeviceCheck);
                   if (jj >= 0 && jj < C) {
                     acc_add<kComp>(accum, comp, g * Crow + l * C + jj, lc.cv[l][row], e[u], 0.0f);
                     ++n_atom;

@@ -156,6 +156,8 @@ def scoup_uplift_noalloc(scene: Scene, cams: Sequence, region_maps, map_offsets,
     """scoup_uplift with the library's fixed scratch array (no workspace
     argument, nothing allocated); synchronises and returns the stats dict."""
     import torch
+    if accum is not None and accum.numel() < scene.n * C * (2 if accum_mode & SCOUP_ACCUM_COMPENSATED else 1):
+        raise ValueError("accum is too small for n x C (x 2 when compensated)")
     _need(region_maps, torch.int32, "region_maps")
     _need(code_idx, torch.int32, "code_idx")
     _need(code_val, torch.float32, "code_val")

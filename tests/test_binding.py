@@ -33,3 +33,29 @@ def test_render_decode_fused_checks_types():
     f = torch.zeros((4, 16), dtype=torch.float16)
     with pytest.raises((TypeError, ValueError)):
         gb.scoup_render_decode_fused(None, None, None, 1, 8, None, torch.zeros((8, 16)), f, None, None, None, None)
+
+
+@pytest.mark.parametrize("entry", ["scoup_uplift", "scoup_uplift_host_maps", "scoup_uplift_noalloc"])
+@pytest.mark.parametrize("mode", [0, gb.SCOUP_ACCUM_COMPENSATED])
+def test_uplift_refuses_a_short_accumulator(monkeypatch, entry, mode):
+    """An accumulator shorter than n x C (2 n C when compensated) is refused in
+    the binding, before the library sees a pointer it would write past."""
+    def no_library():
+        raise AssertionError("the library must not be called")
+    monkeypatch.setattr(gb.scoup, "load", no_library)
+    from paper_2605_13600_gb300 import _lib
+    scene = _lib.Scene()
+    scene.n = 10
+    C = 8
+    short = torch.zeros(10 * C * (2 if mode else 1) - 1, dtype=torch.float32)
+    maps = torch.zeros(4, dtype=torch.int32)
+    args = dict(scene=scene, cams=[], map_offsets=[0], R_total=1, code_idx=None, code_val=None, s=1, C=C,
+                K=1, accum=short, accum_mode=mode, topk_idx=None, topk_val=None)
+    fn = getattr(gb, entry)
+    with pytest.raises(ValueError, match="accum is too small"):
+        if entry == "scoup_uplift_host_maps":
+            fn(host_region_maps=maps, workspace=None, **args)
+        elif entry == "scoup_uplift":
+            fn(region_maps=maps, workspace=None, **args)
+        else:
+            fn(region_maps=maps, **args)

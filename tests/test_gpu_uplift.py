@@ -73,12 +73,12 @@ def test_random_scene_parity(gb, oracle_lib, seed, W, H, n, V, R, C, s, K, lsm):
 
 def test_long_tile_lists_use_several_windows(gb, oracle_lib):
     """Thousands of Gaussians over a 48x32 image: every tile list is longer
-    than one sort window, so the windowed radix select is exercised."""
+    than one ordering window, so several windows are composited per tile."""
     wl = synth.tiny_workload(36, n=6000, width=48, height=32, V=2, R=4, C=16, s=3, K=3,
                              log_scale_mean=-2.0)
     wl.scene.opacity[:] = np.minimum(wl.scene.opacity, 0.08)  # keep pixels open for long
     up, st, *_ = _parity(gb, oracle_lib, wl, "long")
-    assert st["listed"] / (2 * 6) > 1500  # mean listed Gaussians per tile, above one 1024-key window
+    assert st["listed"] / (2 * 6) > 1500  # mean listed Gaussians per tile: several 256-key windows
 
 
 def test_unlabelled_pixels(gb, oracle_lib):
