@@ -17,6 +17,11 @@
 // pass expands the items only once and writes each CTA's keys of a tile into
 // one contiguous run.  Rectangles larger than kBigRect tiles go to separate
 // global counters and are placed after the reserved runs.
+//
+// Depth slabs.  Called for slab s of a view, both passes take only the
+// Gaussians whose depth lies in the slab, and for s > 0 only the tiles that
+// still hold an open pixel: a Gaussian whose rectangle has no such tile is
+// dropped before expansion, and items in done tiles are skipped.
 #include "scoup_internal.cuh"
 
 namespace scoup {
@@ -29,6 +34,45 @@ constexpr int64_t kChunk = 512;
 constexpr int kLocalMax = 4096;  // tiles of the per-CTA bounding box kept in shared memory
 constexpr int kBigRect = 256;
 constexpr unsigned kFull = 0xffffffffu;
+
+// Which Gaussians and tiles one binning call takes.
+struct SlabSel {
+  uint32_t lo, hi;       // depth bits [lo, hi) (hi unused when last)
+  bool active, last;
+  const uint8_t* done;   // tile done flags, or null (no tile is skipped)
+
+  __device__ __forceinline__ bool skip_tile(int t) const { return done && done[t]; }
+};
+
+__device__ __forceinline__ SlabSel slab_sel(const WsHeader* __restrict__ hdr, int slot, int slab, int last,
+                                            const uint8_t* done) {
+  SlabSel s;
+  s.active = slab >= 0;
+  s.last = last != 0;
+  s.done = s.active ? done : nullptr;
+  s.lo = s.active ? hdr->slab_lo[slot][slab] : 0u;
+  s.hi = (s.active && !s.last) ? hdr->slab_lo[slot][slab + 1] : 0xffffffffu;
+  return s;
+}
+
+// The rectangle Gaussian i is binned with in this call (empty if it is not).
+__device__ __forceinline__ ushort4 slab_rect(const ushort4* __restrict__ rects, const uint32_t* __restrict__ depth,
+                                             int64_t i, int64_t hi, const SlabSel& sel, int gx) {
+  const ushort4 none = make_ushort4(0, 0, 0, 0);
+  if (i >= hi) return none;
+  const ushort4 r = rects[i];
+  if (!sel.active || r.z <= r.x) return r;
+  const uint32_t d = depth[i];
+  if (d < sel.lo || (!sel.last && d >= sel.hi)) return none;
+  if (sel.done) {
+    bool open = false;
+    for (int ty = r.y; ty < r.w && !open; ++ty)
+      for (int tx = r.x; tx < r.z; ++tx)
+        if (!sel.done[ty * gx + tx]) { open = true; break; }
+    if (!open) return none;
+  }
+  return r;
+}
 
 struct LocalBox {
   int x0, y0, w, h;
@@ -82,16 +126,14 @@ __device__ __forceinline__ void expand_items(const ushort4& r, F&& f) {
   }
 }
 
-// Block-wide bounding box of the chunk's non-big rectangles.
-__device__ LocalBox chunk_box(const ushort4* __restrict__ rects, int64_t lo, int64_t hi) {
+// Block-wide bounding box of the chunk's non-big rectangles (one per thread).
+__device__ LocalBox chunk_box(const ushort4& r) {
   __shared__ int s_box[4];
   if (threadIdx.x == 0) { s_box[0] = 1 << 30; s_box[1] = 1 << 30; s_box[2] = 0; s_box[3] = 0; }
   __syncthreads();
   int x0 = 1 << 30, y0 = 1 << 30, x1 = 0, y1 = 0;
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    const ushort4 r = rects[i];
-    if (r.z <= r.x || big(r)) continue;
-    x0 = min(x0, (int)r.x); y0 = min(y0, (int)r.y); x1 = max(x1, (int)r.z); y1 = max(y1, (int)r.w);
+  if (r.z > r.x && !big(r)) {
+    x0 = r.x; y0 = r.y; x1 = r.z; y1 = r.w;
   }
   for (int off = 16; off > 0; off >>= 1) {
     x0 = min(x0, __shfl_xor_sync(0xffffffffu, x0, off));
@@ -113,22 +155,28 @@ __device__ LocalBox chunk_box(const ushort4* __restrict__ rects, int64_t lo, int
   return b;
 }
 
-__global__ void __launch_bounds__(kBinThreads) count_kernel(const ushort4* __restrict__ rects, int64_t n,
+static_assert(kChunk == kBinThreads, "one Gaussian per binning thread");
+
+__global__ void __launch_bounds__(kBinThreads) count_kernel(const ushort4* __restrict__ rects,
+                                                            const uint32_t* __restrict__ depth, int64_t n,
                                                             int gx, uint32_t* __restrict__ tile_count,
                                                             uint32_t* __restrict__ tile_glob,
-                                                            uint32_t* __restrict__ run_base) {
+                                                            uint32_t* __restrict__ run_base,
+                                                            const WsHeader* __restrict__ hdr, int slot, int slab,
+                                                            int last, const uint8_t* __restrict__ done) {
   __shared__ uint32_t s_cnt[kLocalMax];
+  const SlabSel sel = slab_sel(hdr, slot, slab, last, done);
   const int64_t lo = blockIdx.x * kChunk, hi = min(n, lo + kChunk);
-  const LocalBox box = chunk_box(rects, lo, hi);
+  const ushort4 r = slab_rect(rects, depth, lo + threadIdx.x, hi, sel, gx);
+  const LocalBox box = chunk_box(r);
   const int area = box.w * box.h;
   if (box.ok)
     for (int t = threadIdx.x; t < area; t += blockDim.x) s_cnt[t] = 0u;
   __syncthreads();
-  for (int k = 0; k < (int)(kChunk / kBinThreads); ++k) {
-    const int64_t i = lo + (int64_t)k * kBinThreads + threadIdx.x;
-    const ushort4 r = i < hi ? rects[i] : make_ushort4(0, 0, 0, 0);
+  {
     const unsigned lmask = __ballot_sync(kFull, box.ok && !big(r));
     expand_items(r, [&](int src, int tx, int ty) {
+      if (sel.skip_tile(ty * gx + tx)) return;
       if ((lmask >> src) & 1u) atomicAdd(&s_cnt[box.idx(tx, ty)], 1u);
       else atomicAdd(&tile_glob[ty * gx + tx], 1u);
     });
@@ -205,12 +253,15 @@ __global__ void __launch_bounds__(1024) scan_kernel(uint32_t* __restrict__ tile_
 __global__ void __launch_bounds__(kBinThreads) fill_kernel(
     const ushort4* __restrict__ rects, const uint32_t* __restrict__ depth, const int32_t* __restrict__ orig,
     int64_t n, int gx, const uint32_t* __restrict__ tile_start, uint32_t* __restrict__ tile_fill,
-    const uint32_t* __restrict__ run_base, unsigned long long* __restrict__ keys, const WsHeader* __restrict__ hdr) {
+    const uint32_t* __restrict__ run_base, unsigned long long* __restrict__ keys, const WsHeader* __restrict__ hdr,
+    int slot, int slab, int last, const uint8_t* __restrict__ done) {
   __shared__ uint32_t s_cnt[kLocalMax];
   __shared__ uint32_t s_base[kLocalMax];
   if (hdr->status & kStatCapacity) return;
+  const SlabSel sel = slab_sel(hdr, slot, slab, last, done);
   const int64_t lo = blockIdx.x * kChunk, hi = min(n, lo + kChunk);
-  const LocalBox box = chunk_box(rects, lo, hi);
+  const ushort4 r = slab_rect(rects, depth, lo + threadIdx.x, hi, sel, gx);
+  const LocalBox box = chunk_box(r);
   const int area = box.w * box.h;
   if (box.ok) {
     // the runs reserved by the counting pass (same chunk, same box)
@@ -221,9 +272,8 @@ __global__ void __launch_bounds__(kBinThreads) fill_kernel(
     }
     __syncthreads();
   }
-  for (int k = 0; k < (int)(kChunk / kBinThreads); ++k) {
-    const int64_t i = lo + (int64_t)k * kBinThreads + threadIdx.x;
-    const ushort4 r = i < hi ? rects[i] : make_ushort4(0, 0, 0, 0);
+  {
+    const int64_t i = lo + threadIdx.x;
     const unsigned long long my_key =
         i < hi ? (((unsigned long long)depth[i] << 32) | (uint32_t)orig[i]) : 0ull;
     const unsigned lmask = __ballot_sync(kFull, box.ok && !big(r));
@@ -255,6 +305,7 @@ __global__ void __launch_bounds__(kBinThreads) fill_kernel(
         const int local = item - e_src;
         const int yy = div_small(local, w_src);
         const int tx = (p_src & 0xffff) + (local - yy * w_src), ty = (p_src >> 16) + yy;
+        if (sel.skip_tile(ty * gx + tx)) continue;
         uint32_t pos;
         if ((lmask >> src) & 1u) {
           const int t = box.idx(tx, ty);
@@ -276,16 +327,20 @@ size_t binning_run_base_bytes(int64_t n) {
 }
 
 cudaError_t launch_binning(const CamArgs& cam, int64_t n, const UpliftWs& ws, int slot,
-                           cudaStream_t st) {
+                           cudaStream_t st, int slab, bool last_slab) {
   const int ntiles = cam.gx * cam.gy;
   const int blocks = (int)((n + kChunk - 1) / kChunk);
+  const uint8_t* done = slab > 0 ? ws.tile_done : nullptr;
+  const int last = last_slab ? 1 : 0;
   if (n > 0)
-    count_kernel<<<blocks, kBinThreads, 0, st>>>(ws.rect, n, cam.gx, ws.tile_count, ws.tile_glob, ws.run_base);
+    count_kernel<<<blocks, kBinThreads, 0, st>>>(ws.rect, ws.depth, n, cam.gx, ws.tile_count, ws.tile_glob,
+                                                 ws.run_base, ws.hdr, slot, slab, last, done);
   scan_kernel<<<1, 1024, 0, st>>>(ws.tile_count, ws.tile_glob, ws.tile_start, ws.tile_fill, ntiles,
                                   ws.dup_capacity, ws.hdr, slot);
   if (n > 0)
     fill_kernel<<<blocks, kBinThreads, 0, st>>>(ws.rect, ws.depth, ws.sp.orig, n, cam.gx, ws.tile_start,
-                                                ws.tile_fill, ws.run_base, ws.keys, ws.hdr);
+                                                ws.tile_fill, ws.run_base, ws.keys, ws.hdr, slot, slab, last,
+                                                done);
   g_launches += n > 0 ? 3 : 1;
   return cudaGetLastError();
 }

@@ -11,6 +11,11 @@
 // evaluated left to right in IEEE binary32 with each operation rounded, in the
 // operation order written here, so the discrete outcomes (cull, radius,
 // rectangle, depth) are reproducible on any IEEE binary32 machine.
+//
+// With depth slabs the kernel also resets the per-pixel slab state of the view
+// and counts the listed Gaussians in a depth histogram (float bits >> 16: 128
+// buckets per octave from 0.2 up); the last CTA to finish turns the histogram
+// into the slab bounds (its quantiles) and clears it for the next view.
 #include <math.h>
 
 #include "scoup_internal.cuh"
@@ -24,6 +29,62 @@ __device__ __forceinline__ int tile_clamp(float v, int g) {
   return (int)v;
 }
 
+__device__ __forceinline__ int depth_bucket(uint32_t bits) {
+  const uint32_t b = (bits >> 16) - kDepthBucketBase;  // bits >= those of 0.2f for every listed Gaussian
+  return (int)min(b, (uint32_t)(kDepthBuckets - 1));
+}
+
+// Slab state of a view: the per-pixel transmittance records and the tile
+// done flags start cleared (0 = untouched pixel, tile open).
+struct SlabArgs {
+  SlabPlan plan;
+  uint32_t* dhist;
+  float* pix_state;
+  uint8_t* tile_done;
+  int ntiles;
+};
+
+// Run by the last CTA of the projection: slab bounds at the plan's quantiles
+// of the histogram; the histogram and the CTA counter are cleared.
+__device__ void slab_bounds(const SlabArgs& sa, WsHeader* __restrict__ hdr, int slot) {
+  constexpr int kPer = kDepthBuckets / 256;
+  __shared__ uint32_t s_warp[8];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint32_t c[kPer], sum = 0;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) { c[q] = __ldcg(&sa.dhist[tid * kPer + q]); sum += c[q]; }
+  uint32_t incl = sum;
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += y;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  uint32_t wbase = 0, total = 0;
+  for (int w = 0; w < 8; ++w) { total += s_warp[w]; if (w < warp) wbase += s_warp[w]; }
+  const uint32_t excl = wbase + incl - sum;
+  if (tid == 0) hdr->slab_lo[slot][0] = 0u;
+  for (int k = 0; k + 1 < sa.plan.nslabs; ++k) {
+    // slab k + 1 starts after the bucket in which the running count reaches the target
+    const uint32_t target = (uint32_t)ceilf(sa.plan.q[k] * (float)total);
+    if (target == 0u) {
+      if (tid == 0) hdr->slab_lo[slot][k + 1] = 0u;
+    } else if (target > excl && target <= excl + sum) {
+      uint32_t run = excl;
+      int b = tid * kPer;
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        run += c[q];
+        if (run >= target) { b = tid * kPer + q; break; }
+      }
+      hdr->slab_lo[slot][k + 1] = (uint32_t)(b + 1 + kDepthBucketBase) << 16;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) sa.dhist[tid * kPer + q] = 0u;
+  if (tid == 0) hdr->pp_blocks[slot] = 0u;
+}
+
 // Thread p projects Gaussian p of the spatially ordered copy; the record is
 // stored at its original index, depth and rectangle in spatial order.
 __global__ void __launch_bounds__(256) preprocess_kernel(
@@ -32,7 +93,20 @@ __global__ void __launch_bounds__(256) preprocess_kernel(
     const float* __restrict__ tau, const int32_t* __restrict__ orig, int64_t n, CamArgs cam,
     ProjRec* __restrict__ proj,
     uint32_t* __restrict__ depth_bits, ushort4* __restrict__ rects, WsHeader* __restrict__ hdr,
-    int slot) {
+    int slot, SlabArgs sa) {
+  __shared__ uint32_t s_hist[kDepthBuckets];
+  const bool slabs = sa.plan.nslabs > 1;
+  if (slabs) {
+    for (int b = threadIdx.x; b < kDepthBuckets; b += blockDim.x) s_hist[b] = 0u;
+    const int64_t nstate = (int64_t)sa.ntiles * (kTilePixels / 4);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nstate;
+         i += (int64_t)gridDim.x * blockDim.x)
+      reinterpret_cast<float4*>(sa.pix_state)[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < sa.ntiles;
+         i += (int64_t)gridDim.x * blockDim.x)
+      sa.tile_done[i] = 0;
+    __syncthreads();
+  }
   unsigned long long my_vis = 0, my_dups = 0;
   uint32_t my_dmin = 0xffffffffu, my_dmax = 0u;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -111,7 +185,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(
         if (xhi > xlo && yhi > ylo) {
           ProjRec pr;
           pr.a = make_float4(mx, my, -0.5f * con_a, -con_b);
-          pr.b = make_float4(-0.5f * con_c, opacity[i], tau[i], 0.0f);
+          pr.b = make_float4(-0.5f * con_c, opacity[i], tau[i], log2f(opacity[i]));
           proj[orig[i]] = pr;
           // Binning lists only the tiles of the rectangle that also meet the
           // bounding box of the alpha >= 1/255 ellipse {d : power(d) >= tau}:
@@ -130,11 +204,13 @@ __global__ void __launch_bounds__(256) preprocess_kernel(
             ly0 = max(ylo, tile_clamp(floorf((my - ey) / 16.0f), cam.gy));
             ly1 = min(yhi, tile_clamp(floorf((my + ey) / 16.0f) + 1.0f, cam.gy));
           }
-          if (lx1 > lx0 && ly1 > ly0)
+          if (lx1 > lx0 && ly1 > ly0) {
             rect = make_ushort4((unsigned short)lx0, (unsigned short)ly0, (unsigned short)lx1,
                                 (unsigned short)ly1);
-          else
+            if (slabs) atomicAdd(&s_hist[depth_bucket(__float_as_uint(t2))], 1u);
+          } else {
             rect = make_ushort4(0, 0, 0, 0);
+          }
           my_vis += 1;
           my_dups += (unsigned long long)(xhi - xlo) * (unsigned long long)(yhi - ylo);
           my_dmin = min(my_dmin, __float_as_uint(t2));
@@ -169,18 +245,38 @@ __global__ void __launch_bounds__(256) preprocess_kernel(
       atomicMax(&hdr->drange[slot][1], hi);
     }
   }
+  if (slabs) {
+    __shared__ bool s_last;
+    for (int b = threadIdx.x; b < kDepthBuckets; b += blockDim.x)
+      if (s_hist[b]) atomicAdd(&sa.dhist[b], s_hist[b]);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&hdr->pp_blocks[slot], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      slab_bounds(sa, hdr, slot);
+    }
+  }
 }
 
 }  // namespace
 
 cudaError_t launch_preprocess(const scoup_scene& sc, const CamArgs& cam, const UpliftWs& ws,
-                              int slot, cudaStream_t st) {
+                              int slot, cudaStream_t st, const SlabPlan* plan) {
   if (sc.n <= 0) return cudaSuccess;
   int blocks = (int)((sc.n + 255) / 256);
   if (blocks > num_sms() * 8) blocks = num_sms() * 8;
+  SlabArgs sa;
+  sa.plan.nslabs = 1;
+  if (plan && plan->nslabs > 1) sa.plan = *plan;
+  sa.dhist = ws.dhist;
+  sa.pix_state = ws.pix_state;
+  sa.tile_done = ws.tile_done;
+  sa.ntiles = cam.gx * cam.gy;
   preprocess_kernel<<<blocks, 256, 0, st>>>(ws.sp.means, ws.sp.scales, ws.sp.quats, ws.sp.opacity,
                                             ws.sp.tau, ws.sp.orig, sc.n, cam, ws.proj, ws.depth, ws.rect,
-                                            ws.hdr, slot);
+                                            ws.hdr, slot, sa);
   g_launches += 1;
   return cudaGetLastError();
 }

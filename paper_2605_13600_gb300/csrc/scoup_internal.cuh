@@ -26,9 +26,19 @@ constexpr int kStatCapacity = 1;
 constexpr int kStatDeviceCheck = 2;
 constexpr int kStatTimeout = 4;
 
+// Depth slabs.  The visible Gaussians of a view are split by depth into up to
+// kMaxSlabs slabs (front to back) at quantiles of their depth; every key of
+// slab s is smaller than every key of slab s + 1, so compositing the slabs in
+// turn, each in exact (depth, index) order, is compositing the whole list in
+// that order.  Slab s > 0 is binned only into tiles with a pixel that is still
+// open, which skips the Gaussians hidden behind saturated tiles.
+constexpr int kMaxSlabs = 6;
+constexpr int kDepthBuckets = 2048;        // depth histogram: float bits >> 16, from 0.2 up
+constexpr uint32_t kDepthBucketBase = 0x3E4Cu;  // (bits of 0.2f) >> 16
+
 // Workspace header: status word, per-view depth range (double-buffered by
-// view parity in each of the two view pipelines), scene bounding box and
-// counters, 256 bytes.
+// view parity in each of the two view pipelines), scene bounding box,
+// counters and the slab bounds of each slot, 256 bytes.
 struct WsHeader {
   int32_t status;
   int32_t max_dups_view;
@@ -41,12 +51,21 @@ struct WsHeader {
   unsigned long long flushes;
   unsigned long long atomics;
   unsigned long long listed;
-  unsigned long long reserved[17];
+  uint32_t slab_lo[4][kMaxSlabs];  // [slot][s]: smallest depth bits of slab s (slab 0 starts at 0)
+  uint32_t pp_blocks[4];           // projection CTAs finished in this slot's view (last one sets slab_lo)
+  unsigned long long reserved[3];
 };
 static_assert(sizeof(WsHeader) == 256, "header size");
 
+// Slab schedule of one uplift: nslabs slabs whose bounds sit at the given
+// quantiles of the visible Gaussians' depths (nslabs - 1 of them, ascending).
+struct SlabPlan {
+  int nslabs;
+  float q[kMaxSlabs - 1];
+};
+
 // Projected Gaussian of one view, 32 bytes:
-//   a = (mx, my, qa, qb), b = (qc, opacity, tau, unused)
+//   a = (mx, my, qa, qb), b = (qc, opacity, tau, log2(opacity))
 // power(dx, dy) = dx*(qa*dx + qb*dy) + (qc*dy)*dy and the Gaussian is
 // accepted at a pixel iff tau <= power <= 0  (tau: smallest float with
 // o*exp(tau) >= 1/255).
@@ -133,6 +152,10 @@ struct UpliftWs {
   uint32_t* run_base;       // [chunks x box tiles] offset of each binning CTA's run in a tile list
   uint32_t* tile_start;     // [max_tiles + 1]
   uint32_t* tile_fill;      // [max_tiles]
+  float* pix_state;         // [max_tiles * 256] per pixel between slabs: 0 = untouched (T = 1),
+                            //     > 0 = transmittance T, < 0 = stopped
+  uint8_t* tile_done;       // [max_tiles] 1 once every pixel of the tile has stopped
+  uint32_t* dhist;          // [kDepthBuckets] depth histogram of the view being projected
   unsigned long long* keys; // [dup_capacity] (depth bits << 32 | gid)
   int64_t dup_capacity;
   int max_tiles;
@@ -182,14 +205,23 @@ void header_stats(const struct WsHeader& h, scoup_stats* stats);
 // Launchers (each defined in its own translation unit).
 size_t reorder_scratch_bytes();
 cudaError_t launch_reorder(const scoup_scene& sc, const UpliftWs& ws, cudaStream_t st);
+// With slabs (plan and plan->nslabs > 1) the projection also clears the
+// per-pixel slab state and builds the depth histogram from which its last CTA
+// sets hdr->slab_lo[slot].
 cudaError_t launch_preprocess(const scoup_scene& sc, const CamArgs& cam, const UpliftWs& ws,
-                              int slot, cudaStream_t st);
+                              int slot, cudaStream_t st, const SlabPlan* plan = nullptr);
 size_t binning_run_base_bytes(int64_t n);
+// slab < 0: every listed Gaussian into every tile of its rectangle.  slab s >= 0:
+// only Gaussians of slab s (bounds in hdr->slab_lo[slot]; s = last takes no
+// upper bound), and for s > 0 only into tiles not yet marked done.
 cudaError_t launch_binning(const CamArgs& cam, int64_t n, const UpliftWs& ws, int slot,
-                           cudaStream_t st);
+                           cudaStream_t st, int slab = -1, bool last_slab = true);
 // Accumulator rows are Crow = L * C floats wide; level l owns columns [l C, (l + 1) C).
+// slab / nslabs: the tiles composite slab `slab` of nslabs, resuming each
+// pixel from ws.pix_state unless slab == 0 and saving it unless it is the last.
 cudaError_t launch_uplift_tiles(const CamArgs& cam, const UpliftWs& ws, int slot, const LevelCodes& lc, int C,
-                                int Crow, float* accum, float* comp, int warp_w, cudaStream_t st);
+                                int Crow, float* accum, float* comp, int warp_w, cudaStream_t st,
+                                int slab = 0, int nslabs = 1);
 size_t render_smem_bytes(int C, int K);
 bool render_uses_mma(int C, int K);
 bool render_mma_supported(int C, int K);

@@ -45,6 +45,11 @@
 // it independently (records staged per warp, no block barrier) and leaves as
 // soon as its 32 pixels are saturated; the block meets again only at the end
 // of the window.
+//
+// Depth slabs.  With several slabs per view the kernel runs once per slab;
+// each pixel's transmittance (or its stop) is carried from one slab to the
+// next in pix_state, and a tile whose pixels have all stopped is marked done:
+// it returns at once in later slabs, and binning lists nothing for it.
 #include <math.h>
 
 #include "scoup_internal.cuh"
@@ -64,7 +69,11 @@ constexpr int kMaxSlots = 4;
 constexpr int kMaxS = 64;  // codes of up to kMaxS entries are staged in shared memory; longer
                            // ones (dense features, Eq. 3) are read from the code table in the flush
 constexpr int kGroup = 8;
+// Records of a window are box-tested and compacted per warp in batches of
+// kCompact; the warp composites the compacted list in full groups of kGroup.
+constexpr int kCompact = 128;
 constexpr unsigned kFull = 0xffffffffu;
+constexpr float kLog2e = 1.4426950408889634f;
 
 // Region of a pixel: the region id (one level) or the packed level tuple.
 template <int kL> struct RegionKey { using T = int; };
@@ -80,8 +89,9 @@ struct TileSmem {
   uint32_t bstart[kNB + 1];
   uint32_t bcur[kNB];
   unsigned long long win[kWin];
-  float4 rec_a[kWin];  // the window's projected records, loaded once per window
-  float4 rec_b[kWin];
+  float4 rec_a[kWin + 1];  // the window's projected records, loaded once per window; entry kWin is
+  float4 rec_b[kWin + 1];  // a record no pixel accepts (pads the warps' lists to whole groups)
+  int wlist[kThreads / 32][kCompact + kGroup];  // per warp: window entries that may reach its pixels
   float part[kMaxSlots][kWin];
   float part_c[kComp ? kMaxSlots : 1][kComp ? kWin : 1];
   uint32_t nz[kMaxSlots][kWin / 32];  // window entries whose partial became non-zero
@@ -194,6 +204,15 @@ __device__ __forceinline__ float transpose_reduce8(const float (&v)[kGroup], int
   return d;
 }
 
+// 2^x by the SFU's approximate base-2 exponential (relative error about
+// 2^-22; results below the smallest normal flush to zero, far below any
+// accepted alpha).
+__device__ __forceinline__ float exp2f_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Error of s = fl(a + b) (Knuth's TwoSum): a + b = s + err exactly.
 __device__ __forceinline__ float two_sum_err(float a, float b, float s) {
   const float bp = __fsub_rn(s, a);
@@ -232,7 +251,9 @@ template <bool kComp, int kBW, int kL>
 __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
     CamArgs cam, const ProjRec* __restrict__ proj, const unsigned long long* __restrict__ keys,
     const uint32_t* __restrict__ tile_start, int slot, LevelCodes lc, int C, int Crow,
-    float* __restrict__ accum, float* __restrict__ comp, WsHeader* __restrict__ hdr) {
+    float* __restrict__ accum, float* __restrict__ comp, WsHeader* __restrict__ hdr,
+    float* __restrict__ pix_state, uint8_t* __restrict__ tile_done, int slab, int nslabs) {
+  const bool first_slab = slab == 0, last_slab = slab == nslabs - 1;
   using RK = typename RegionKey<kL>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TileSmem<kComp, kL>& sm = *reinterpret_cast<TileSmem<kComp, kL>*>(smem_raw);
@@ -242,15 +263,21 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
   const float* __restrict__ code_val = lc.cv[0];
   const int tile = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (pix_state && !first_slab && tile_done[tile]) return;  // every pixel stopped in an earlier slab
   const uint32_t begin = tile_start[tile];
   const int n = (int)(tile_start[tile + 1] - begin);
-  if (n == 0) return;
+  if (n == 0) return;  // nothing of this slab here: the pixels' state stays as it is
   if (hdr->status & kStatCapacity) return;
   const unsigned long long* tkeys = keys + begin;
 
   Buckets bk;
   {
-    const uint32_t dmin = hdr->drange[slot][0], dmax = hdr->drange[slot][1];
+    // the buckets span the view's visible depths, cut to this slab's range
+    uint32_t dmin = hdr->drange[slot][0], dmax = hdr->drange[slot][1];
+    if (nslabs > 1) {
+      dmin = max(dmin, hdr->slab_lo[slot][slab]);
+      if (!last_slab && hdr->slab_lo[slot][slab + 1] > 0u) dmax = min(dmax, hdr->slab_lo[slot][slab + 1] - 1u);
+    }
     const uint32_t span = dmax >= dmin ? dmax - dmin : 0u;
     const int nb = span ? 32 - __clz((int)span) : 0;
     bk.dmin = dmin;
@@ -292,6 +319,11 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
   if constexpr (kComp)
     for (int k = tid; k < kMaxSlots * kWin; k += kThreads) (&sm.part_c[0][0])[k] = 0.0f;
   for (int k = tid; k < kMaxSlots * (kWin / 32); k += kThreads) (&sm.nz[0][0])[k] = 0u;
+  if (tid == 0) {
+    // power = 0 for any pixel, never >= tau = +inf: no pixel accepts it
+    sm.rec_a[kWin] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    sm.rec_b[kWin] = make_float4(0.0f, 0.0f, INFINITY, 0.0f);
+  }
   for (int b = tid; b < kNB; b += kThreads) sm.bcur[b] = 0u;
   if (tid < 4) sm.cnt[tid] = 0ull;
   __syncthreads();
@@ -368,6 +400,11 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
 
   float T = 1.0f;
   bool done = !inside;
+  if (pix_state && !first_slab) {
+    const float sv = pix_state[(int64_t)tile * kTilePixels + tid];
+    if (sv < 0.0f) done = true;
+    else if (sv > 0.0f) T = sv;
+  }
   unsigned n_eval = 0, n_contrib = 0, n_flush = 0, n_atom = 0;  // per thread and tile: fits 32 bits
 
   int b0 = 0;
@@ -504,74 +541,77 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
     bool warp_done = __all_sync(kFull, done);
     const float4* st_a = sm.rec_a;
     const float4* st_b = sm.rec_b;
-    for (int j0 = 0; j0 < m && !warp_done; j0 += 32) {
-      bool rel = false;
-      if (j0 + lane < m) {
-        ProjRec pr;
-        pr.a = st_a[j0 + lane];
-        pr.b = st_b[j0 + lane];
-        rel = box_may_hit(pr, bx0, by0, (float)kBW, (float)kBH);
-      }
-      unsigned rmask = __ballot_sync(kFull, rel);
-      __syncwarp();
-      while (rmask != 0u && !warp_done) {
-        int idx[kGroup];
-#pragma unroll
-        for (int u = 0; u < kGroup; ++u) {
-          idx[u] = rmask ? __ffs(rmask) - 1 : -1;
-          rmask &= rmask ? rmask - 1u : 0u;
+    int* wl = sm.wlist[warp];
+    for (int c0 = 0; c0 < m && !warp_done; c0 += kCompact) {
+      // box test of the next kCompact records; the warp's list keeps, in
+      // window order, the entries that may reach one of its pixels, padded
+      // with the dummy entry kWin to whole groups
+      const int c1 = min(m, c0 + kCompact);
+      int cnt = 0;
+      for (int j0 = c0; j0 < c1; j0 += 32) {
+        const int j = j0 + lane;
+        bool rel = false;
+        if (j < c1) {
+          ProjRec pr;
+          pr.a = st_a[j];
+          pr.b = st_b[j];
+          rel = box_may_hit(pr, bx0, by0, (float)kBW, (float)kBH);
         }
+        const unsigned rmask = __ballot_sync(kFull, rel);
+        if (rel) wl[cnt + __popc(rmask & ((1u << lane) - 1u))] = j;
+        cnt += __popc(rmask);
+      }
+      if (lane < kGroup) wl[cnt + lane] = kWin;
+      __syncwarp();
+      for (int g0 = 0; g0 < cnt && !warp_done; g0 += kGroup) {
+        const int* idx = wl + g0;  // this group's window entries (read per slot: fewer live registers)
+        // slots of this group this pixel examines: all real ones while it is
+        // open, up to and including the one at which it stops
+        int ev = done ? 0 : min(kGroup, cnt - g0);
         float e[kGroup];
 #pragma unroll
         for (int u = 0; u < kGroup; ++u) {
-          // branch-free: every lane evaluates, inactive lanes discard the result
-          const int q = idx[u] < 0 ? 0 : idx[u];
-          const float4 a = st_a[j0 + q];
-          const float4 b = st_b[j0 + q];
-          const bool live = idx[u] >= 0 && !done;
+          const float4 a = st_a[idx[u]];
+          const float4 b = st_b[idx[u]];
           const float dx = a.x - fpx, dy = a.y - fpy;
           // power = dx*(qa*dx + qb*dy) + (qc*dy)*dy: products rounded, two fused sums
           const float power = fmaf(dx, fmaf(a.z, dx, __fmul_rn(a.w, dy)), __fmul_rn(__fmul_rn(b.x, dy), dy));
-          const bool accept = live && power <= 0.0f && power >= b.z;
-          const float alpha = fminf(0.99f, b.y * __expf(power));
-          const float test = T * (1.0f - alpha);
+          const bool accept = !done && power <= 0.0f && power >= b.z;
+          // alpha = min(0.99, o exp(power)) = min(0.99, 2^(power log2(e) + log2(o))), b.w = log2(o)
+          const float alpha = fminf(0.99f, exp2f_approx(fmaf(power, kLog2e, b.w)));
+          const float test = fmaf(-T, alpha, T);  // T (1 - alpha)
           const bool stop = accept && test < 1e-4f;
           const bool take = accept && !stop;
           e[u] = take ? alpha * T : 0.0f;
           T = take ? test : T;
+          ev = stop ? u + 1 : ev;
           done = done || stop;
-          n_eval += live ? 1u : 0u;
           n_contrib += take ? 1u : 0u;
         }
-        bool has = false;
+        n_eval += (unsigned)ev;
+        // Gaussian of this lane's quarter of the reduction (its window entry)
+        const int jq = wl[g0 + (lane >> 2)];
+        if (wslot >= 0) {
+          const float S = transpose_reduce8(e, lane);
+          if ((lane & 3) == 0 && S > 0.0f)
+            part_add<kComp>(sm.part[wslot], sm.part_c[kComp ? wslot : 0], sm.nz[wslot], jq, S);
+        } else {
+          // pixels of several regions: one masked transpose reduction per slot present
+          for (unsigned qm = wslots; qm != 0u; qm &= qm - 1u) {
+            const int q = __ffs(qm) - 1;
+            float v[kGroup];
 #pragma unroll
-        for (int u = 0; u < kGroup; ++u) has |= e[u] > 0.0f;
-        if (__any_sync(kFull, has)) {
-          int jq = idx[0];
-#pragma unroll
-          for (int u = 1; u < kGroup; ++u) jq = (lane >> 2) == u ? idx[u] : jq;
-          if (wslot >= 0) {
-            const float S = transpose_reduce8(e, lane);
+            for (int u = 0; u < kGroup; ++u) v[u] = my_slot == q ? e[u] : 0.0f;
+            const float S = transpose_reduce8(v, lane);
             if ((lane & 3) == 0 && S > 0.0f)
-              part_add<kComp>(sm.part[wslot], sm.part_c[kComp ? wslot : 0], sm.nz[wslot], j0 + jq, S);
-          } else {
-            // pixels of several regions: one masked transpose reduction per slot present
-            for (unsigned qm = wslots; qm != 0u; qm &= qm - 1u) {
-              const int q = __ffs(qm) - 1;
-              float v[kGroup];
-#pragma unroll
-              for (int u = 0; u < kGroup; ++u) v[u] = my_slot == q ? e[u] : 0.0f;
-              const float S = transpose_reduce8(v, lane);
-              if ((lane & 3) == 0 && S > 0.0f)
-                part_add<kComp>(sm.part[q], sm.part_c[kComp ? q : 0], sm.nz[q], j0 + jq, S);
-            }
+              part_add<kComp>(sm.part[q], sm.part_c[kComp ? q : 0], sm.nz[q], jq, S);
           }
-          if (any_unslotted && has && my_slot < 0 && region_set(region)) {
+          if (any_unslotted && my_slot < 0 && region_set(region)) {
             // more regions in this tile than slots: scatter this pixel directly
 #pragma unroll
             for (int u = 0; u < kGroup; ++u) {
               if (!(e[u] > 0.0f)) continue;
-              const int64_t g = (int64_t)(sm.win[j0 + idx[u]] & 0xffffffffull);
+              const int64_t g = (int64_t)(sm.win[idx[u]] & 0xffffffffull);
               for (int l = 0; l < (kL == 1 ? 1 : lc.L); ++l) {
                 int r;
                 if constexpr (kL == 1) r = region; else r = level_region(region, l);
@@ -592,7 +632,7 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
         }
         warp_done = __all_sync(kFull, done);
       }
-      __syncwarp();
+      __syncwarp();  // the list is rewritten by the next batch
     }
     __syncthreads();
     // ---- flush the (region, Gaussian) tile partials of this window ----
@@ -658,6 +698,12 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
     __syncthreads();
   }
 
+  // ---- state for the next slab ----
+  if (pix_state && !last_slab) {
+    pix_state[(int64_t)tile * kTilePixels + tid] = done ? -1.0f : T;
+    if (__syncthreads_and(done) && tid == 0) tile_done[tile] = 1;
+  }
+
   // ---- counters ----
   for (int off = 16; off > 0; off >>= 1) {
     n_eval += __shfl_xor_sync(kFull, n_eval, off);
@@ -680,41 +726,54 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
   }
 }
 
+struct SlabLaunch {
+  float* pix_state;  // null with a single slab
+  uint8_t* tile_done;
+  int slab, nslabs;
+};
+
 template <bool kComp, int kBW, int kL>
 cudaError_t launch_tiles_t(const CamArgs& cam, const UpliftWs& ws, int slot, const LevelCodes& lc, int C, int Crow,
-                           float* accum, float* comp, cudaStream_t st) {
+                           float* accum, float* comp, const SlabLaunch& sl, cudaStream_t st) {
   const int ntiles = cam.gx * cam.gy;
   const size_t smem = sizeof(TileSmem<kComp, kL>);
   cudaError_t err = cudaFuncSetAttribute(uplift_tile_kernel<kComp, kBW, kL>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  uplift_tile_kernel<kComp, kBW, kL><<<ntiles, kThreads, smem, st>>>(cam, ws.proj, ws.keys, ws.tile_start, slot, lc,
-                                                                     C, Crow, accum, comp, ws.hdr);
+  uplift_tile_kernel<kComp, kBW, kL><<<ntiles, kThreads, smem, st>>>(
+      cam, ws.proj, ws.keys, ws.tile_start, slot, lc, C, Crow, accum, comp, ws.hdr, sl.pix_state, sl.tile_done,
+      sl.slab, sl.nslabs);
   g_launches += 1;
   return cudaGetLastError();
 }
 
 template <bool kComp>
 cudaError_t launch_tiles_shape(int warp_w, const CamArgs& cam, const UpliftWs& ws, int slot, const LevelCodes& lc,
-                               int C, int Crow, float* accum, float* comp, cudaStream_t st) {
-  if (lc.L > 1) return launch_tiles_t<kComp, 8, 3>(cam, ws, slot, lc, C, Crow, accum, comp, st);
+                               int C, int Crow, float* accum, float* comp, const SlabLaunch& sl, cudaStream_t st) {
+  if (lc.L > 1) return launch_tiles_t<kComp, 8, 3>(cam, ws, slot, lc, C, Crow, accum, comp, sl, st);
   switch (warp_w) {
-    case 16: return launch_tiles_t<kComp, 16, 1>(cam, ws, slot, lc, C, Crow, accum, comp, st);
-    case 4: return launch_tiles_t<kComp, 4, 1>(cam, ws, slot, lc, C, Crow, accum, comp, st);
-    default: return launch_tiles_t<kComp, 8, 1>(cam, ws, slot, lc, C, Crow, accum, comp, st);
+    case 16: return launch_tiles_t<kComp, 16, 1>(cam, ws, slot, lc, C, Crow, accum, comp, sl, st);
+    case 4: return launch_tiles_t<kComp, 4, 1>(cam, ws, slot, lc, C, Crow, accum, comp, sl, st);
+    default: return launch_tiles_t<kComp, 8, 1>(cam, ws, slot, lc, C, Crow, accum, comp, sl, st);
   }
 }
 
 }  // namespace
 
 cudaError_t launch_uplift_tiles(const CamArgs& cam, const UpliftWs& ws, int slot, const LevelCodes& lc, int C,
-                                int Crow, float* accum, float* comp, int warp_w, cudaStream_t st) {
+                                int Crow, float* accum, float* comp, int warp_w, cudaStream_t st, int slab,
+                                int nslabs) {
   static_assert(sizeof(TileSmem<false, 1>) <= 55 * 1024, "4 CTAs per SM");
   static_assert(sizeof(TileSmem<false, 3>) <= 55 * 1024, "4 CTAs per SM");
   static_assert(sizeof(TileSmem<true, 3>) <= 74 * 1024, "3 CTAs per SM");
   if (cam.gx * cam.gy <= 0) return cudaSuccess;
-  if (comp) return launch_tiles_shape<true>(warp_w, cam, ws, slot, lc, C, Crow, accum, comp, st);
-  return launch_tiles_shape<false>(warp_w, cam, ws, slot, lc, C, Crow, accum, nullptr, st);
+  SlabLaunch sl;
+  sl.pix_state = nslabs > 1 ? ws.pix_state : nullptr;
+  sl.tile_done = ws.tile_done;
+  sl.slab = nslabs > 1 ? slab : 0;
+  sl.nslabs = nslabs > 1 ? nslabs : 1;
+  if (comp) return launch_tiles_shape<true>(warp_w, cam, ws, slot, lc, C, Crow, accum, comp, sl, st);
+  return launch_tiles_shape<false>(warp_w, cam, ws, slot, lc, C, Crow, accum, nullptr, sl, st);
 }
 
 }  // namespace scoup
