@@ -150,7 +150,7 @@ __device__ LocalBox chunk_box(const ushort4& r) {
   b.y0 = s_box[1];
   b.w = max(0, s_box[2] - s_box[0]);
   b.h = max(0, s_box[3] - s_box[1]);
-  b.ok = b.w * b.h <= kLocalMax;
+  b.ok = (b.w + 1) * (b.h + 1) <= kLocalMax;  // the counting pass's difference array has one more row and column
   __syncthreads();
   return b;
 }
@@ -170,24 +170,52 @@ __global__ void __launch_bounds__(kBinThreads) count_kernel(const ushort4* __res
   const ushort4 r = slab_rect(rects, depth, lo + threadIdx.x, hi, sel, gx);
   const LocalBox box = chunk_box(r);
   const int area = box.w * box.h;
+  // Per-tile counts of the chunk's box from a 2D difference array: each
+  // rectangle adds +1 / -1 / -1 / +1 at its four corners of a (w + 1) x
+  // (h + 1) grid, and prefix sums along x then y give, at every tile, the
+  // number of rectangles covering it (items in done tiles are counted here
+  // but neither reserved nor filled).  Big rectangles, and every rectangle
+  // of a chunk whose box is too large, count item by item in global memory.
+  const int pw = box.w + 1;
   if (box.ok)
-    for (int t = threadIdx.x; t < area; t += blockDim.x) s_cnt[t] = 0u;
+    for (int t = threadIdx.x; t < pw * (box.h + 1); t += blockDim.x) s_cnt[t] = 0u;
   __syncthreads();
+  const bool local = box.ok && r.z > r.x && !big(r);
+  if (local) {
+    const int x0 = r.x - box.x0, x1 = r.z - box.x0, y0 = r.y - box.y0, y1 = r.w - box.y0;
+    atomicAdd(&s_cnt[y0 * pw + x0], 1u);
+    atomicAdd(&s_cnt[y0 * pw + x1], 0xffffffffu);
+    atomicAdd(&s_cnt[y1 * pw + x0], 0xffffffffu);
+    atomicAdd(&s_cnt[y1 * pw + x1], 1u);
+  }
   {
-    const unsigned lmask = __ballot_sync(kFull, box.ok && !big(r));
-    expand_items(r, [&](int src, int tx, int ty) {
+    const ushort4 rg = local ? make_ushort4(0, 0, 0, 0) : r;
+    expand_items(rg, [&](int src, int tx, int ty) {
       if (sel.skip_tile(ty * gx + tx)) return;
-      if ((lmask >> src) & 1u) atomicAdd(&s_cnt[box.idx(tx, ty)], 1u);
-      else atomicAdd(&tile_glob[ty * gx + tx], 1u);
+      atomicAdd(&tile_glob[ty * gx + tx], 1u);
     });
+  }
+  __syncthreads();
+  if (box.ok) {
+    for (int y = threadIdx.x; y < box.h; y += blockDim.x) {  // along x, one row per thread
+      uint32_t run = 0u;
+      for (int x = 0; x < box.w; ++x) { run += s_cnt[y * pw + x]; s_cnt[y * pw + x] = run; }
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < box.w; x += blockDim.x) {  // along y, one column per thread
+      uint32_t run = 0u;
+      for (int y = 0; y < box.h; ++y) { run += s_cnt[y * pw + x]; s_cnt[y * pw + x] = run; }
+    }
   }
   __syncthreads();
   // reserve this CTA's run in every tile of its box (offset inside the tile's list)
   if (box.ok) {
     uint32_t* base = run_base + (int64_t)blockIdx.x * kLocalMax;
     for (int t = threadIdx.x; t < area; t += blockDim.x) {
-      const uint32_t c = s_cnt[t];
-      base[t] = c ? atomicAdd(&tile_count[(box.y0 + t / box.w) * gx + box.x0 + t % box.w], c) : 0u;
+      const int ty = t / box.w, tx = t - ty * box.w;
+      const uint32_t c = s_cnt[ty * pw + tx];
+      const int g = (box.y0 + ty) * gx + box.x0 + tx;
+      base[t] = (c && !sel.skip_tile(g)) ? atomicAdd(&tile_count[g], c) : 0u;
     }
   }
 }

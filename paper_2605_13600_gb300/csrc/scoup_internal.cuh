@@ -107,6 +107,50 @@ __device__ __forceinline__ bool box_may_hit(const ProjRec& r, float x0, float y0
   return best >= tau - (0.01f + 1e-3f * fabsf(best));
 }
 
+// Conservative test of a whole grid of boxes at once: bit r * kCols + c is
+// set when box (c, r) -- pixels x0 + c w .. x0 + c w + w - 1 by
+// y0 + r h .. y0 + r h + h - 1 -- may hold a pixel centre with power >= tau.
+// In offsets (u, v) = (x - mx, y - my) the accepted set is the ellipse
+// E = {qa u^2 + qb u v + qc v^2 >= lvl}, with the level lvl a margin below
+// tau that covers the binary32 rounding of the per-pixel exponent (the terms
+// of the exponent reach |tau| times the ellipse's aspect ratio, so the margin
+// grows with it).  For each row of boxes (a strip va <= v <= vb) the x-extent
+// of E inside the strip is found in closed form: the right end of E's chord
+// at height v is a concave function of v whose maximum is E's rightmost point
+// (u_e, v_e), so over the strip it peaks at v = clamp(v_e, va, vb); the left
+// end, by symmetry, at clamp(-v_e, va, vb).  A strip that misses E has no
+// chord there (negative discriminant).  The extent is widened by 0.01 px.
+template <int kCols, int kRows>
+__device__ __forceinline__ uint32_t box_grid_mask(const ProjRec& r, float x0, float y0, float w, float h) {
+  constexpr uint32_t kAll = kCols * kRows >= 32 ? 0xffffffffu : ((1u << (kCols * kRows)) - 1u);
+  const float mx = r.a.x, my = r.a.y, qa = r.a.z, qb = r.a.w, qc = r.b.x, tau = r.b.z;
+  const float det = 4.0f * qa * qc - qb * qb;  // > 0 for a negative-definite exponent
+  if (!(qa < 0.0f && qc < 0.0f && det > 0.0f && tau < 0.0f)) return kAll;
+  const float aspect = 4.0f * (qa + qc) * (qa + qc) / det;  // >= the ratio of the ellipse's axes squared
+  const float lvl = tau - (0.02f + 2e-3f * fabsf(tau) + 1e-5f * fabsf(tau) * aspect);
+  const float c4 = 4.0f * qa * lvl;                           // > 0
+  const float ue = sqrtf(4.0f * qc * lvl / det);              // rightmost point of E
+  const float ve = -qb * ue / (2.0f * qc);
+  const float inv2a = 0.5f / qa;                              // < 0
+  uint32_t mask = 0u;
+#pragma unroll
+  for (int row = 0; row < kRows; ++row) {
+    const float va = y0 + (float)row * h - my - 0.01f, vb = va + (h - 1.0f) + 0.02f;
+    const float vr = fminf(fmaxf(ve, va), vb), vl = fminf(fmaxf(-ve, va), vb);
+    const float dr = fmaf(-det, vr * vr, c4), dl = fmaf(-det, vl * vl, c4);
+    if (dr < 0.0f && dl < 0.0f) continue;
+    // chord roots (-qb v -/+ sqrt(D)) / (2 qa): the right end takes -sqrt(D)
+    const float xr = mx + (-qb * vr - sqrtf(fmaxf(dr, 0.0f))) * inv2a + 0.01f;
+    const float xl = mx + (-qb * vl + sqrtf(fmaxf(dl, 0.0f))) * inv2a - 0.01f;
+#pragma unroll
+    for (int col = 0; col < kCols; ++col) {
+      const float bx0 = x0 + (float)col * w;
+      if (xr >= bx0 && xl <= bx0 + (w - 1.0f)) mask |= 1u << (row * kCols + col);
+    }
+  }
+  return mask;
+}
+
 // Region maps and code tables of one view, one per semantic level (a single
 // level for scoup_uplift; up to three for scoup_uplift_levels).
 constexpr int kMaxLevels = 3;

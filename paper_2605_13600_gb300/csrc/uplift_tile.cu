@@ -58,6 +58,7 @@ namespace scoup {
 namespace {
 
 constexpr int kThreads = 256;
+static_assert(kThreads / 32 == 8, "one 8-bit block mask per record: eight warps per tile");
 // Window of 256 keys over 1024 depth buckets: most pixels saturate within the
 // first ~200 entries of a tile (1M-Gaussian views), so ordering more per
 // window is mostly wasted; measured against 512/1024-key windows and 512/2048
@@ -69,9 +70,9 @@ constexpr int kMaxSlots = 4;
 constexpr int kMaxS = 64;  // codes of up to kMaxS entries are staged in shared memory; longer
                            // ones (dense features, Eq. 3) are read from the code table in the flush
 constexpr int kGroup = 8;
-// Records of a window are box-tested and compacted per warp in batches of
-// kCompact; the warp composites the compacted list in full groups of kGroup.
-constexpr int kCompact = 128;
+// Each warp compacts the window entries whose box mask has its bit (up to
+// kCompact at a time) and composites that list in full groups of kGroup.
+constexpr int kCompact = kWin;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr float kLog2e = 1.4426950408889634f;
 
@@ -92,6 +93,7 @@ struct TileSmem {
   float4 rec_a[kWin + 1];  // the window's projected records, loaded once per window; entry kWin is
   float4 rec_b[kWin + 1];  // a record no pixel accepts (pads the warps' lists to whole groups)
   int wlist[kThreads / 32][kCompact + kGroup];  // per warp: window entries that may reach its pixels
+  uint8_t rec_mask[kWin];  // per window entry: the warps whose pixel block it may reach
   float part[kMaxSlots][kWin];
   float part_c[kComp ? kMaxSlots : 1][kComp ? kWin : 1];
   uint32_t nz[kMaxSlots][kWin / 32];  // window entries whose partial became non-zero
@@ -287,7 +289,6 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
   const int tx = tile % cam.gx, ty = tile / cam.gx;
   constexpr int kBH = 32 / kBW, kWarpsX = kTile / kBW;
   const int bxi = tx * kTile + (warp % kWarpsX) * kBW, byi = ty * kTile + (warp / kWarpsX) * kBH;
-  const float bx0 = (float)bxi, by0 = (float)byi;
   const int px = bxi + lane % kBW;
   const int py = byi + lane / kBW;
   const bool inside = px < cam.width && py < cam.height;
@@ -528,14 +529,16 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
 
     // ---- composite the window: every warp walks it on its own ----
     // The CTA loads the window's records into shared memory once (one per
-    // thread, all loads in flight together).  Each lane then tests one of the
-    // next 32 records against the warp's pixel block (box_may_hit); the warp
-    // composites only the Gaussians that can reach one of its pixels, in
+    // thread, all loads in flight together), and the same thread marks which
+    // of the tile's eight warp blocks the record may reach (box_grid_mask).
+    // Each warp composites only the Gaussians whose mark has its bit, in
     // window order.
     for (int j = tid; j < m; j += kThreads) {
       const ProjRec pr = proj[(int)(sm.win[j] & 0xffffffffull)];
       sm.rec_a[j] = pr.a;
       sm.rec_b[j] = pr.b;
+      sm.rec_mask[j] = (uint8_t)box_grid_mask<kWarpsX, kTile / kBH>(pr, (float)(tx * kTile), (float)(ty * kTile),
+                                                                   (float)kBW, (float)kBH);
     }
     __syncthreads();
     bool warp_done = __all_sync(kFull, done);
@@ -550,13 +553,7 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
       int cnt = 0;
       for (int j0 = c0; j0 < c1; j0 += 32) {
         const int j = j0 + lane;
-        bool rel = false;
-        if (j < c1) {
-          ProjRec pr;
-          pr.a = st_a[j];
-          pr.b = st_b[j];
-          rel = box_may_hit(pr, bx0, by0, (float)kBW, (float)kBH);
-        }
+        const bool rel = j < c1 && ((sm.rec_mask[j] >> warp) & 1u);
         const unsigned rmask = __ballot_sync(kFull, rel);
         if (rel) wl[cnt + __popc(rmask & ((1u << lane) - 1u))] = j;
         cnt += __popc(rmask);
