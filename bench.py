@@ -327,7 +327,8 @@ def run_gb300(args, dist):
     # argument scale, alpha = o exp, min with 0.99, 1 - alpha, T (1 - alpha),
     # stop compare -> 15 operations
     ops = 15.0 * evaluated_per_launch
-    alu_peak = 152 * 128 * pk["sm_max_mhz"] * 1e6  # FP32 lanes x max SM clock
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = n_sms * 128 * pk["sm_max_mhz"] * 1e6  # FP32 lanes x max SM clock
     achieved = ops / per_launch_s
     npx = up.cams[0].width * up.cams[0].height
     # algorithmic HBM bytes of one view: region map + one FP32 read-modify-write per
@@ -343,7 +344,8 @@ def run_gb300(args, dist):
                              "peak_gbs": pk["hbm_gbs"],
                              "frac": bytes_launch / per_launch_s / 1e9 / pk["hbm_gbs"]},
                 "ops_per_launch": ops, "op_count": "15 FP32 ops per evaluated pair (exp on the SFU not counted)",
-                "peak_source": pk["source"] + " (HBM); FP32 lanes x max SM clock (ALU)"}
+                "peak_source": pk["source"] + f" (HBM); FP32 lanes x max SM clock x {n_sms} SMs (ALU)"}
+    roofline["step"] = step_roofline(gb, up, wl, st0, t_step, pk, alu_peak)
 
     # end to end through the public API with host buffers
     e2e = None
@@ -579,6 +581,70 @@ def render_decode_leg(args, dist, wl, up, dev, pk):
     }
 
 
+def red_ceiling(gb, log2_n: int = 29, count: int = 1 << 28, reps: int = 3):
+    """Measured FP32 atomic-update throughput (updates/s): `count` reductions
+    to pseudo-random elements of a 2^log2_n-float buffer (2 GB, far larger
+    than L2), best of `reps` runs timed with CUDA events."""
+    import torch
+    buf = torch.zeros(1 << log2_n, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    gb.scoup_selftest_red_throughput(buf, count // 4, seed=7)  # warm-up
+    best = None
+    for r in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gb.scoup_selftest_red_throughput(buf, count, seed=11 + r)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        best = t if best is None else min(best, t)
+    del buf
+    torch.cuda.empty_cache()
+    return count / best
+
+
+def step_roofline(gb, up, wl, st0, t_step, pk, alu_peak):
+    """The uplift step against its three ceilings (HBM bytes, atomic updates,
+    FP32 ALU), with the method's algorithmic work:
+      bytes   = sum_v (44 N + 4 H W + 8 U_v) + 4 N C + 8 N K
+                (parameters read per view, region map, one read-modify-write
+                per distinct (Gaussian, atom) updated in view v, the final
+                accumulator read and the Top-K write);
+      atomics = sum_v U_v (lower bound; the issued count and s x contributions
+                of Algorithm 1 are reported beside it);
+      ALU     = 15 FP32 operations per evaluated (Gaussian, pixel) pair.
+    U_v is counted exactly: view v alone is uplifted into a cleared
+    accumulator and its non-zero entries are counted."""
+    import torch
+    n, C, K, s = wl.scene.n, wl.C, wl.K, wl.s
+    V = len(up.cams)
+    U = []
+    for v in range(V):
+        up.run(stats=False, views=[v], topk=False)
+        U.append(int(torch.count_nonzero(up.accum).item()))
+    up.run(stats=False)  # the later legs start from the full step's accumulator
+    pix = sum(c.width * c.height for c in up.cams)
+    sum_u = float(sum(U))
+    bytes_step = 44.0 * n * V + 4.0 * pix + 8.0 * sum_u + 4.0 * n * C + 8.0 * n * K
+    red = red_ceiling(gb)
+    t_hbm = bytes_step / (pk["hbm_gbs"] * 1e9)
+    t_atom = sum_u / red
+    t_alu = 15.0 * st0["evaluated_pairs"] / alu_peak
+    t_roof = max(t_hbm, t_atom)
+    ceilings = {"hbm": t_hbm, "atomic": t_atom, "alu": t_alu}
+    return {"ms_per_step": t_step * 1e3,
+            "bytes_per_step": bytes_step, "hbm_ms": t_hbm * 1e3, "hbm_frac": t_hbm / t_step,
+            "atomics_lower_bound": sum_u, "atomics_issued": float(st0["atomics"]),
+            "atomics_alg1_literal": float(s) * st0["contributions"],
+            "red_peak_per_s": red, "red_peak_source": "measured: scoup_selftest_red_throughput, 2^28 FP32 "
+                                                      "reductions over a 2 GB buffer, best of 3",
+            "atomic_ms": t_atom * 1e3, "atomic_frac": t_atom / t_step,
+            "alu_ms": t_alu * 1e3, "alu_frac": t_alu / t_step,
+            "roofline_ms": t_roof * 1e3, "frac": t_roof / t_step,
+            "binding": max(ceilings, key=ceilings.get),
+            "formula": "t_roof = max(bytes / HBM, sum_v U_v / RED peak); ALU (15 ops per evaluated pair) beside it"}
+
+
 def entropy_leg(args, up, pk):
     """Top-K with the coefficient entropy fused in, and the entropy filter,
     at full size on the accumulator the uplift just produced (1M x 256)."""
@@ -630,7 +696,7 @@ def entropy_leg(args, up, pk):
                                   "frac": (nbytes + 4.0 * n) / t_ent / 1e9 / pk["hbm_gbs"],
                                   "algorithmic_bytes": nbytes + 4.0 * n},
         "entropy_filter_ms": t_filter * 1e3, "entropy_filter_keep": n // 2, "entropy_filter_kept": kept,
-        "entropy_filter_form": "8 radix-select passes over the entropies (host reads each digit histogram)",
+        "entropy_filter_form": "8 radix-select passes over the entropies, each digit picked on the device (no host round-trip)",
     }
 
 

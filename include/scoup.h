@@ -73,6 +73,8 @@ typedef struct scoup_stats {
   int64_t listed;           /* (Gaussian, tile) pairs kept after the exact alpha-reach test */
   int32_t status;           /* SCOUP_OK or the first device-side error */
   int32_t max_dups_view;    /* largest per-view duplicate count seen */
+  int64_t split_windows;    /* ordering windows cut out of one depth bucket that held more
+                               keys than a window (ties in depth, fronto-parallel sheets) */
 } scoup_stats;
 
 const char* scoup_version(void);
@@ -300,9 +302,11 @@ int scoup_topk_entropy(const float* accum, const float* comp, int64_t n, int32_t
  *  entropy    DEVICE float32 [n] (e.g. from scoup_topk_entropy).
  *  topk_idx, topk_val  DEVICE [n, K], modified in place, or both NULL.
  *  keep_mask  DEVICE uint8 [n] (1 kept, 0 removed) or NULL.
- *  workspace  DEVICE, >= scoup_entropy_filter_workspace_size() bytes.
- * Exact selection in 8 histogram passes whose digits are read back on the
- * host: the call synchronises `stream`. */
+ *  workspace  DEVICE, >= scoup_entropy_filter_workspace_size() bytes,
+ *             16-byte aligned (overwritten).
+ * Exact selection in 8 histogram passes; each pass's last CTA picks the next
+ * digit on the device, so the call is asynchronous (enqueued on `stream`, no
+ * synchronisation) and can be captured in a CUDA graph. */
 size_t scoup_entropy_filter_workspace_size(void);
 int scoup_entropy_filter(const float* entropy, int64_t n, int64_t keep, int32_t K, int32_t* topk_idx,
                          float* topk_val, uint8_t* keep_mask, void* workspace, size_t ws_bytes, void* stream);

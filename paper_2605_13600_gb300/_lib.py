@@ -45,7 +45,7 @@ class Stats(ct.Structure):
                 ("evaluated_pairs", ct.c_int64), ("contributions", ct.c_int64),
                 ("flushes", ct.c_int64), ("atomics", ct.c_int64), ("listed", ct.c_int64),
                 ("status", ct.c_int32),
-                ("max_dups_view", ct.c_int32)]
+                ("max_dups_view", ct.c_int32), ("split_windows", ct.c_int64)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -127,6 +127,7 @@ PROTOS = {
     "scoup_plan_info_get": (ct.c_int, [P, ct.POINTER(PlanInfo)]),
     "scoup_plan_destroy": (ct.c_int, [P]),
     "scoup_selftest_gemm_timeout": (ct.c_int, [P, SZ, P]),
+    "scoup_selftest_red_throughput": (ct.c_int, [P, ct.c_int32, ct.c_int64, ct.c_uint32, P]),
     "scoup_profile_enable": (ct.c_int, [I32]),
     "scoup_profile_read": (ct.c_int, [P, P, I32]),
     "scoup_launch_count": (I64, []),

@@ -260,6 +260,7 @@ void read_header(const WsHeader& h, scoup_stats* st) {
   st->atomics = (int64_t)h.atomics;
   st->listed = (int64_t)h.listed;
   st->max_dups_view = h.max_dups_view;
+  st->split_windows = (int64_t)h.split_windows;
   st->status = SCOUP_OK;
   if (h.status & kStatCapacity) st->status = SCOUP_ERR_CAPACITY;
   else if (h.status & kStatDeviceCheck) st->status = SCOUP_ERR_DEVICE_CHECK;
@@ -976,7 +977,9 @@ int scoup_topk_entropy(const float* accum, const float* comp, int64_t n, int32_t
   return e == cudaSuccess ? SCOUP_OK : cuda_fail(e, "top-k + entropy");
 }
 
-size_t scoup_entropy_filter_workspace_size(void) { return 1024; }
+size_t scoup_entropy_filter_workspace_size(void) {
+  return entropy_filter_state_bytes() < 1024 ? 1024 : entropy_filter_state_bytes();
+}
 
 int scoup_entropy_filter(const float* entropy, int64_t n, int64_t keep, int32_t K, int32_t* topk_idx,
                          float* topk_val, uint8_t* keep_mask, void* workspace, size_t ws_bytes, void* stream) {
@@ -989,8 +992,8 @@ int scoup_entropy_filter(const float* entropy, int64_t n, int64_t keep, int32_t 
   if (!workspace || ws_bytes < scoup_entropy_filter_workspace_size())
     return fail(SCOUP_ERR_OOM, "workspace too small: need %zu bytes", scoup_entropy_filter_workspace_size());
   if (n == 0) return SCOUP_OK;
-  return entropy_filter_run(entropy, n, keep, K, topk_idx, topk_val, keep_mask, (uint32_t*)workspace,
-                            (cudaStream_t)stream);
+  if ((uintptr_t)workspace & 15u) return fail(SCOUP_ERR_INVALID_ARG, "workspace must be 16-byte aligned");
+  return entropy_filter_run(entropy, n, keep, K, topk_idx, topk_val, keep_mask, workspace, (cudaStream_t)stream);
 }
 
 int scoup_relevancy(const float* sim, int64_t P, int32_t ncols, int32_t n_canon, float alpha, float* R,

@@ -5,8 +5,10 @@
 // Gaussians of lowest coefficient entropy, ties to the lower index.  Every
 // Gaussian gets the unique 64-bit key (order-preserving bits of H_i) << 32 | i;
 // the key of rank keep - 1 is found exactly by an 8-pass radix select (one
-// 256-bin histogram per pass, the digit chosen on the host), then one pass
-// marks the kept rows and clears the Top-K rows of the others to (-1, 0).
+// 256-bin histogram per pass; the last CTA of each pass picks the digit and
+// updates the selection state in the workspace, so nothing returns to the
+// host), then one pass marks the kept rows and clears the Top-K rows of the
+// others to (-1, 0).
 //
 // Relevancy (App. B, Eq. 9): R = min_k e^{a s_q} / (e^{a s_q} + e^{a s_k})
 // = min_k 1 / (1 + e^{a (s_k - s_q)}) from the similarity matrix, whose first
@@ -24,9 +26,24 @@ __device__ __forceinline__ unsigned long long entropy_key(float h, int64_t i) {
   return ((unsigned long long)u << 32) | (uint32_t)i;
 }
 
-__global__ void key_hist_kernel(const float* __restrict__ H, int64_t n, unsigned long long prefix,
-                                unsigned long long pmask, int shift, uint32_t* __restrict__ hist) {
+// Radix-select state, in the caller's workspace (cleared before the first pass).
+struct SelectState {
+  unsigned long long prefix;  // digits chosen so far
+  unsigned long long pmask;   // their bits
+  long long rank;             // rank of the wanted key among the keys matching the prefix
+  unsigned int done;          // CTAs finished in the current pass
+  unsigned int pad;
+  uint32_t hist[256];
+};
+
+// One pass: histogram of digit `shift` over the keys that match the prefix;
+// the last CTA turns it into the next digit (the bin holding `rank`), clears
+// the histogram and the CTA counter for the next pass.
+__global__ void __launch_bounds__(256) select_pass_kernel(const float* __restrict__ H, int64_t n, int shift,
+                                                          long long rank0, SelectState* __restrict__ st) {
   __shared__ uint32_t sh[256];
+  __shared__ bool s_last;
+  const unsigned long long prefix = st->prefix, pmask = st->pmask;
   for (int b = threadIdx.x; b < 256; b += blockDim.x) sh[b] = 0u;
   __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -35,12 +52,46 @@ __global__ void key_hist_kernel(const float* __restrict__ H, int64_t n, unsigned
   }
   __syncthreads();
   for (int b = threadIdx.x; b < 256; b += blockDim.x)
-    if (sh[b]) atomicAdd(&hist[b], sh[b]);
+    if (sh[b]) atomicAdd(&st->hist[b], sh[b]);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&st->done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x < 32) {
+    // bins 8 lane .. 8 lane + 7; inclusive scan of their sums across the warp
+    const int lane = threadIdx.x;
+    const long long rank = shift == 56 ? rank0 : st->rank;
+    uint32_t c[8], sum = 0;
+    for (int d = 0; d < 8; ++d) { c[d] = __ldcg(&st->hist[lane * 8 + d]); sum += c[d]; }
+    unsigned long long incl = sum;
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += y;
+    }
+    const unsigned long long excl = incl - sum;
+    if ((unsigned long long)rank >= excl && (unsigned long long)rank < incl) {
+      unsigned long long cum = excl;
+      for (int d = 0; d < 8; ++d) {
+        if ((unsigned long long)rank < cum + c[d]) {
+          st->prefix = prefix | ((unsigned long long)(lane * 8 + d) << shift);
+          st->pmask = pmask | (0xffull << shift);
+          st->rank = rank - (long long)cum;
+          break;
+        }
+        cum += c[d];
+      }
+    }
+    for (int d = 0; d < 8; ++d) st->hist[lane * 8 + d] = 0u;
+    if (lane == 0) st->done = 0u;
+  }
 }
 
-__global__ void filter_kernel(const float* __restrict__ H, int64_t n, unsigned long long thr, int keep_none,
-                              int K, int32_t* __restrict__ idx, float* __restrict__ val,
-                              uint8_t* __restrict__ mask) {
+__global__ void filter_kernel(const float* __restrict__ H, int64_t n, const SelectState* __restrict__ sel,
+                              int keep_all, int keep_none, int K, int32_t* __restrict__ idx,
+                              float* __restrict__ val, uint8_t* __restrict__ mask) {
+  const unsigned long long thr = keep_all ? ~0ull : sel->prefix;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const bool keep = !keep_none && entropy_key(H[i], i) <= thr;
     if (mask) mask[i] = keep ? 1 : 0;
@@ -103,30 +154,23 @@ int grid_for(int64_t n) {
 
 }  // namespace
 
+size_t entropy_filter_state_bytes() { return sizeof(SelectState); }
+
 int entropy_filter_run(const float* H, int64_t n, int64_t keep, int K, int32_t* idx, float* val, uint8_t* mask,
-                       uint32_t* hist, cudaStream_t st) {
+                       void* workspace, cudaStream_t st) {
   cudaError_t e;
-  unsigned long long thr = ~0ull;
+  SelectState* sel = reinterpret_cast<SelectState*>(workspace);
   const int keep_none = keep <= 0;
-  if (keep > 0 && keep < n) {
-    unsigned long long prefix = 0ull, pmask = 0ull;
-    int64_t rank = keep - 1;
+  const int keep_all = keep >= n;
+  if (!keep_none && !keep_all) {
+    if ((e = cudaMemsetAsync(sel, 0, sizeof(SelectState), st)) != cudaSuccess)
+      return set_error(SCOUP_ERR_CUDA, cudaGetErrorString(e));
     for (int shift = 56; shift >= 0; shift -= 8) {
-      if ((e = cudaMemsetAsync(hist, 0, 256 * sizeof(uint32_t), st)) != cudaSuccess) return set_error(SCOUP_ERR_CUDA, cudaGetErrorString(e));
-      key_hist_kernel<<<grid_for(n), 256, 0, st>>>(H, n, prefix, pmask, shift, hist);
+      select_pass_kernel<<<grid_for(n), 256, 0, st>>>(H, n, shift, (long long)(keep - 1), sel);
       g_launches += 1;
-      uint32_t h[256];
-      if ((e = cudaMemcpyAsync(h, hist, sizeof(h), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-          (e = cudaStreamSynchronize(st)) != cudaSuccess)
-        return set_error(SCOUP_ERR_CUDA, cudaGetErrorString(e));
-      int d = 0;
-      while (d < 255 && rank >= (int64_t)h[d]) rank -= h[d++];
-      prefix |= (unsigned long long)d << shift;
-      pmask |= 0xffull << shift;
     }
-    thr = prefix;
   }
-  filter_kernel<<<grid_for(n), 256, 0, st>>>(H, n, thr, keep_none, K, idx, val, mask);
+  filter_kernel<<<grid_for(n), 256, 0, st>>>(H, n, sel, keep_all, keep_none, K, idx, val, mask);
   g_launches += 1;
   if ((e = cudaGetLastError()) != cudaSuccess) return set_error(SCOUP_ERR_CUDA, cudaGetErrorString(e));
   return SCOUP_OK;

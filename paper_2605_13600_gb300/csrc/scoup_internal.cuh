@@ -53,7 +53,8 @@ struct WsHeader {
   unsigned long long listed;
   uint32_t slab_lo[4][kMaxSlabs];  // [slot][s]: smallest depth bits of slab s (slab 0 starts at 0)
   uint32_t pp_blocks[4];           // projection CTAs finished in this slot's view (last one sets slab_lo)
-  unsigned long long reserved[3];
+  unsigned long long split_windows;  // windows cut out of a depth bucket holding more than a window
+  unsigned long long reserved[2];
 };
 static_assert(sizeof(WsHeader) == 256, "header size");
 
@@ -303,8 +304,9 @@ cudaError_t launch_row_norm2_f32(const float* X, int64_t R, int D, float* out, c
 // ld: row stride of accum / comp in floats (C for a plain [n, C] accumulator).
 cudaError_t launch_topk(const float* accum, const float* comp, int64_t n, int C, int K, int32_t* idx, float* val,
                         float* entropy, cudaStream_t st, int64_t ld = 0);
+size_t entropy_filter_state_bytes();
 int entropy_filter_run(const float* H, int64_t n, int64_t keep, int K, int32_t* idx, float* val, uint8_t* mask,
-                       uint32_t* hist, cudaStream_t st);
+                       void* workspace, cudaStream_t st);
 cudaError_t launch_relevancy(const float* sim, int64_t P, int ncols, int n_canon, float alpha, float* R,
                              cudaStream_t st);
 cudaError_t launch_code_topk(const int32_t* ci, const float* cv, int64_t R, int s, int K,

@@ -258,6 +258,7 @@ __device__ int order_next_window(S& sm, const unsigned long long* __restrict__ k
     }
   } else {
     if (!st.in_split) { st.in_split = true; st.split_first = true; st.consumed = 0; }
+    if (tid == 0) atomicAdd(&hdr->split_windows, 1ull);
     const int left = total_b0 - st.consumed;
     unsigned long long hi_key = ~0ull;
     if (left > kWin) hi_key = order_select(sm, keys, n, bk, st.b0, st.split_last, st.split_first, kWin - 1);

@@ -488,6 +488,7 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
     } else {
       // ---- oversize bucket b0: the kWin smallest of its remaining keys ----
       if (!in_split) { in_split = true; split_first = true; consumed = 0; }
+      if (tid == 0) atomicAdd(&hdr->split_windows, 1ull);
       const int left = total_b0 - consumed;
       unsigned long long hi_key = ~0ull;
       if (left > kWin) hi_key = select_in_bucket(sm, tkeys, n, bk, b0, split_last, split_first, kWin - 1);

@@ -417,9 +417,14 @@ def scoup_topk_entropy(accum, K: int, topk_idx, topk_val, entropy, comp=None, st
                                     _ptr(entropy), _stream(stream)))
 
 
+def scoup_entropy_filter_workspace_size() -> int:
+    return int(load().scoup_entropy_filter_workspace_size())
+
+
 def scoup_entropy_filter(entropy, keep: int, topk_idx=None, topk_val=None, keep_mask=None, workspace=None,
                          stream=None):
-    """Keep the `keep` lowest-entropy Gaussians; clear the others' Top-K rows (synchronises)."""
+    """Keep the `keep` lowest-entropy Gaussians; clear the others' Top-K rows
+    (asynchronous on `stream`; capturable in a CUDA graph with a given workspace)."""
     import torch
     _need(entropy, torch.float32, "entropy")
     _need(topk_idx, torch.int32, "topk_idx")
@@ -428,6 +433,8 @@ def scoup_entropy_filter(entropy, keep: int, topk_idx=None, topk_val=None, keep_
     if workspace is None:
         workspace = torch.empty(int(load().scoup_entropy_filter_workspace_size()), dtype=torch.uint8,
                                 device=entropy.device)
+        if stream is not None and hasattr(stream, "cuda_stream"):
+            workspace.record_stream(stream)  # still in use by the kernels after this call returns
     K = int(topk_idx.shape[1]) if topk_idx is not None else 0
     check(load().scoup_entropy_filter(_ptr(entropy), entropy.numel(), int(keep), K, _ptr(topk_idx),
                                       _ptr(topk_val), _ptr(keep_mask), _ptr(workspace), workspace.numel(),
@@ -443,6 +450,18 @@ def scoup_relevancy(sim, n_canon: int, R, alpha: float = 10.0, stream=None) -> N
     if tuple(R.shape) != (P, ncols - n_canon):
         raise ValueError("R must be [P, ncols - n_canon]")
     check(load().scoup_relevancy(_ptr(sim), P, ncols, int(n_canon), float(alpha), _ptr(R), _stream(stream)))
+
+
+def scoup_selftest_red_throughput(buf, count: int, seed: int = 1, stream=None) -> None:
+    """Enqueues `count` FP32 atomic additions to pseudo-random elements of the
+    CUDA float32 tensor buf (whose size must be a power of two, >= 1024)."""
+    import torch
+    _need(buf, torch.float32, "buf")
+    n = buf.numel()
+    if n < 1024 or n & (n - 1) or n > (1 << 31):
+        raise ValueError("buf must hold a power of two of floats, 2^10 .. 2^31")
+    check(load().scoup_selftest_red_throughput(_ptr(buf), n.bit_length() - 1, int(count), int(seed) & 0xffffffff,
+                                               _stream(stream)))
 
 
 def scoup_selftest_gemm_timeout(stream=None) -> tuple:
@@ -712,6 +731,6 @@ __all__ = ["ScoupError", "SCOUP_ACCUM_CONTINUE", "SCOUP_ACCUM_COMPENSATED", "sce
            "scoup_render", "scoup_render_backward", "Render", "Uplift",
            "scoup_decode_workspace_size", "scoup_decode", "scoup_similarity_workspace_size",
            "scoup_similarity", "scoup_decode_fp32", "scoup_similarity_fp32", "BatchedUplift",
-           "SCOUP_BATCH_EAGER", "LevelUplift", "scoup_selftest_gemm_timeout", "scoup_topk_entropy", "scoup_entropy_filter", "scoup_relevancy",
+           "SCOUP_BATCH_EAGER", "LevelUplift", "scoup_selftest_gemm_timeout", "scoup_selftest_red_throughput", "scoup_topk_entropy", "scoup_entropy_filter", "scoup_entropy_filter_workspace_size", "scoup_relevancy",
            "scoup_render_decode_workspace_size", "scoup_render_decode_fused",
            "scoup_uplift_host_maps_workspace_size", "scoup_uplift_host_maps"]

@@ -145,3 +145,11 @@ def test_relevancy_rejects_bad_alpha(lib):
         assert L.scoup_relevancy(fake, 10, 8, 2, a, fake, None) != 0
         assert "alpha" in L.scoup_last_error().decode()
     assert L.scoup_relevancy(fake, 10, 2, 2, 10.0, fake, None) != 0  # no query column
+
+
+def test_red_throughput_rejects_bad_arguments(lib):
+    f = lib.load().scoup_selftest_red_throughput
+    assert f(None, 20, 10, 1, None) == lib.SCOUP_ERR_INVALID_ARG
+    assert f(ct.c_void_p(256), 9, 10, 1, None) == lib.SCOUP_ERR_INVALID_ARG
+    assert f(ct.c_void_p(256), 32, 10, 1, None) == lib.SCOUP_ERR_INVALID_ARG
+    assert f(ct.c_void_p(256), 20, -1, 1, None) == lib.SCOUP_ERR_INVALID_ARG

@@ -85,6 +85,40 @@ def test_entropy_filter_exact(gb, oracle_lib, n):
         assert (idx.cpu().numpy()[kept] >= 0).all()
 
 
+def test_entropy_filter_in_a_cuda_graph(gb, oracle_lib):
+    """The filter runs without host round-trips: captured once in a CUDA graph
+    and replayed on new entropies, it keeps exactly the oracle's Gaussians."""
+    import torch
+    n, K, keep = 70_000, 4, 31_337
+    rng = np.random.default_rng(71)
+    dev = torch.device("cuda:0")
+    Hd = torch.empty(n, dtype=torch.float32, device=dev)
+    idx = torch.empty((n, K), dtype=torch.int32, device=dev)
+    val = torch.empty((n, K), dtype=torch.float32, device=dev)
+    mask = torch.empty(n, dtype=torch.uint8, device=dev)
+    ws = torch.empty(int(gb.scoup_entropy_filter_workspace_size()), dtype=torch.uint8, device=dev)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):  # warm-up outside the capture
+        gb.scoup_entropy_filter(Hd.fill_(1.0), keep, idx, val, mask, workspace=ws)
+    torch.cuda.current_stream().wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        gb.scoup_entropy_filter(Hd, keep, idx, val, mask, workspace=ws)
+    for trial in range(2):
+        H32 = np.round(rng.random(n) * 3.0, 2).astype(np.float32)  # many ties
+        Hd.copy_(torch.from_numpy(H32))
+        idx.copy_(torch.arange(n * K, dtype=torch.int32).reshape(n, K))
+        val.fill_(1.0)
+        g.replay()
+        torch.cuda.synchronize()
+        want = oracle_lib.entropy_filter(H32.astype(np.float64), keep)
+        np.testing.assert_array_equal(mask.cpu().numpy(), want)
+        kept = want.astype(bool)
+        assert kept.sum() == keep
+        assert (idx.cpu().numpy()[~kept] == -1).all() and (idx.cpu().numpy()[kept] >= 0).all()
+
+
 def test_relevancy_matches_oracle(gb, oracle_lib):
     import torch
     rng = np.random.default_rng(9)

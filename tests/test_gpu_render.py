@@ -301,3 +301,20 @@ def test_cfg4_full_size_sampled_pixels(gb, oracle_lib):
         assert (np.abs(Wg[k] - wo) <= tol).all(), (pts[k], float(np.max(np.abs(Wg[k] - wo) - tol)))
         assert abs(Tg[k] - To) <= 1e-5 + 1e-4 * To
     assert flips <= 2
+
+
+@pytest.mark.parametrize("kernel", ["tensor", "simt"])
+def test_render_equal_depth_sheet(gb, oracle_lib, monkeypatch, kernel):
+    """The fronto-parallel sheet of the uplift tests (every Gaussian at one
+    depth): both render kernels cut their windows out of one oversize depth
+    bucket and still composite in the oracle's (depth, index) order."""
+    from test_gpu_uplift import _sheet_workload
+    if kernel == "simt":
+        monkeypatch.setenv("SCOUP_RENDER_SIMT", "1")
+    wl = _sheet_workload()
+    rng = np.random.default_rng(62)
+    idx, val = synth.sparse_topk_codes(rng, wl.scene.n, 32, 4)
+    Wg, Tg, lastg, st, Wo, To, risk, cnt = _render_pair(gb, oracle_lib, wl.scene, idx, val, 32, wl.cams[0])
+    check_render(Wg, Tg, Wo, To, risk)
+    assert st["split_windows"] > 0, st
+    assert abs(st["contributions"] - cnt["contributions"]) <= 2 * risk.sum()

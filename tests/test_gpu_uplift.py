@@ -179,17 +179,53 @@ def test_topk_kernel_against_oracle(gb, oracle_lib):
         np.testing.assert_allclose(tv.cpu().numpy(), ov, rtol=2e-6, atol=1e-7)
 
 
+def _cfg2_rows(wl, rng):
+    """256 rows of the 1M-Gaussian workload: 128 seeded random Gaussians, 64
+    whose view-0 means fall in the 16 tiles holding the most means (the longest
+    tile lists), 64 in view-0 tiles with more than 4 regions (the pixels whose
+    regions get no slot and scatter directly).  Chosen from the inputs alone."""
+    import torch
+    cam = wl.cams[0]
+    vm = np.asarray(cam.viewmat, np.float64).reshape(3, 4)
+    t = wl.scene.means.astype(np.float64) @ vm[:, :3].T + vm[:, 3]
+    vis = t[:, 2] > 0.2
+    mx = cam.fx * t[:, 0] / np.where(vis, t[:, 2], 1.0) + cam.cx - 0.5
+    my = cam.fy * t[:, 1] / np.where(vis, t[:, 2], 1.0) + cam.cy - 0.5
+    gx, gy = (cam.width + 15) // 16, (cam.height + 15) // 16
+    inside = vis & (mx >= 0) & (mx < cam.width) & (my >= 0) & (my < cam.height)
+    tile = np.where(inside, (my // 16).astype(np.int64) * gx + (mx // 16).astype(np.int64), -1)
+    counts = np.bincount(tile[tile >= 0], minlength=gx * gy)
+    dense = np.argsort(-counts)[:16]
+    m = torch.as_tensor(wl.region_maps[:cam.width * cam.height]).reshape(cam.height, cam.width).cpu()
+    pad = torch.full((gy * 16, gx * 16), -2, dtype=m.dtype)
+    pad[:cam.height, :cam.width] = m
+    blocks = pad.reshape(gy, 16, gx, 16).permute(0, 2, 1, 3).reshape(gx * gy, 256)
+    srt = torch.sort(blocks, dim=1).values
+    distinct = ((srt[:, 1:] != srt[:, :-1]) & (srt[:, 1:] >= 0)).sum(1) + (srt[:, 0] >= 0).long()
+    many = np.nonzero(distinct.numpy() > 4)[0]
+    picks = [rng.choice(wl.scene.n, 128, replace=False)]
+    for t_ in dense:
+        cand = np.nonzero(tile == t_)[0]
+        picks.append(rng.choice(cand, min(4, len(cand)), replace=False))
+    cand = np.nonzero(np.isin(tile, many))[0]
+    assert len(many) > 0 and len(cand) >= 64
+    picks.append(rng.choice(cand, 64, replace=False))
+    return np.unique(np.concatenate(picks))
+
+
 @pytest.mark.slow
 def test_cfg2_full_size_sampled_rows(gb, oracle_lib):
     """Full 1M-Gaussian x 200-view x 988x731 uplift in the benchmark's launch
-    configuration; rows of 16 seeded random Gaussians checked against the oracle."""
+    configuration; 256 rows (random, from the densest tiles and from tiles of
+    more than 4 regions) checked against the oracle over all 200 views."""
     import torch
     wl = synth.uplift_cfg2(device="cuda")
     up = gb.Uplift(wl)
     st = up.run()
     assert st["status"] == 0 and st["contributions"] > 1e9
     acc_g = up.accum
-    rows = np.sort(np.random.default_rng(0).choice(wl.scene.n, 16, replace=False))
+    rows = _cfg2_rows(wl, np.random.default_rng(0))
+    assert len(rows) >= 250
     acc, risk, cnt = oracle_lib.uplift(wl, rows=rows)
     ga = acc_g[torch.as_tensor(rows, device="cuda")].cpu().numpy()
     info = check_accum(ga, acc, risk)
@@ -237,3 +273,31 @@ def test_host_region_maps_ragged_views(gb, oracle_lib):
     info = check_accum(up.accum.cpu().numpy(), acc, risk)
     assert info["n_bad"] == 0, info
     assert abs(st["contributions"] - cnt["contributions"]) <= 2 * cnt["at_risk"]
+
+
+def _sheet_workload(n=1200, seed=61, opacity=0.05):
+    """A fronto-parallel sheet: every Gaussian at exactly the same camera depth
+    (3.0), spread over a few tiles around the image centre, so each of those
+    tiles holds hundreds of keys in one depth bucket and the front-to-back
+    order rests on the index tie-break alone."""
+    from conftest import axis_camera, make_scene
+    rng = np.random.default_rng(seed)
+    means = np.zeros((n, 3))
+    means[:, :2] = rng.uniform(-0.8, 0.8, size=(n, 2))
+    scales = np.full((n, 3), 0.05)
+    q = rng.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    scene = make_scene(means, scales, q, np.full(n, opacity))
+    cam = axis_camera(width=64, height=48, f=50.0, z=3.0)
+    maps, offs, rpv, R_tot = synth.scenes._pack_maps(synth.scenes._draw_seeds(rng, [cam], [5]), [cam], "cpu")
+    ci, cv = synth.region_codes(rng, R_tot, 16, 3)
+    return synth.UpliftWorkload("sheet", scene, [cam], maps, offs, ci, cv, 16, 3, 3, rpv)
+
+
+def test_equal_depth_sheet_splits_buckets(gb, oracle_lib):
+    """Hundreds of keys per tile at one depth: the ordering cuts windows out of
+    a single oversize depth bucket (radix select on the keys, index
+    tie-break); the result still matches the oracle's (depth, index) order."""
+    wl = _sheet_workload()
+    up, st, *_ = _parity(gb, oracle_lib, wl, "sheet")
+    assert st["split_windows"] > 0, st
