@@ -538,6 +538,24 @@ def render_decode_leg(args, dist, wl, up, dev, pk):
     torch.cuda.synchronize()
     t_rel = ev0.elapsed_time(ev1) / 1e3 / 10
     rel_bytes = 4.0 * P * Q + 4.0 * P * (Q - 4)
+    # similarity + relevancy as two calls vs relevancy in the similarity GEMM's epilogue
+    rws = gb.scoup_similarity_relevancy(feats, text, 4, Rel, feat_norm2=n2)
+
+    def time_reps(fn, reps=10):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(reps):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / 1e3 / reps
+
+    t_two = time_reps(lambda: (gb.scoup_similarity(feats, text, sim, feat_norm2=n2, workspace=sws),
+                               gb.scoup_relevancy(sim, 4, Rel)))
+    t_epi = time_reps(lambda: gb.scoup_similarity_relevancy(feats, text, 4, Rel, feat_norm2=n2, workspace=rws))
+    epi_bytes = 2.0 * P * D + 4.0 * P * (Q - 4)  # bf16 features in, relevancy out
 
     # the decode GEMM alone: bf16 codes in, bf16 features out (one launch + a 256x512 transpose)
     codes_bf16 = out[0].view(P, wl.C)
@@ -563,7 +581,13 @@ def render_decode_leg(args, dist, wl, up, dev, pk):
         "ms_per_view": t * 1e3 / len(cams), "phase_ms_per_view": phase_ms,
         "relevancy": {"ms_per_view": t_rel * 1e3, "queries": Q - 4, "canonical": 4, "bound": "hbm",
                       "achieved": rel_bytes / t_rel / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                      "frac": rel_bytes / t_rel / 1e9 / pk["hbm_gbs"]},
+                      "frac": rel_bytes / t_rel / 1e9 / pk["hbm_gbs"],
+                      "similarity_then_relevancy_ms": t_two * 1e3,
+                      "epilogue_form": {"call": "scoup_similarity_relevancy", "ms_per_view": t_epi * 1e3,
+                                        "bound": "hbm", "achieved": epi_bytes / t_epi / 1e9,
+                                        "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                        "frac": epi_bytes / t_epi / 1e9 / pk["hbm_gbs"],
+                                        "speedup_vs_two_calls": t_two / t_epi}},
         "fused_call": {"form": "scoup_render_decode_fused + scoup_similarity",
                        "value": len(cams) * P / t_fused / 1e6, "unit": "MPix/s",
                        "ms_per_view": t_fused * 1e3 / len(cams)},
@@ -738,59 +762,89 @@ def dense_leg(args, dist, wl, up, dev):
 
 
 def backward_leg(args, dist, dev):
-    """Secondary measurement: the differentiable sparse render (500k Gaussians,
-    800x600 views, K = 8 of C = 256): per view the forward render and the
-    hand-written backward to the Top-K values and opacities, for a seeded
-    upstream gradient dL/dWhat.  MPix/s of forward + backward."""
+    """Secondary measurement: the differentiable sparse render of BASELINE
+    configuration 5 (500k Gaussians, 32 views at 800x600, K = 8 of C = 256,
+    a 256 x 512 codebook) with its own uplift: the scene's region codes are
+    uplifted over its 32 views (scoup_uplift, outside the timed region), and
+    per view the whole loss chain runs in the library -- render (Eq. 7) ->
+    bf16 decode (Eq. 8) -> L2 loss against the decoded region codes and its
+    gradient -> dL/dWhat = dL/dF C^T on the tensor cores -> render backward to
+    the Top-K values and opacities.  MPix/s of the chain."""
     import torch
 
     import synth
     import paper_2605_13600_gb300 as gb
 
-    rw = synth.render_cfg5()
-    cams = rw.cams[:max(1, args.backward_views)]
-    ren = gb.Render(rw.scene, rw.topk_idx, rw.topk_val, rw.C, cams, device=str(dev))
+    wl, codebook = synth.uplift_cfg5(device=str(dev))
+    up = gb.Uplift(wl, device=str(dev))
+    st = up.run(stats=True)
+    if st["status"] != 0:
+        raise RuntimeError(f"cfg5 uplift status {st['status']}")
+    cams = wl.cams[:max(1, args.backward_views)]
+    topk_idx, topk_val = up.topk_idx.cpu().numpy(), up.topk_val.cpu().numpy()
+    del up
+    torch.cuda.empty_cache()
+    ren = gb.Render(wl.scene, topk_idx, topk_val, wl.C, cams, device=str(dev))
     H, W = cams[0].height, cams[0].width
+    P, C = H * W, wl.C
+    cb = torch.as_tensor(codebook, device=dev)
+    D = cb.shape[1]
+    maps = torch.as_tensor(wl.region_maps, device=dev)
+    ci = torch.as_tensor(wl.code_idx, device=dev)
+    cv = torch.as_tensor(wl.code_val, device=dev)
     out = ren.outputs(cams[0])
-    gen = torch.Generator(device=dev).manual_seed(5)
-    g = torch.randn((H, W, rw.C), generator=gen, device=dev) * 1e-3
+    feats = torch.empty((P, D), dtype=torch.bfloat16, device=dev)
+    dF = torch.empty((P, D), dtype=torch.bfloat16, device=dev)
+    dW = torch.empty((H, W, C), dtype=torch.float32, device=dev)
+    loss = torch.zeros((), dtype=torch.float64, device=dev)
     d_val = torch.zeros_like(ren.topk_val)
     d_op = torch.zeros_like(ren.opacity)
+    dws = gb.scoup_decode(out[0].view(P, C), cb, feats)
+    lws = gb.scoup_region_l2_grad(feats, maps[:P], ci, cv, cb, dF, loss)
+    bws = gb.scoup_decode_backward(dF, cb, dW.view(P, C))
     stream = torch.cuda.current_stream()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
 
     def view(v):
         cam = cams[v]
+        o = int(wl.map_offsets[v])
         gb.scoup_render(ren.scene, ren.topk_idx, ren.topk_val, ren.K, ren.C, cam, out[0], out[1], out[2],
                         ren.workspace, stats=False)
-        gb.scoup_render_backward(ren.scene, ren.topk_idx, ren.topk_val, ren.K, ren.C, cam, g, d_val, d_op,
+        gb.scoup_decode(out[0].view(P, C), cb, feats, workspace=dws)
+        gb.scoup_region_l2_grad(feats, maps[o:o + P], ci, cv, cb, dF, loss, workspace=lws)
+        gb.scoup_decode_backward(dF, cb, dW.view(P, C), workspace=bws)
+        gb.scoup_render_backward(ren.scene, ren.topk_idx, ren.topk_val, ren.K, ren.C, cam, dW, d_val, d_op,
                                  ren.workspace)
 
     for _ in range(max(2, args.warmup)):
         view(0)
     torch.cuda.synchronize()
     dist.barrier()
+    loss.zero_()
     ev[0].record(stream)
     for v in range(len(cams)):
         view(v)
     ev[1].record(stream)
     torch.cuda.synchronize()
     t = dist.max(ev[0].elapsed_time(ev[1]) / 1e3)
+    loss_val = float(loss.item())
     gb.scoup_profile_enable(True)
     for v in range(len(cams)):
         view(v)
     torch.cuda.synchronize()
     prof = gb.scoup_profile_read()
     gb.scoup_profile_enable(False)
-    st = gb.scoup_read_stats(ren.workspace)
-    if st["status"] != 0:
-        raise RuntimeError("render backward status")
-    P = H * W
-    return {"metric": "render forward+backward pixels/s", "value": dist.world * len(cams) * P / t / 1e6,
-            "unit": "MPix/s", "workload": rw.name, "views_timed": len(cams), "pixels_per_view": P,
-            "C": rw.C, "K": rw.K, "ms_per_view": t * 1e3 / len(cams),
-            "phase_ms_per_view": {k: prof[k][0] / len(cams) for k in ("render", "render_bwd") if k in prof},
-            "gradient": "seeded N(0, 1e-3) dL/dWhat"}
+    for w in (ren.workspace, dws, lws, bws):
+        if gb.scoup_read_stats(w)["status"] != 0:
+            raise RuntimeError("loss chain device status")
+    return {"metric": "render+decode+loss+backward pixels/s", "value": dist.world * len(cams) * P / t / 1e6,
+            "unit": "MPix/s", "workload": wl.name, "views_timed": len(cams), "pixels_per_view": P,
+            "C": C, "D": D, "K": wl.K, "ms_per_view": t * 1e3 / len(cams),
+            "phase_ms_per_view": {k: prof[k][0] / len(cams) for k in ("render", "decode", "render_bwd") if k in prof},
+            "loss_per_view": loss_val / len(cams),
+            "chain": "scoup_render -> scoup_decode (bf16) -> scoup_region_l2_grad -> scoup_decode_backward "
+                     "(bf16 tensor cores) -> scoup_render_backward",
+            "codes": "Top-K of the workload's own uplift (32 views, 200 regions per view, s = 8)"}
 
 
 def levels_leg(args, dist, dev):

@@ -311,6 +311,22 @@ size_t scoup_entropy_filter_workspace_size(void);
 int scoup_entropy_filter(const float* entropy, int64_t n, int64_t keep, int32_t K, int32_t* topk_idx,
                          float* topk_val, uint8_t* keep_mask, void* workspace, size_t ws_bytes, void* stream);
 
+/* Similarity and relevancy in one pass (App. B, Eq. 9): the cosine
+ * similarity GEMM of scoup_similarity whose epilogue turns each pixel's row of
+ * Q similarities straight into the relevancy of the Q - n_canon queries
+ * against the n_canon canonical phrases (the first n_canon text vectors), as
+ * scoup_relevancy would from scoup_similarity's output: the similarity matrix
+ * never reaches memory.  Same features, feat_norm2, text, workspace (size
+ * scoup_similarity_workspace_size(P, D, Q)) and rounding as scoup_similarity.
+ *  Q          16 or 32 (one column tile); Q - n_canon a multiple of 4.
+ *  alpha      > 0 (10 in the paper).
+ *  R          DEVICE float32 [P, Q - n_canon], 16-byte aligned.
+ * Results equal scoup_similarity followed by scoup_relevancy bit for bit.
+ * Asynchronous. */
+int scoup_similarity_relevancy(const void* features, int64_t P, int32_t D, const float* feat_norm2,
+                               const float* text, int32_t Q, int32_t n_canon, float alpha, float* R,
+                               void* workspace, size_t ws_bytes, void* stream);
+
 /* Relevancy score of text queries (App. B, Eq. 9):
  *   R[p][q] = min_k exp(a s_q) / (exp(a s_q) + exp(a s_k))
  * from the similarities sim [P, ncols] (scoup_similarity output) whose first
@@ -450,6 +466,44 @@ size_t scoup_similarity_workspace_size(int64_t P, int32_t D, int32_t Q);
  * set with zero rows).  Asynchronous; errors as for scoup_decode. */
 int scoup_similarity(const void* features, int64_t P, int32_t D, const float* feat_norm2, const float* text,
                      int32_t Q, float* out, void* workspace, size_t ws_bytes, void* stream);
+
+/* Backward of the decode (Eq. 8) for the differentiable render: with
+ * F = What C, dL/dWhat = dL/dF C^T, a [P, D] x [D, C] contraction on the
+ * tensor cores (the codebook rows are its K-major operand as stored).
+ *  dF         DEVICE [P, D], float32 (dF_dtype 0, rounded to bf16 inside, in
+ *             chunks of the workspace) or bf16 (dF_dtype 1), 16-byte aligned.
+ *  codebook   DEVICE float32 [C, D] (rounded to bf16 inside).
+ *  dcodes     DEVICE float32 [P, C], 16-byte aligned: overwritten.
+ *  C          multiple of 16 in [16, 4096]; D a positive multiple of 8.
+ *  workspace  DEVICE, >= scoup_decode_backward_workspace_size(P, C, D) bytes.
+ * BF16 operands, FP32 accumulation in tensor memory.  Asynchronous.
+ * scoup_decode_backward_fp32 is the FP32 SIMT comparison form (float32 dF,
+ * no workspace, any P, C, D >= 1). */
+size_t scoup_decode_backward_workspace_size(int64_t P, int32_t C, int32_t D);
+int scoup_decode_backward(const void* dF, int32_t dF_dtype, int64_t P, int32_t D, const float* codebook, int32_t C,
+                          float* dcodes, void* workspace, size_t ws_bytes, void* stream);
+int scoup_decode_backward_fp32(const float* dF, int64_t P, int32_t D, const float* codebook, int32_t C,
+                               float* dcodes, void* stream);
+
+/* The L2 loss of the differentiable render against per-pixel region targets
+ * and its gradient: the target of pixel p is the decoded code of its region,
+ * F*(p) = sum_j v_j C[j] over code_{r(p)} (the region codes of Eq. 5 and the
+ * codebook of Eq. 8); L = sum over labelled pixels of |F(p) - F*(p)|^2 and
+ * dL/dF(p) = 2 (F(p) - F*(p)) (zero at unlabelled pixels, region -1).
+ *  F           DEVICE [P, D] float32 (F_dtype 0) or bf16 (F_dtype 1).
+ *  region_map  DEVICE int32 [P]: region of each pixel (row of the code table), -1 none.
+ *  code_idx, code_val  DEVICE [R, s] (atom -1 = padding); codebook DEVICE float32 [C, D].
+ *  dF          DEVICE [P, D] float32 (dF_dtype 0) or bf16 (dF_dtype 1): overwritten.
+ *  loss        DEVICE double: L is added to it (FP32 terms, FP64 sum), or NULL.
+ *  workspace   DEVICE, >= scoup_region_l2_grad_workspace_size(R, D) bytes
+ *              (the decoded region targets, FP32).
+ * A region id >= R or an atom >= C sets the device status read by
+ * scoup_read_stats(workspace) (SCOUP_ERR_DEVICE_CHECK).  Asynchronous. */
+size_t scoup_region_l2_grad_workspace_size(int32_t R, int32_t D);
+int scoup_region_l2_grad(const void* F, int32_t F_dtype, int64_t P, int32_t D, const int32_t* region_map,
+                         const int32_t* code_idx, const float* code_val, int32_t R, int32_t s,
+                         const float* codebook, int32_t C, void* dF, int32_t dF_dtype, double* loss,
+                         void* workspace, size_t ws_bytes, void* stream);
 
 /* FP32 comparison forms of scoup_decode and scoup_similarity: the same
  * results computed with FP32 operands and FP32 FFMA accumulation on the SIMT

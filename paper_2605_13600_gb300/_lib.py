@@ -127,6 +127,14 @@ PROTOS = {
     "scoup_plan_info_get": (ct.c_int, [P, ct.POINTER(PlanInfo)]),
     "scoup_plan_destroy": (ct.c_int, [P]),
     "scoup_selftest_gemm_timeout": (ct.c_int, [P, SZ, P]),
+    "scoup_similarity_relevancy": (ct.c_int, [P, ct.c_int64, ct.c_int32, P, P, ct.c_int32, ct.c_int32, ct.c_float,
+                                              P, P, SZ, P]),
+    "scoup_decode_backward_workspace_size": (SZ, [ct.c_int64, ct.c_int32, ct.c_int32]),
+    "scoup_decode_backward": (ct.c_int, [P, ct.c_int32, ct.c_int64, ct.c_int32, P, ct.c_int32, P, P, SZ, P]),
+    "scoup_decode_backward_fp32": (ct.c_int, [P, ct.c_int64, ct.c_int32, P, ct.c_int32, P, P]),
+    "scoup_region_l2_grad_workspace_size": (SZ, [ct.c_int32, ct.c_int32]),
+    "scoup_region_l2_grad": (ct.c_int, [P, ct.c_int32, ct.c_int64, ct.c_int32, P, P, P, ct.c_int32, ct.c_int32,
+                                        P, ct.c_int32, P, ct.c_int32, P, P, SZ, P]),
     "scoup_selftest_red_throughput": (ct.c_int, [P, ct.c_int32, ct.c_int64, ct.c_uint32, P]),
     "scoup_profile_enable": (ct.c_int, [I32]),
     "scoup_profile_read": (ct.c_int, [P, P, I32]),

@@ -924,6 +924,147 @@ int scoup_similarity(const void* features, int64_t P, int32_t D, const float* fe
   return SCOUP_OK;
 }
 
+int scoup_similarity_relevancy(const void* features, int64_t P, int32_t D, const float* feat_norm2,
+                               const float* text, int32_t Q, int32_t n_canon, float alpha, float* R,
+                               void* workspace, size_t ws_bytes, void* stream) {
+  if (P < 0 || P > 0x7fffffffLL) return fail(SCOUP_ERR_INVALID_ARG, "P=%lld outside [0, 2^31)", (long long)P);
+  if (D < 8 || D % 8) return fail(SCOUP_ERR_INVALID_ARG, "D=%d must be a positive multiple of 8", D);
+  if (Q != 16 && Q != 32) return fail(SCOUP_ERR_INVALID_ARG, "Q=%d: the fused form takes 16 or 32 text vectors", Q);
+  if (n_canon < 1 || n_canon >= Q || (Q - n_canon) % 4)
+    return fail(SCOUP_ERR_INVALID_ARG, "n_canon=%d: need 1 <= n_canon < Q and Q - n_canon a multiple of 4", n_canon);
+  if (!(alpha > 0.0f) || alpha > 3.0e38f) return fail(SCOUP_ERR_INVALID_ARG, "alpha must be positive and finite");
+  if (P > 0 && (!features || !text || !R)) return fail(SCOUP_ERR_INVALID_ARG, "NULL array");
+  if (((uintptr_t)features & 15u) || ((uintptr_t)R & 15u))
+    return fail(SCOUP_ERR_INVALID_ARG, "features and R must be 16-byte aligned");
+  if (!workspace || ws_bytes < scoup_similarity_workspace_size(P, D, Q))
+    return fail(SCOUP_ERR_OOM, "workspace too small: need %zu bytes", scoup_similarity_workspace_size(P, D, Q));
+  if (!gemm_tma_available()) return fail(SCOUP_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+  cudaStream_t st = (cudaStream_t)stream;
+  char* w = (char*)workspace;
+  WsHeader* hdr = (WsHeader*)w;
+  void* tb = w + align_up(sizeof(WsHeader));
+  float* tnorm = (float*)((char*)tb + align_up((size_t)Q * D * 2));
+  float* fnorm2 = (float*)((char*)tnorm + align_up((size_t)Q * 4));
+  cudaError_t e;
+  PhaseScope ps(SCOUP_PHASE_SIMILARITY, st);
+  if ((e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
+  if (P == 0) return SCOUP_OK;
+  if ((e = launch_f32_to_bf16(text, tb, (int64_t)Q * D, st)) != cudaSuccess) return cuda_fail(e, "text");
+  if ((e = launch_row_norm_bf16(tb, Q, D, tnorm, 0, st)) != cudaSuccess) return cuda_fail(e, "text norms");
+  const float* rn2 = feat_norm2;
+  if (!rn2) {
+    if ((e = launch_row_norm_bf16(features, P, D, fnorm2, 1, st)) != cudaSuccess) return cuda_fail(e, "norms");
+    rn2 = fnorm2;
+  }
+  GemmEpi ep;
+  ep.M = (int)P;
+  ep.N = Q;
+  ep.K = D;
+  ep.mode = kOutRel;
+  ep.out = R;
+  ep.ldo = Q - n_canon;
+  ep.rownorm2 = const_cast<float*>(rn2);
+  ep.colnorm = tnorm;
+  ep.n_canon = n_canon;
+  ep.alpha = alpha;
+  ep.status = &hdr->status;
+  if ((e = launch_gemm_bf16(features, tb, ep, st)) != cudaSuccess) return cuda_fail(e, "similarity gemm");
+  return SCOUP_OK;
+}
+
+size_t scoup_decode_backward_workspace_size(int64_t P, int32_t C, int32_t D) {
+  if (P < 0 || C <= 0 || D <= 0) return 0;
+  return align_up(sizeof(WsHeader)) + align_up((size_t)C * D * 2) + align_up((size_t)decode_chunk_rows(P) * D * 2);
+}
+
+int scoup_decode_backward(const void* dF, int32_t dF_dtype, int64_t P, int32_t D, const float* codebook, int32_t C,
+                          float* dcodes, void* workspace, size_t ws_bytes, void* stream) {
+  if (P < 0 || P > 0x7fffffffLL) return fail(SCOUP_ERR_INVALID_ARG, "P=%lld outside [0, 2^31)", (long long)P);
+  if (C < 16 || C % 16 || C > 4096) return fail(SCOUP_ERR_INVALID_ARG, "C=%d must be a multiple of 16 in [16, 4096]", C);
+  if (D < 8 || D % 8) return fail(SCOUP_ERR_INVALID_ARG, "D=%d must be a positive multiple of 8", D);
+  if (dF_dtype != 0 && dF_dtype != 1) return fail(SCOUP_ERR_INVALID_ARG, "dF_dtype must be 0 (f32) or 1 (bf16)");
+  if (P > 0 && (!dF || !codebook || !dcodes)) return fail(SCOUP_ERR_INVALID_ARG, "NULL array");
+  if (((uintptr_t)dF & 15u) || ((uintptr_t)dcodes & 15u))
+    return fail(SCOUP_ERR_INVALID_ARG, "dF and dcodes must be 16-byte aligned");
+  if (!workspace || ws_bytes < scoup_decode_backward_workspace_size(P, C, D))
+    return fail(SCOUP_ERR_OOM, "workspace too small: need %zu bytes", scoup_decode_backward_workspace_size(P, C, D));
+  if (!gemm_tma_available()) return fail(SCOUP_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+  cudaStream_t st = (cudaStream_t)stream;
+  char* w = (char*)workspace;
+  WsHeader* hdr = (WsHeader*)w;
+  void* Bt = w + align_up(sizeof(WsHeader));  // the codebook rows are the K-major operand as they are
+  void* Abuf = (char*)Bt + align_up((size_t)C * D * 2);
+  cudaError_t e;
+  PhaseScope ps(SCOUP_PHASE_DECODE, st);
+  if ((e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
+  if (P == 0) return SCOUP_OK;
+  if ((e = launch_f32_to_bf16(codebook, Bt, (int64_t)C * D, st)) != cudaSuccess) return cuda_fail(e, "codebook");
+  const int64_t chunk = dF_dtype == 1 ? P : decode_chunk_rows(P);
+  for (int64_t r0 = 0; r0 < P; r0 += chunk) {
+    const int64_t rows = P - r0 < chunk ? P - r0 : chunk;
+    const void* A;
+    if (dF_dtype == 0) {
+      if ((e = launch_f32_to_bf16((const float*)dF + r0 * D, Abuf, rows * D, st)) != cudaSuccess)
+        return cuda_fail(e, "convert");
+      A = Abuf;
+    } else {
+      A = (const char*)dF + (size_t)r0 * D * 2;
+    }
+    GemmEpi ep;
+    ep.M = (int)rows;
+    ep.N = C;
+    ep.K = D;
+    ep.mode = kOutF32;
+    ep.out = dcodes + (size_t)r0 * C;
+    ep.ldo = C;
+    ep.rownorm2 = nullptr;
+    ep.colnorm = nullptr;
+    ep.status = &hdr->status;
+    if ((e = launch_gemm_bf16(A, Bt, ep, st)) != cudaSuccess) return cuda_fail(e, "decode backward gemm");
+  }
+  return SCOUP_OK;
+}
+
+int scoup_decode_backward_fp32(const float* dF, int64_t P, int32_t D, const float* codebook, int32_t C,
+                               float* dcodes, void* stream) {
+  if (P < 0 || C < 1 || D < 1) return fail(SCOUP_ERR_INVALID_ARG, "bad sizes P=%lld C=%d D=%d", (long long)P, C, D);
+  if (P > 0 && (!dF || !codebook || !dcodes)) return fail(SCOUP_ERR_INVALID_ARG, "NULL array");
+  PhaseScope ps(SCOUP_PHASE_DECODE, (cudaStream_t)stream);
+  const cudaError_t e = launch_sgemm(dF, codebook, true, dcodes, P, C, D, nullptr, nullptr, (cudaStream_t)stream);
+  return e == cudaSuccess ? SCOUP_OK : cuda_fail(e, "sgemm");
+}
+
+size_t scoup_region_l2_grad_workspace_size(int32_t R, int32_t D) {
+  if (R < 0 || D <= 0) return 0;
+  return align_up(sizeof(WsHeader)) + align_up((size_t)(R > 0 ? R : 1) * D * 4);
+}
+
+int scoup_region_l2_grad(const void* F, int32_t F_dtype, int64_t P, int32_t D, const int32_t* region_map,
+                         const int32_t* code_idx, const float* code_val, int32_t R, int32_t s,
+                         const float* codebook, int32_t C, void* dF, int32_t dF_dtype, double* loss,
+                         void* workspace, size_t ws_bytes, void* stream) {
+  if (P < 0 || D < 1 || R < 0 || s < 1 || C < 1) return fail(SCOUP_ERR_INVALID_ARG, "bad sizes");
+  if ((F_dtype != 0 && F_dtype != 1) || (dF_dtype != 0 && dF_dtype != 1))
+    return fail(SCOUP_ERR_INVALID_ARG, "F_dtype and dF_dtype must be 0 (f32) or 1 (bf16)");
+  if (P > 0 && (!F || !region_map || !dF || !codebook)) return fail(SCOUP_ERR_INVALID_ARG, "NULL array");
+  if (R > 0 && (!code_idx || !code_val)) return fail(SCOUP_ERR_INVALID_ARG, "code table is NULL");
+  if (!workspace || ws_bytes < scoup_region_l2_grad_workspace_size(R, D))
+    return fail(SCOUP_ERR_OOM, "workspace too small: need %zu bytes", scoup_region_l2_grad_workspace_size(R, D));
+  cudaStream_t st = (cudaStream_t)stream;
+  char* w = (char*)workspace;
+  WsHeader* hdr = (WsHeader*)w;
+  float* target = (float*)(w + align_up(sizeof(WsHeader)));
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
+  if (P == 0) return SCOUP_OK;
+  if ((e = launch_region_targets(code_idx, code_val, R, s, codebook, C, D, target, &hdr->status, st)) != cudaSuccess)
+    return cuda_fail(e, "region targets");
+  if ((e = launch_l2_grad(F, F_dtype, P, D, region_map, R, target, dF, dF_dtype, loss, &hdr->status, st)) !=
+      cudaSuccess)
+    return cuda_fail(e, "loss gradient");
+  return SCOUP_OK;
+}
+
 int scoup_decode_fp32(const float* codes, int64_t P, int32_t C, const float* codebook, int32_t D,
                       float* features, void* stream) {
   if (P < 0 || C < 1 || D < 1) return fail(SCOUP_ERR_INVALID_ARG, "bad sizes P=%lld C=%d D=%d", (long long)P, C, D);

@@ -130,7 +130,7 @@ __global__ void relevancy_kernel(const float* __restrict__ sim, int64_t P, int n
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) c = fmaxf(c, __shfl_xor_sync(0xffffffffu, c, off));
         const float sq = __shfl_sync(0xffffffffu, v[u], min(n_canon + lane, 31));
-        if (p0 + u < P && lane < nq) R[(p0 + u) * nq + lane] = fminf(1.0f, 1.0f / (1.0f + expf(alpha * (c - sq))));
+        if (p0 + u < P && lane < nq) R[(p0 + u) * nq + lane] = relevancy_term(alpha, c, sq);
       }
     }
     return;
@@ -141,7 +141,7 @@ __global__ void relevancy_kernel(const float* __restrict__ sim, int64_t P, int n
     for (int k = 0; k < n_canon; ++k) smax = fmaxf(smax, row[k]);
     for (int q = lane; q < nq; q += 32) {
       const float sq = row[n_canon + q];
-      R[p * nq + q] = fminf(1.0f, 1.0f / (1.0f + expf(alpha * (smax - sq))));
+      R[p * nq + q] = relevancy_term(alpha, smax, sq);
     }
   }
 }

@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_bf16_kernel(const __grid
       ptx::tc_fence_after();
       const int row = m0 + q * 32 + lane;
       float rinv = 0.0f;
-      if (ep.mode == kOutCos && row < ep.M) {
+      if ((ep.mode == kOutCos || ep.mode == kOutRel) && row < ep.M) {
         const float rn = sqrtf(ep.rownorm2[row]);
         rinv = rn < 1e-12f ? 0.0f : 1.0f / rn;
       }
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_bf16_kernel(const __grid
             }
           }
         } else {
-          if (ep.mode == kOutCos) {
+          if (ep.mode == kOutCos || ep.mode == kOutRel) {
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
               const int c = n0 + c0 + i;
@@ -214,10 +214,30 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_bf16_kernel(const __grid
               v[i] = (rinv == 0.0f || cn == 0.0f) ? 0.0f : v[i] * rinv / cn;
             }
           }
+          if (ep.mode == kOutRel) {
+            // Eq. 9 on the thread's whole row of similarities (N <= 32, one
+            // column tile): R_q = min_k 1 / (1 + e^{a (s_k - s_q)}) is the
+            // term of the largest canonical similarity; query q is column
+            // n_canon + q, staged at column q of the relevancy row
+            float smax = -INFINITY;
 #pragma unroll
-          for (int j = 0; j < 8; ++j)
-            *reinterpret_cast<float4*>(rowp + ((j ^ (lane & 7)) << 4)) =
-                make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+            for (int i = 0; i < 32; ++i)
+              if (i < ep.n_canon) smax = fmaxf(smax, v[i]);
+            float* rowf = reinterpret_cast<float*>(rowp);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              const int q = i - ep.n_canon;
+              if (q >= 0 && i < ep.N) {
+                const float r = relevancy_term(ep.alpha, smax, v[i]);
+                rowf[(((q >> 2) ^ (lane & 7)) << 2) + (q & 3)] = r;
+              }
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              *reinterpret_cast<float4*>(rowp + ((j ^ (lane & 7)) << 4)) =
+                  make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+          }
         }
         ptx::fence_async_shared();
         __syncwarp();

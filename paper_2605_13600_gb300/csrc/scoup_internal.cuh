@@ -152,6 +152,18 @@ __device__ __forceinline__ uint32_t box_grid_mask(const ProjRec& r, float x0, fl
   return mask;
 }
 
+// One relevancy term of App. B, Eq. 9: e^{a s_q} / (e^{a s_q} + e^{a s_k}) =
+// 1 / (1 + e^{a (s_k - s_q)}), with s_k the largest canonical similarity (the
+// term decreases in s_k, so it is the minimum over the canonical phrases).
+// The exponential is the SFU's base-2 one and the quotient the fast
+// reciprocal (about 2^-21 relative together); both relevancy paths use this
+// one function, so they agree bit for bit.
+__device__ __forceinline__ float relevancy_term(float alpha, float s_canon_max, float s_query) {
+  float e;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(alpha * 1.4426950408889634f * (s_canon_max - s_query)));
+  return fminf(1.0f, __fdividef(1.0f, 1.0f + e));
+}
+
 // Region maps and code tables of one view, one per semantic level (a single
 // level for scoup_uplift; up to three for scoup_uplift_levels).
 constexpr int kMaxLevels = 3;
@@ -281,14 +293,16 @@ size_t render_bwd_smem_bytes(int C, int K);
 cudaError_t launch_render_bwd(const CamArgs& cam, const UpliftWs& ws, int slot, const int32_t* topk_idx,
                               const float* topk_val, int K, int C, const float* dL_dcodes, float* d_val,
                               float* d_opacity, cudaStream_t st);
-constexpr int kOutBF16 = 0, kOutF32 = 1, kOutCos = 2;
+constexpr int kOutBF16 = 0, kOutF32 = 1, kOutCos = 2, kOutRel = 3;
 struct GemmEpi {
   int M, N, K;
-  int mode;              // kOutBF16 / kOutF32 / kOutCos
-  void* out;
+  int mode;              // kOutBF16 / kOutF32 / kOutCos / kOutRel
+  void* out;             // kOutRel: the relevancy [M, N - n_canon] (ldo = N - n_canon, a multiple of 4)
   int64_t ldo;           // elements
-  float* rownorm2;       // kOutBF16: accumulated squared row norms (may be null); kOutCos: input
-  const float* colnorm;  // kOutCos: column norms
+  float* rownorm2;       // kOutBF16: accumulated squared row norms (may be null); kOutCos, kOutRel: input
+  const float* colnorm;  // kOutCos, kOutRel: column norms
+  int n_canon = 0;       // kOutRel (N <= 32): the first n_canon columns are the canonical phrases
+  float alpha = 0.0f;    // kOutRel: softmax temperature of Eq. 9
   int* status;
   int stall_loads = 0;   // self-test only: the producer issues no loads, so the bounded waits run out
 };
@@ -307,6 +321,10 @@ cudaError_t launch_topk(const float* accum, const float* comp, int64_t n, int C,
 size_t entropy_filter_state_bytes();
 int entropy_filter_run(const float* H, int64_t n, int64_t keep, int K, int32_t* idx, float* val, uint8_t* mask,
                        void* workspace, cudaStream_t st);
+cudaError_t launch_region_targets(const int32_t* ci, const float* cv, int R, int s, const float* codebook, int C,
+                                  int D, float* target, int* status, cudaStream_t st);
+cudaError_t launch_l2_grad(const void* F, int F_bf16, int64_t P, int D, const int32_t* rmap, int R,
+                           const float* target, void* dF, int dF_bf16, double* loss, int* status, cudaStream_t st);
 cudaError_t launch_relevancy(const float* sim, int64_t P, int ncols, int n_canon, float alpha, float* R,
                              cudaStream_t st);
 cudaError_t launch_code_topk(const int32_t* ci, const float* cv, int64_t R, int s, int K,

@@ -376,6 +376,94 @@ def scoup_similarity(features, text, out, feat_norm2=None, workspace=None, strea
     return workspace
 
 
+def scoup_similarity_relevancy(features, text, n_canon: int, R, alpha: float = 10.0, feat_norm2=None,
+                               workspace=None, stream=None):
+    """Relevancy R [P, Q - n_canon] (Eq. 9) of bf16 features [P, D] for the
+    float32 text vectors [Q, D] whose first n_canon rows are the canonical
+    phrases, computed in the similarity GEMM's epilogue."""
+    import torch
+    _need(features, torch.bfloat16, "features")
+    _need(text, torch.float32, "text")
+    _need(R, torch.float32, "R")
+    _need(feat_norm2, torch.float32, "feat_norm2")
+    P, D = features.shape
+    Q = text.shape[0]
+    if text.shape[1] != D or tuple(R.shape) != (P, Q - n_canon):
+        raise ValueError("shape mismatch")
+    if workspace is None:
+        workspace = torch.empty(scoup_similarity_workspace_size(P, D, Q), dtype=torch.uint8,
+                                device=features.device)
+    _need(workspace, torch.uint8, "workspace")
+    check(load().scoup_similarity_relevancy(_ptr(features), P, D, _ptr(feat_norm2), _ptr(text), Q, int(n_canon),
+                                            float(alpha), _ptr(R), _ptr(workspace), workspace.numel(),
+                                            _stream(stream)))
+    return workspace
+
+
+def scoup_decode_backward(dF, codebook, dcodes, workspace=None, stream=None):
+    """dcodes [P, C] = dF [P, D] @ codebook[C, D]^T on the tensor cores (bf16
+    operands, FP32 accumulation); dF float32 or bf16.  Returns the workspace."""
+    import torch
+    if not isinstance(dF, torch.Tensor) or dF.dtype not in (torch.float32, torch.bfloat16):
+        raise TypeError("dF must be a float32 or bfloat16 tensor")
+    _need(dF, dF.dtype, "dF")
+    _need(codebook, torch.float32, "codebook")
+    _need(dcodes, torch.float32, "dcodes")
+    P, D = dF.shape
+    C = codebook.shape[0]
+    if codebook.shape[1] != D or tuple(dcodes.shape) != (P, C):
+        raise ValueError("shape mismatch")
+    if workspace is None:
+        workspace = torch.empty(int(load().scoup_decode_backward_workspace_size(P, C, D)), dtype=torch.uint8,
+                                device=dF.device)
+    _need(workspace, torch.uint8, "workspace")
+    check(load().scoup_decode_backward(_ptr(dF), 1 if dF.dtype == torch.bfloat16 else 0, P, D, _ptr(codebook), C,
+                                       _ptr(dcodes), _ptr(workspace), workspace.numel(), _stream(stream)))
+    return workspace
+
+
+def scoup_decode_backward_fp32(dF, codebook, dcodes, stream=None) -> None:
+    """FP32 SIMT comparison form of scoup_decode_backward."""
+    import torch
+    for t, nm in ((dF, "dF"), (codebook, "codebook"), (dcodes, "dcodes")):
+        _need(t, torch.float32, nm)
+    P, D = dF.shape
+    C = codebook.shape[0]
+    if codebook.shape[1] != D or tuple(dcodes.shape) != (P, C):
+        raise ValueError("shape mismatch")
+    check(load().scoup_decode_backward_fp32(_ptr(dF), P, D, _ptr(codebook), C, _ptr(dcodes), _stream(stream)))
+
+
+def scoup_region_l2_grad(F, region_map, code_idx, code_val, codebook, dF, loss=None, workspace=None, stream=None):
+    """L2 loss of features F [P, D] (float32 or bf16) against the decoded codes
+    of their regions and its gradient dF [P, D] (float32 or bf16); the loss is
+    added to the float64 device scalar `loss` when given.  Returns the workspace."""
+    import torch
+    for t, nm in ((F, "F"), (dF, "dF")):
+        if not isinstance(t, torch.Tensor) or t.dtype not in (torch.float32, torch.bfloat16):
+            raise TypeError(f"{nm} must be a float32 or bfloat16 tensor")
+        _need(t, t.dtype, nm)
+    _need(region_map, torch.int32, "region_map")
+    _need(code_idx, torch.int32, "code_idx")
+    _need(code_val, torch.float32, "code_val")
+    _need(codebook, torch.float32, "codebook")
+    _need(loss, torch.float64, "loss")
+    P, D = F.shape
+    R, s = code_idx.shape
+    C = codebook.shape[0]
+    if tuple(dF.shape) != (P, D) or region_map.numel() != P or codebook.shape[1] != D or code_val.shape != code_idx.shape:
+        raise ValueError("shape mismatch")
+    if workspace is None:
+        workspace = torch.empty(int(load().scoup_region_l2_grad_workspace_size(R, D)), dtype=torch.uint8,
+                                device=F.device)
+    _need(workspace, torch.uint8, "workspace")
+    bf = lambda t: 1 if t.dtype == torch.bfloat16 else 0  # noqa: E731
+    check(load().scoup_region_l2_grad(_ptr(F), bf(F), P, D, _ptr(region_map), _ptr(code_idx), _ptr(code_val), R, s,
+                                      _ptr(codebook), C, _ptr(dF), bf(dF), _ptr(loss), _ptr(workspace),
+                                      workspace.numel(), _stream(stream)))
+    return workspace
+
+
 def scoup_decode_fp32(codes, codebook, features, stream=None) -> None:
     """FP32 SIMT comparison form of scoup_decode: features [P, D] = codes [P, C] @ codebook [C, D]."""
     import torch
@@ -733,4 +821,6 @@ __all__ = ["ScoupError", "SCOUP_ACCUM_CONTINUE", "SCOUP_ACCUM_COMPENSATED", "sce
            "scoup_similarity", "scoup_decode_fp32", "scoup_similarity_fp32", "BatchedUplift",
            "SCOUP_BATCH_EAGER", "LevelUplift", "scoup_selftest_gemm_timeout", "scoup_selftest_red_throughput", "scoup_topk_entropy", "scoup_entropy_filter", "scoup_entropy_filter_workspace_size", "scoup_relevancy",
            "scoup_render_decode_workspace_size", "scoup_render_decode_fused",
-           "scoup_uplift_host_maps_workspace_size", "scoup_uplift_host_maps"]
+           "scoup_uplift_host_maps_workspace_size", "scoup_uplift_host_maps",
+           "scoup_similarity_relevancy", "scoup_decode_backward", "scoup_decode_backward_fp32",
+           "scoup_region_l2_grad"]

@@ -33,7 +33,7 @@ __all__ = [
     "gaussians", "look_at", "camera_at", "fibonacci_cameras", "band_cameras",
     "voronoi_map", "region_codes", "sparse_topk_codes", "unit_rows",
     "tiny_workload", "uplift_cfg1", "uplift_cfg2", "uplift_cfg3_scene",
-    "render_cfg4", "render_cfg5", "dense_feature_codes", "level_workloads",
+    "render_cfg4", "render_cfg5", "uplift_cfg5", "dense_feature_codes", "level_workloads",
 ]
 
 
@@ -369,8 +369,27 @@ def render_cfg4(topk_idx: Optional[np.ndarray] = None, topk_val: Optional[np.nda
                           256, 8, codebook, text)
 
 
+def uplift_cfg5(n: int = 500_000, V: int = 32, width: int = 800, height: int = 600, R: int = 200,
+                C: int = 256, s: int = 8, K: int = 8, D: int = 512, seed: int = 5, device: str = "cpu"):
+    """The differentiable-render workload with its own uplift inputs: n blob
+    Gaussians, V band views, R Voronoi regions per view with s-sparse codes
+    over C atoms, Top-K of K (the Top-K comes from uplifting these inputs),
+    and a C x D unit-norm codebook.  The loss targets are the decoded region
+    codes, F*(p) = code_{r(p)} C.  Returns (UpliftWorkload, codebook)."""
+    rng = np.random.default_rng(seed)
+    scene = gaussians(rng, n, "blobs")
+    cams = band_cameras(rng, V, 3.0, width, height, 60.0)
+    maps, offs, rpv, R_tot = _pack_maps(_draw_seeds(rng, cams, [R] * V), cams, device)
+    ci, cv = region_codes(rng, R_tot, C, s)
+    codebook = unit_rows(rng, C, D)
+    wl = UpliftWorkload(f"cfg5_diff_render_{n}_{V}v_{width}x{height}", scene, cams, maps, offs, ci, cv, C, s, K, rpv)
+    return wl, codebook
+
+
 def render_cfg5(n: int = 500_000, V: int = 32) -> RenderWorkload:
-    """500k blob Gaussians, 32 band views at 800x600, K=8 of C=256 (seed 5)."""
+    """500k blob Gaussians, 32 band views at 800x600, K=8 of C=256 (seed 5),
+    random K-sparse codes (for backward checks that need no uplift; the
+    benchmark's differentiable-render leg uses uplift_cfg5's own uplift)."""
     rng = np.random.default_rng(5)
     scene = gaussians(rng, n, "blobs")
     cams = band_cameras(rng, V, 3.0, 800, 600, 60.0)

@@ -153,3 +153,13 @@ def test_red_throughput_rejects_bad_arguments(lib):
     assert f(ct.c_void_p(256), 9, 10, 1, None) == lib.SCOUP_ERR_INVALID_ARG
     assert f(ct.c_void_p(256), 32, 10, 1, None) == lib.SCOUP_ERR_INVALID_ARG
     assert f(ct.c_void_p(256), 20, -1, 1, None) == lib.SCOUP_ERR_INVALID_ARG
+
+
+def test_similarity_relevancy_rejects_bad_arguments(lib):
+    f = lib.load().scoup_similarity_relevancy
+    buf = ct.c_void_p(256)
+    # Q must be 16 or 32; Q - n_canon a multiple of 4; alpha positive
+    assert f(buf, 10, 512, None, buf, 28, 4, 10.0, buf, buf, 1 << 20, None) == lib.SCOUP_ERR_INVALID_ARG
+    assert f(buf, 10, 512, None, buf, 32, 3, 10.0, buf, buf, 1 << 20, None) == lib.SCOUP_ERR_INVALID_ARG
+    assert f(buf, 10, 512, None, buf, 32, 0, 10.0, buf, buf, 1 << 20, None) == lib.SCOUP_ERR_INVALID_ARG
+    assert f(buf, 10, 512, None, buf, 32, 4, 0.0, buf, buf, 1 << 20, None) == lib.SCOUP_ERR_INVALID_ARG

@@ -59,3 +59,23 @@ def test_uplift_refuses_a_short_accumulator(monkeypatch, entry, mode):
             fn(region_maps=maps, workspace=None, **args)
         else:
             fn(region_maps=maps, **args)
+
+
+def test_every_declared_entry_point_has_a_python_wrapper():
+    """Each extern "C" function of include/*.h that takes device arrays is
+    reachable from the package (its wrapper is exported)."""
+    import os
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    names = set()
+    for fn in os.listdir(os.path.join(root, "include")):
+        if fn.endswith(".h"):
+            src = re.sub(r"/\*.*?\*/", "", open(os.path.join(root, "include", fn)).read(), flags=re.S)
+            names |= set(re.findall(r"\b(scoup_[a-z0-9_]+)\s*\(", src))
+    host_only = {"scoup_last_error", "scoup_plan_create", "scoup_plan_destroy", "scoup_plan_set",
+                 "scoup_plan_stats", "scoup_plan_info_get", "scoup_autotune", "scoup_uplift_batched",
+                 "scoup_uplift_levels", "scoup_uplift_levels_workspace_size",
+                 "scoup_region_l2_grad_workspace_size", "scoup_decode_backward_workspace_size",
+                 "scoup_render_workspace_size", "scoup_render_backward_workspace_size"}
+    missing = sorted(n for n in names - host_only if not hasattr(gb, n))
+    assert not missing, missing

@@ -159,6 +159,35 @@ def test_relevancy_pipeline_bf16(gb, oracle_lib):
     err = np.abs(R.cpu().numpy() - want)
     # dR/ds <= alpha / 4 per similarity; two similarities per term, each within the bf16 bound
     assert err.max() <= 1e-2 and err.mean() <= 1e-3
+    # the same relevancy computed in the similarity GEMM's epilogue
+    Rf = torch.empty((P, 28), dtype=torch.float32, device=dev)
+    gb.scoup_similarity_relevancy(feats, torch.from_numpy(T).to(dev), 4, Rf, feat_norm2=n2)
+    torch.cuda.synchronize()
+    assert torch.equal(Rf, R)
+
+
+@pytest.mark.parametrize("P,Q,n_canon", [(5037, 32, 4), (300, 16, 4), (1, 32, 8), (2900, 16, 12)])
+def test_similarity_relevancy_epilogue_equals_two_calls(gb, P, Q, n_canon):
+    """The fused form (relevancy in the similarity GEMM's epilogue) equals
+    scoup_similarity followed by scoup_relevancy bit for bit: ragged row
+    counts, rows of zero norm (similarity 0, relevancy 1/2), 16 or 32 text
+    vectors, several canonical phrases."""
+    import torch
+    rng = np.random.default_rng(P + Q)
+    D = 512
+    dev = torch.device("cuda:0")
+    F = torch.from_numpy(rng.normal(size=(P, D)).astype(np.float32)).to(dev).to(torch.bfloat16)
+    F[::97] = 0.0
+    T = torch.from_numpy(synth.unit_rows(rng, Q, D)).to(dev)
+    sim = torch.empty((P, Q), dtype=torch.float32, device=dev)
+    gb.scoup_similarity(F, T, sim)
+    R = torch.empty((P, Q - n_canon), dtype=torch.float32, device=dev)
+    gb.scoup_relevancy(sim, n_canon, R, alpha=10.0)
+    Rf = torch.full((P, Q - n_canon), -7.0, dtype=torch.float32, device=dev)
+    gb.scoup_similarity_relevancy(F, T, n_canon, Rf, alpha=10.0)
+    torch.cuda.synchronize()
+    assert torch.equal(Rf, R)
+    assert torch.all(Rf[::97] == 0.5)
 
 
 @pytest.mark.parametrize("n_canon,nq", [(1, 31), (2, 43), (4, 28)])
