@@ -96,7 +96,8 @@ struct TileSmem {
   uint8_t rec_mask[kWin];  // per window entry: the warps whose pixel block it may reach
   float part[kMaxSlots][kWin];
   float part_c[kComp ? kMaxSlots : 1][kComp ? kWin : 1];
-  uint32_t nz[kMaxSlots][kWin / 32];  // window entries whose partial became non-zero
+  uint8_t nzb[kMaxSlots][kWin];  // window entries whose partial became non-zero (plain byte stores)
+  int flist[kThreads / 32][32];  // per warp: the marked entries of one mask word, in order
   typename RegionKey<kL>::T slot_region[kMaxSlots];
   int slot_idx[kMaxSlots][kMaxS];
   float slot_val[kMaxSlots][kMaxS];
@@ -222,15 +223,19 @@ __device__ __forceinline__ float two_sum_err(float a, float b, float s) {
   return __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
 }
 
-// part[i] += v (v > 0, shared memory), compensated when kComp; the first
-// addition into an entry marks it in the non-zero mask nz.
+// part[i] += v (v > 0, shared memory), compensated when kComp; every
+// addition marks the entry for the flush with a plain byte store (all
+// writers store the same 1, so no atomic is needed).  The plain form never
+// reads the atomic's result, so the warp does not wait for it.
 template <bool kComp>
-__device__ __forceinline__ void part_add(float* part, float* part_c, uint32_t* nz, int i, float v) {
-  const float old = atomicAdd(&part[i], v);
-  if (old == 0.0f) atomicOr(&nz[i >> 5], 1u << (i & 31));
+__device__ __forceinline__ void part_add(float* part, float* part_c, uint8_t* nzb, int i, float v) {
+  nzb[i] = 1;
   if constexpr (kComp) {
+    const float old = atomicAdd(&part[i], v);
     const float err = two_sum_err(old, v, __fadd_rn(old, v));
     if (err != 0.0f) atomicAdd(&part_c[i], err);
+  } else {
+    atomicAdd(&part[i], v);
   }
 }
 
@@ -319,7 +324,7 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
   for (int k = tid; k < kMaxSlots * kWin; k += kThreads) (&sm.part[0][0])[k] = 0.0f;
   if constexpr (kComp)
     for (int k = tid; k < kMaxSlots * kWin; k += kThreads) (&sm.part_c[0][0])[k] = 0.0f;
-  for (int k = tid; k < kMaxSlots * (kWin / 32); k += kThreads) (&sm.nz[0][0])[k] = 0u;
+  for (int k = tid; k < kMaxSlots * kWin / 4; k += kThreads) reinterpret_cast<uint32_t*>(&sm.nzb[0][0])[k] = 0u;
   if (tid == 0) {
     // power = 0 for any pixel, never >= tau = +inf: no pixel accepts it
     sm.rec_a[kWin] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -592,7 +597,7 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
         if (wslot >= 0) {
           const float S = transpose_reduce8(e, lane);
           if ((lane & 3) == 0 && S > 0.0f)
-            part_add<kComp>(sm.part[wslot], sm.part_c[kComp ? wslot : 0], sm.nz[wslot], jq, S);
+            part_add<kComp>(sm.part[wslot], sm.part_c[kComp ? wslot : 0], sm.nzb[wslot], jq, S);
         } else {
           // pixels of several regions: one masked transpose reduction per slot present
           for (unsigned qm = wslots; qm != 0u; qm &= qm - 1u) {
@@ -602,7 +607,7 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
             for (int u = 0; u < kGroup; ++u) v[u] = my_slot == q ? e[u] : 0.0f;
             const float S = transpose_reduce8(v, lane);
             if ((lane & 3) == 0 && S > 0.0f)
-              part_add<kComp>(sm.part[q], sm.part_c[kComp ? q : 0], sm.nz[q], jq, S);
+              part_add<kComp>(sm.part[q], sm.part_c[kComp ? q : 0], sm.nzb[q], jq, S);
           }
           if (any_unslotted && my_slot < 0 && region_set(region)) {
             // more regions in this tile than slots: scatter this pixel directly
@@ -634,33 +639,47 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
     }
     __syncthreads();
     // ---- flush the (region, Gaussian) tile partials of this window ----
-    // Only the entries marked in nz are visited.  A warp takes one 32-entry
-    // mask word at a time and 32 / min(s, 32) of its set entries per step;
-    // each lane issues the atomics of one code entry.  (Numbering the set
-    // entries across all warps balances better but costs more per entry:
-    // measured slower.)  Visited entries are cleared here, the mask below.
+    // A warp takes one 32-entry word of the marks at a time (window entries
+    // [32 w, 32 w + 32) of one slot), compacts the marked entries into its
+    // list and issues the atomics of 32 / min(s, 32) of them per step, one
+    // code entry per lane; the first lane of an entry's group reads (and
+    // clears) the partial and passes it on with a shuffle.  (Numbering the
+    // marked entries across all warps balances better but costs more per
+    // entry: measured slower.)
     const int nwords = (m + 31) >> 5;
     const int nw = nslots * nwords;
     {
       const int lanes_per = s < 32 ? s : 32;
       const int per = 32 / lanes_per;
       const int sub = lane / lanes_per, a0 = lane - sub * lanes_per;
+      int* fl = sm.flist[warp];
       for (int wi = warp; wi < nw; wi += kThreads / 32) {
-        const int q = wi / nwords, w = wi - q * nwords;
-        unsigned bits = sm.nz[q][w];
-        while (bits != 0u) {
-          const int take = min(per, __popc(bits));
-          const int p = sub < take ? w * 32 + (int)__fns(bits, 0, sub + 1) : -1;
-          for (int t = 0; t < take; ++t) bits &= bits - 1u;
-          const float v = p >= 0 ? sm.part[q][p] : 0.0f;
-          const float vc = (kComp && p >= 0) ? sm.part_c[kComp ? q : 0][kComp ? p : 0] : 0.0f;
-          __syncwarp();
-          if (p >= 0) {
-            if (a0 == 0) {
-              sm.part[q][p] = 0.0f;
-              if constexpr (kComp) sm.part_c[q][p] = 0.0f;
-              ++n_flush;
+        const int q = wi / nwords, j = (wi - q * nwords) * 32 + lane;
+        const bool f = sm.nzb[q][j] != 0;
+        const unsigned bits = __ballot_sync(kFull, f);
+        if (f) {
+          fl[__popc(bits & ((1u << lane) - 1u))] = j;
+          sm.nzb[q][j] = 0;
+        }
+        __syncwarp();
+        const int cnt = __popc(bits);
+        for (int k0 = 0; k0 < cnt; k0 += per) {
+          const int k = k0 + sub;
+          const bool act = sub < per && k < cnt;
+          const int p = act ? fl[k] : 0;
+          float v = 0.0f, vc = 0.0f;
+          if (act && a0 == 0) {
+            v = sm.part[q][p];
+            sm.part[q][p] = 0.0f;
+            if constexpr (kComp) {
+              vc = sm.part_c[q][p];
+              sm.part_c[q][p] = 0.0f;
             }
+            ++n_flush;
+          }
+          v = __shfl_sync(kFull, v, sub * lanes_per);
+          if constexpr (kComp) vc = __shfl_sync(kFull, vc, sub * lanes_per);
+          if (act) {
             const int64_t g = (int64_t)(sm.win[p] & 0xffffffffull);
             for (int a = a0; a < s; a += lanes_per) {
               int jj;
@@ -678,11 +697,10 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
             }
           }
         }
+        __syncwarp();  // the list is rewritten for the next word
       }
     }
     all_done = __syncthreads_and(done) != 0;
-    // the mask words were read by every warp above: clear them for the next window
-    for (int wi = tid; wi < nw; wi += kThreads) sm.nz[wi / nwords][wi % nwords] = 0u;
 
     // ---- advance to the next window ----
     if (in_split) {
