@@ -450,8 +450,10 @@ def run_gb300(args, dist):
 def render_decode_leg(args, dist, wl, up, dev, pk):
     """Secondary measurement: sparse-code rendering (Eq. 7) of 1920x1080 views of
     the same 1M Gaussians with the Top-K codes the uplift just produced, codebook
-    decode (Eq. 8) to bf16 features and cosine similarity to 32 text vectors.
-    Returns the MPix/s figure with its phase split and the decode GEMM roofline."""
+    decode (Eq. 8) to bf16 features and cosine similarity to 32 text vectors,
+    the similarity computed in the decode GEMM (scoup_decode_query).  Returns
+    the MPix/s figure with its phase split, the decode GEMM roofline and the
+    three-call form (render, scoup_decode, scoup_similarity) beside it."""
     import numpy as np
     import torch
 
@@ -473,9 +475,15 @@ def render_decode_leg(args, dist, wl, up, dev, pk):
     sim = torch.empty((P, Q), dtype=torch.float32, device=dev)
     dws = torch.empty(gb.scoup_decode_workspace_size(P, wl.C, D), dtype=torch.uint8, device=dev)
     sws = torch.empty(gb.scoup_similarity_workspace_size(P, D, Q), dtype=torch.uint8, device=dev)
+    qws = torch.empty(gb.scoup_decode_query_workspace_size(P, wl.C, D, Q), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
     def view(v):
+        ren.run(v, out=out, stats=False)
+        gb.scoup_decode_query(out[0].view(P, wl.C), codebook, text, sim, features=feats, feat_norm2=n2,
+                              workspace=qws)
+
+    def view_three(v):
         ren.run(v, out=out, stats=False)
         gb.scoup_decode(out[0].view(P, wl.C), codebook, feats, n2, workspace=dws)
         gb.scoup_similarity(feats, text, sim, feat_norm2=n2, workspace=sws)
@@ -506,6 +514,28 @@ def render_decode_leg(args, dist, wl, up, dev, pk):
     prof = gb.scoup_profile_read()
     gb.scoup_profile_enable(False)
     phase_ms = {k: prof[k][0] / len(cams) for k in ("render", "decode", "similarity") if k in prof}
+    if "decode" in phase_ms:
+        phase_ms["decode_with_similarity"] = phase_ms.pop("decode")
+    if gb.scoup_read_stats(qws)["status"] != 0:
+        raise RuntimeError("decode + query device status")
+
+    # the three-call form: render, decode, similarity (the features read back)
+    for _ in range(3):
+        view_three(0)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for v in range(len(cams)):
+        view_three(v)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_three = ev0.elapsed_time(ev1) / 1e3
+    gb.scoup_profile_enable(True)
+    for v in range(len(cams)):
+        view_three(v)
+    torch.cuda.synchronize()
+    prof3 = gb.scoup_profile_read()
+    gb.scoup_profile_enable(False)
+    phase3 = {k: prof3[k][0] / len(cams) for k in ("render", "decode", "similarity") if k in prof3}
     if gb.scoup_read_stats(dws)["status"] != 0 or gb.scoup_read_stats(sws)["status"] != 0:
         raise RuntimeError("decode/similarity device status")
 
@@ -556,6 +586,15 @@ def render_decode_leg(args, dist, wl, up, dev, pk):
                                gb.scoup_relevancy(sim, 4, Rel)))
     t_epi = time_reps(lambda: gb.scoup_similarity_relevancy(feats, text, 4, Rel, feat_norm2=n2, workspace=rws))
     epi_bytes = 2.0 * P * D + 4.0 * P * (Q - 4)  # bf16 features in, relevancy out
+    # decode + similarity + relevancy: three calls vs one decode GEMM whose query unit writes the relevancy
+    codes_v = out[0].view(P, wl.C)
+    t_dsr = time_reps(lambda: (gb.scoup_decode(codes_v, codebook, feats, n2, workspace=dws),
+                               gb.scoup_similarity(feats, text, sim, feat_norm2=n2, workspace=sws),
+                               gb.scoup_relevancy(sim, 4, Rel)))
+    t_qrel = time_reps(lambda: gb.scoup_decode_query(codes_v, codebook, text, Rel, n_canon=4, features=feats,
+                                                     feat_norm2=n2, workspace=qws))
+    t_qrel_nf = time_reps(lambda: gb.scoup_decode_query(codes_v, codebook, text, Rel, n_canon=4,
+                                                        workspace=qws))
 
     # the decode GEMM alone: bf16 codes in, bf16 features out (one launch + a 256x512 transpose)
     codes_bf16 = out[0].view(P, wl.C)
@@ -571,6 +610,10 @@ def render_decode_leg(args, dist, wl, up, dev, pk):
     t_gemm = ev0.elapsed_time(ev1) / 1e3 / reps
     flops = 2.0 * P * wl.C * D
     gemm_bytes = 2.0 * P * wl.C + 2.0 * P * D
+    # the same GEMM with the query unit: + 4 Q bytes of similarities written per pixel
+    t_query = time_reps(lambda: gb.scoup_decode_query(codes_bf16, codebook, text, sim, features=feats,
+                                                      feat_norm2=n2, workspace=qws))
+    query_bytes = gemm_bytes + 4.0 * P * Q
     evaluated = sum(s["evaluated_pairs"] for s in stats) / len(stats)
     contrib = sum(s["contributions"] for s in stats) / len(stats)
     return {
@@ -587,7 +630,16 @@ def render_decode_leg(args, dist, wl, up, dev, pk):
                                         "bound": "hbm", "achieved": epi_bytes / t_epi / 1e9,
                                         "peak": pk["hbm_gbs"], "unit": "GB/s",
                                         "frac": epi_bytes / t_epi / 1e9 / pk["hbm_gbs"],
-                                        "speedup_vs_two_calls": t_two / t_epi}},
+                                        "speedup_vs_two_calls": t_two / t_epi},
+                      "decode_epilogue_form": {"call": "scoup_decode_query (n_canon 4)",
+                                               "decode_similarity_relevancy_ms": t_dsr * 1e3,
+                                               "ms_per_view": t_qrel * 1e3,
+                                               "speedup_vs_three_calls": t_dsr / t_qrel,
+                                               "without_features_ms": t_qrel_nf * 1e3}},
+        "form": "render -> scoup_decode_query (bf16 features, norms and the similarities from one GEMM)",
+        "three_call_form": {"form": "render -> scoup_decode -> scoup_similarity",
+                            "value": len(cams) * P / t_three / 1e6, "unit": "MPix/s",
+                            "ms_per_view": t_three * 1e3 / len(cams), "phase_ms_per_view": phase3},
         "fused_call": {"form": "scoup_render_decode_fused + scoup_similarity",
                        "value": len(cams) * P / t_fused / 1e6, "unit": "MPix/s",
                        "ms_per_view": t_fused * 1e3 / len(cams)},
@@ -602,6 +654,12 @@ def render_decode_leg(args, dist, wl, up, dev, pk):
                             "tensor_view": {"achieved_tflops": flops / t_gemm / 1e12, "peak_tflops": pk["bf16_tflops"],
                                             "frac": flops / t_gemm / 1e12 / pk["bf16_tflops"]},
                             "peak_source": pk["source"] + " (HBM copy; bf16 burst)"},
+        "decode_query_roofline": {"kernel": "gemm_bf16_kernel (with the query unit)", "bound": "hbm",
+                                  "achieved": query_bytes / t_query / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                  "frac": query_bytes / t_query / 1e9 / pk["hbm_gbs"],
+                                  "algorithmic_bytes_per_launch": query_bytes, "per_launch_ms": t_query * 1e3,
+                                  "vs_decode_then_similarity_ms": (t_gemm * 1e3,
+                                                                   phase3.get("similarity", float("nan")))},
     }
 
 

@@ -327,6 +327,40 @@ int scoup_similarity_relevancy(const void* features, int64_t P, int32_t D, const
                                const float* text, int32_t Q, int32_t n_canon, float alpha, float* R,
                                void* workspace, size_t ws_bytes, void* stream);
 
+/* Workspace bytes for scoup_decode_query. */
+size_t scoup_decode_query_workspace_size(int64_t P, int32_t C, int32_t D, int32_t Q);
+
+/* The codebook decode (Sec. 4.3, Eq. 8) with the text query of App. B in the
+ * same tensor-core GEMM: F = What C is decoded as by scoup_decode (bf16
+ * features, their squared norms), and the similarity of every row,
+ *   s[p][q] = <F_p, t_q> / (|F_p| |t_q|)  (0 where |F_p| < 1e-12 or |t_q| = 0),
+ * comes out of the same GEMM through the associativity
+ * <What_p C, t_q> = <What_p, C t_q>: the Q columns G = C T^T (FP32 sums,
+ * rounded to bf16) are a last 16- or 32-column unit of each 128-row block,
+ * whose epilogue divides by |F_p| (the norm of the row's rounded features,
+ * summed in the same CTA over the block's columns) and |t_q| (FP32, of the
+ * text as given).  The features therefore never have to be read back, and
+ * need not be stored at all.
+ *  codes, codes_dtype, P, C, codebook, D   as for scoup_decode.
+ *  text       DEVICE float32 [Q, D]; Q is 16 or 32 (pad with zero rows:
+ *             their similarity is 0).
+ *  n_canon    0: out receives the similarities [P, Q].  1 <= n_canon < Q:
+ *             out receives the relevancy (App. B, Eq. 9, temperature alpha
+ *             > 0) of the Q - n_canon queries (text rows n_canon..Q-1)
+ *             against the n_canon canonical phrases (rows 0..n_canon-1),
+ *             [P, Q - n_canon]; Q - n_canon a multiple of 4.
+ *  features   DEVICE bf16 [P, D] or NULL (the features are then not written).
+ *  feat_norm2 DEVICE float32 [P] or NULL: squared norms of the rounded rows.
+ *  out        DEVICE float32, 16-byte aligned.
+ *  workspace  DEVICE, >= scoup_decode_query_workspace_size(P, C, D, Q) bytes.
+ * The similarity's numerator rounds What and G (not F) to bf16, so it is not
+ * bit-equal to scoup_decode followed by scoup_similarity; both lie within the
+ * bf16 bounds of the exact FP64 value.  Asynchronous; errors as for
+ * scoup_decode. */
+int scoup_decode_query(const void* codes, int32_t codes_dtype, int64_t P, int32_t C, const float* codebook,
+                       int32_t D, const float* text, int32_t Q, int32_t n_canon, float alpha, void* features,
+                       float* feat_norm2, float* out, void* workspace, size_t ws_bytes, void* stream);
+
 /* Relevancy score of text queries (App. B, Eq. 9):
  *   R[p][q] = min_k exp(a s_q) / (exp(a s_q) + exp(a s_k))
  * from the similarities sim [P, ncols] (scoup_similarity output) whose first

@@ -129,6 +129,9 @@ PROTOS = {
     "scoup_selftest_gemm_timeout": (ct.c_int, [P, SZ, P]),
     "scoup_similarity_relevancy": (ct.c_int, [P, ct.c_int64, ct.c_int32, P, P, ct.c_int32, ct.c_int32, ct.c_float,
                                               P, P, SZ, P]),
+    "scoup_decode_query_workspace_size": (SZ, [ct.c_int64, ct.c_int32, ct.c_int32, ct.c_int32]),
+    "scoup_decode_query": (ct.c_int, [P, ct.c_int32, ct.c_int64, ct.c_int32, P, ct.c_int32, P, ct.c_int32,
+                                      ct.c_int32, ct.c_float, P, P, P, P, SZ, P]),
     "scoup_decode_backward_workspace_size": (SZ, [ct.c_int64, ct.c_int32, ct.c_int32]),
     "scoup_decode_backward": (ct.c_int, [P, ct.c_int32, ct.c_int64, ct.c_int32, P, ct.c_int32, P, P, SZ, P]),
     "scoup_decode_backward_fp32": (ct.c_int, [P, ct.c_int64, ct.c_int32, P, ct.c_int32, P, P]),

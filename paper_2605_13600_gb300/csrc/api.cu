@@ -972,6 +972,78 @@ int scoup_similarity_relevancy(const void* features, int64_t P, int32_t D, const
   return SCOUP_OK;
 }
 
+size_t scoup_decode_query_workspace_size(int64_t P, int32_t C, int32_t D, int32_t Q) {
+  if (P < 0 || C <= 0 || D <= 0 || Q <= 0) return 0;
+  return align_up(scoup_decode_workspace_size(P, C, D)) + align_up((size_t)Q * C * 2) + align_up((size_t)Q * 4);
+}
+
+// Workspace: [decode workspace: header, bf16 codebook^T, bf16 code chunk][bf16 Gt = (text C^T), Q x C][|t_q|].
+int scoup_decode_query(const void* codes, int32_t codes_dtype, int64_t P, int32_t C, const float* codebook,
+                       int32_t D, const float* text, int32_t Q, int32_t n_canon, float alpha, void* features,
+                       float* feat_norm2, float* out, void* workspace, size_t ws_bytes, void* stream) {
+  if (P < 0 || P > 0x7fffffffLL) return fail(SCOUP_ERR_INVALID_ARG, "P=%lld outside [0, 2^31)", (long long)P);
+  if (C < 8 || C % 8 || C > 4096) return fail(SCOUP_ERR_INVALID_ARG, "C=%d must be a multiple of 8 in [8, 4096]", C);
+  if (D < 16 || D % 16) return fail(SCOUP_ERR_INVALID_ARG, "D=%d must be a positive multiple of 16", D);
+  if (codes_dtype != 0 && codes_dtype != 1) return fail(SCOUP_ERR_INVALID_ARG, "codes_dtype must be 0 (f32) or 1 (bf16)");
+  if (Q != 16 && Q != 32) return fail(SCOUP_ERR_INVALID_ARG, "Q=%d: the fused query takes 16 or 32 text vectors", Q);
+  if (n_canon < 0 || n_canon >= Q || (n_canon > 0 && (Q - n_canon) % 4))
+    return fail(SCOUP_ERR_INVALID_ARG, "n_canon=%d: need 0 (similarity) or 1 <= n_canon < Q with Q - n_canon a multiple of 4", n_canon);
+  if (n_canon > 0 && (!(alpha > 0.0f) || alpha > 3.0e38f))
+    return fail(SCOUP_ERR_INVALID_ARG, "alpha must be positive and finite");
+  if (P > 0 && (!codes || !codebook || !text || !out)) return fail(SCOUP_ERR_INVALID_ARG, "NULL array");
+  if (((uintptr_t)codes & 15u) || ((uintptr_t)features & 15u) || ((uintptr_t)out & 15u))
+    return fail(SCOUP_ERR_INVALID_ARG, "codes, features and out must be 16-byte aligned");
+  const size_t need = scoup_decode_query_workspace_size(P, C, D, Q);
+  if (!workspace || ws_bytes < need) return fail(SCOUP_ERR_OOM, "workspace too small: need %zu bytes", need);
+  if (!gemm_tma_available()) return fail(SCOUP_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+  cudaStream_t st = (cudaStream_t)stream;
+  char* w = (char*)workspace;
+  WsHeader* hdr = (WsHeader*)w;
+  void* Bt = w + align_up(sizeof(WsHeader));
+  void* Abuf = (char*)Bt + align_up((size_t)D * C * 2);
+  void* Gt = w + align_up(scoup_decode_workspace_size(P, C, D));
+  float* tnorm = (float*)((char*)Gt + align_up((size_t)Q * C * 2));
+  cudaError_t e;
+  PhaseScope ps(SCOUP_PHASE_DECODE, st);
+  if ((e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st)) != cudaSuccess) return cuda_fail(e, "memset");
+  if (P == 0) return SCOUP_OK;
+  if ((e = launch_transpose_bf16(codebook, Bt, C, D, st)) != cudaSuccess) return cuda_fail(e, "codebook");
+  if ((e = launch_text_codebook(text, codebook, Q, C, D, Gt, tnorm, st)) != cudaSuccess)
+    return cuda_fail(e, "text x codebook");
+  const int64_t ldq = n_canon > 0 ? Q - n_canon : Q;
+  const int64_t chunk = codes_dtype == 1 ? P : decode_chunk_rows(P);
+  for (int64_t r0 = 0; r0 < P; r0 += chunk) {
+    const int64_t rows = P - r0 < chunk ? P - r0 : chunk;
+    const void* A;
+    if (codes_dtype == 0) {
+      if ((e = launch_f32_to_bf16((const float*)codes + r0 * C, Abuf, rows * C, st)) != cudaSuccess)
+        return cuda_fail(e, "convert");
+      A = Abuf;
+    } else {
+      A = (const char*)codes + (size_t)r0 * C * 2;
+    }
+    GemmEpi ep;
+    ep.M = (int)rows;
+    ep.N = D;
+    ep.K = C;
+    ep.mode = kOutBF16;
+    ep.out = features ? (char*)features + (size_t)r0 * D * 2 : nullptr;
+    ep.ldo = D;
+    ep.store = features ? 1 : 0;
+    ep.rownorm2 = feat_norm2 ? feat_norm2 + r0 : nullptr;
+    ep.colnorm = tnorm;
+    ep.n_canon = n_canon;
+    ep.alpha = alpha;
+    ep.sim_n = Q;
+    ep.sim_mode = n_canon > 0 ? kOutRel : kOutCos;
+    ep.sim_out = out + r0 * ldq;
+    ep.sim_ldo = ldq;
+    ep.status = &hdr->status;
+    if ((e = launch_gemm_bf16_query(A, Bt, Gt, ep, st)) != cudaSuccess) return cuda_fail(e, "decode + query gemm");
+  }
+  return SCOUP_OK;
+}
+
 size_t scoup_decode_backward_workspace_size(int64_t P, int32_t C, int32_t D) {
   if (P < 0 || C <= 0 || D <= 0) return 0;
   return align_up(sizeof(WsHeader)) + align_up((size_t)C * D * 2) + align_up((size_t)decode_chunk_rows(P) * D * 2);

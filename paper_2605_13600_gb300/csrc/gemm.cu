@@ -63,10 +63,40 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float x, float y) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
+// Position of a CTA's i-th unit.  Plain: units u = blockIdx.x + i gridDim.x
+// in row-block-major order.  Fused query: the CTA's row blocks
+// rb = blockIdx.x + j gridDim.x, each as its n_tiles column units followed by
+// the query unit (so one epilogue thread sees every column of its row).
+struct UnitPos {
+  int m0, n0;
+  bool query, valid;
+};
+
+template <int BN>
+__device__ __forceinline__ UnitPos unit_at(int i, int n_tiles, int m_blocks, bool fused) {
+  UnitPos p;
+  if (!fused) {
+    const int u = blockIdx.x + i * (int)gridDim.x;
+    p.m0 = (u / n_tiles) * BM;
+    p.n0 = (u % n_tiles) * BN;
+    p.query = false;
+    p.valid = u < m_blocks * n_tiles;
+  } else {
+    const int per = n_tiles + 1, rb = blockIdx.x + (i / per) * (int)gridDim.x, j = i % per;
+    p.m0 = rb * BM;
+    p.n0 = j * BN;
+    p.query = j == n_tiles;
+    p.valid = rb < m_blocks;
+  }
+  return p;
+}
+
 template <int BN>
 __global__ void __launch_bounds__(kGemmThreads, 1) gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                     const __grid_constant__ CUtensorMap tmB,
                                                                     const __grid_constant__ CUtensorMap tmO,
+                                                                    const __grid_constant__ CUtensorMap tmG,
+                                                                    const __grid_constant__ CUtensorMap tmS,
                                                                     GemmEpi ep) {
   using Cfg = GemmCfg<BN>;
   constexpr int kStages = Cfg::kStages;
@@ -76,9 +106,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_bf16_kernel(const __grid
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kt = (ep.K + BK - 1) / BK;
   const int n_tiles = (ep.N + BN - 1) / BN;
-  const int units = ((ep.M + BM - 1) / BM) * n_tiles;
+  const int m_blocks = (ep.M + BM - 1) / BM;
+  const bool fused = ep.sim_n > 0;
   constexpr uint32_t kBytesA = BM * BK * 2, kBytesB = BN * BK * 2;
+  const uint32_t kBytesG = (uint32_t)ep.sim_n * BK * 2;
   constexpr uint32_t idesc = ptx::idesc_bf16_f32(BM, BN);
+  const uint32_t idesc_q = ep.sim_n == 16 ? ptx::idesc_bf16_f32(BM, 16) : ptx::idesc_bf16_f32(BM, 32);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -95,6 +128,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_bf16_kernel(const __grid
     ptx::prefetch_tmap(&tmA);
     ptx::prefetch_tmap(&tmB);
     ptx::prefetch_tmap(&tmO);
+    if (fused) {
+      ptx::prefetch_tmap(&tmG);
+      ptx::prefetch_tmap(&tmS);
+    }
   }
   if (warp == 1) {
     ptx::tmem_alloc(&sm.tmem, Cfg::kTmemCols);
@@ -108,14 +145,17 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_bf16_kernel(const __grid
   if (warp == 0 && lane == 0) {
     // ---- TMA producer ----
     int it = 0;
-    for (int u = blockIdx.x; u < units && !sm.abort && !ep.stall_loads; u += gridDim.x) {
-      const int m0 = (u / n_tiles) * BM, n0 = (u % n_tiles) * BN;
+    for (int i = 0; !sm.abort && !ep.stall_loads; ++i) {
+      const UnitPos t = unit_at<BN>(i, n_tiles, m_blocks, fused);
+      if (!t.valid) break;
+      const CUtensorMap* mb = t.query ? &tmG : &tmB;
+      const int nb = t.query ? 0 : t.n0;
       for (int kb = 0; kb < kt; ++kb, ++it) {
         const int s = it % kStages;
         if (it >= kStages && !wait_or_abort(&sm.empty[s], ((it / kStages) - 1) & 1, &sm.abort, ep.status)) break;
-        ptx::mbar_arrive_expect_tx(&sm.full[s], kBytesA + kBytesB);
-        ptx::tma_load_2d(sm.a[s], &tmA, &sm.full[s], kb * BK, m0);
-        ptx::tma_load_2d(sm.b[s], &tmB, &sm.full[s], kb * BK, n0);
+        ptx::mbar_arrive_expect_tx(&sm.full[s], kBytesA + (t.query ? kBytesG : kBytesB));
+        ptx::tma_load_2d(sm.a[s], &tmA, &sm.full[s], kb * BK, t.m0);
+        ptx::tma_load_2d(sm.b[s], mb, &sm.full[s], kb * BK, nb);
       }
     }
     // wait (bounded) for the last copy issued into each stage before leaving
@@ -127,7 +167,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_bf16_kernel(const __grid
     // ---- MMA issuer ----
     int it = 0, local = 0;
     bool ok = true;
-    for (int u = blockIdx.x; u < units && ok && !sm.abort; u += gridDim.x, ++local) {
+    for (int i = 0; ok && !sm.abort; ++i, ++local) {
+      const UnitPos t = unit_at<BN>(i, n_tiles, m_blocks, fused);
+      if (!t.valid) break;
+      const uint32_t id = t.query ? idesc_q : idesc;
       const int b = local & 1, use = local >> 1;
       if (local >= 2 && !wait_or_abort(&sm.acc_empty[b], (use - 1) & 1, &sm.abort, ep.status)) break;
       ptx::tc_fence_after();
@@ -142,7 +185,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_bf16_kernel(const __grid
         const uint32_t sa = ptx::smem_u32(sm.a[s]), sb = ptx::smem_u32(sm.b[s]);
 #pragma unroll
         for (int k = 0; k < BK / 16; ++k)
-          ptx::mma_f16(d, ptx::smem_desc_k128(sa + k * 32), ptx::smem_desc_k128(sb + k * 32), idesc,
+          ptx::mma_f16(d, ptx::smem_desc_k128(sa + k * 32), ptx::smem_desc_k128(sb + k * 32), id,
                        (kb > 0 || k > 0) ? 1u : 0u);
         ptx::mma_commit(&sm.empty[s]);
       }
@@ -155,37 +198,48 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_bf16_kernel(const __grid
     // ---- epilogue ----
     const int q = warp & 3;  // TMEM lane quarter this warp may access
     constexpr int kCW = 64;  // bf16 columns per 128-byte chunk (32 for f32 output)
-    const bool f32out = ep.mode != kOutBF16;
-    const int cw = f32out ? 32 : kCW;
     int local = 0, sbuf = 0;
-    for (int u = blockIdx.x; u < units && !sm.abort; u += gridDim.x, ++local) {
-      const int m0 = (u / n_tiles) * BM, n0 = (u % n_tiles) * BN;
+    float ss_row = 0.0f;  // fused query: squared norm of the row's rounded outputs over its row block
+    for (int i = 0; !sm.abort; ++i, ++local) {
+      const UnitPos t = unit_at<BN>(i, n_tiles, m_blocks, fused);
+      if (!t.valid) break;
+      const int m0 = t.m0, n0 = t.query ? 0 : t.n0;
+      const int mode = t.query ? ep.sim_mode : ep.mode;
+      const bool f32out = mode != kOutBF16;
+      const int cw = f32out ? 32 : kCW;
+      const int ncols = t.query ? ep.sim_n : BN;  // accumulator columns of this unit (sim_n <= 32)
+      const int nlim = t.query ? ep.sim_n : ep.N;
+      const bool write = t.query || ep.store;
+      const CUtensorMap* mo = t.query ? &tmS : &tmO;
       const int b = local & 1, use = local >> 1;
       if (!wait_or_abort(&sm.acc_full[b], use & 1, &sm.abort, ep.status)) break;
       ptx::tc_fence_after();
       const int row = m0 + q * 32 + lane;
+      if (fused && !t.query && t.n0 == 0) ss_row = 0.0f;
       float rinv = 0.0f;
-      if ((ep.mode == kOutCos || ep.mode == kOutRel) && row < ep.M) {
-        const float rn = sqrtf(ep.rownorm2[row]);
+      if ((mode == kOutCos || mode == kOutRel) && row < ep.M) {
+        const float rn = sqrtf(t.query ? ss_row : ep.rownorm2[row]);
         rinv = rn < 1e-12f ? 0.0f : 1.0f / rn;
       }
       float ss = 0.0f;
       const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN);
-      for (int c0 = 0; c0 < BN; c0 += cw) {
+      for (int c0 = 0; c0 < ncols; c0 += cw) {
         float v[kCW];
         ptx::tmem_ld32(tbase + (uint32_t)c0, *reinterpret_cast<float(*)[32]>(&v[0]));
         if (!f32out) ptx::tmem_ld32(tbase + (uint32_t)(c0 + 32), *reinterpret_cast<float(*)[32]>(&v[32]));
-        if (c0 + cw >= BN) {
+        if (c0 + cw >= ncols) {
           // the accumulator is drained: the MMA warp may reuse it
           ptx::tc_fence_before();
           __syncwarp();
           if (lane == 0) ptx::mbar_arrive(&sm.acc_empty[b]);
         }
         // a box that starts past the last row or column stores nothing: skip it
-        if (n0 + c0 >= ep.N || m0 + q * 32 >= ep.M) continue;
+        if (n0 + c0 >= nlim || m0 + q * 32 >= ep.M) continue;
         unsigned char* buf = sm.out[q][sbuf];
-        if (lane == 0) ptx::bulk_wait_read<1>();  // this buffer's previous store has read it
-        __syncwarp();
+        if (write) {
+          if (lane == 0) ptx::bulk_wait_read<1>();  // this buffer's previous store has read it
+          __syncwarp();
+        }
         unsigned char* rowp = buf + lane * 128;
         if (!f32out) {
 #pragma unroll
@@ -195,41 +249,41 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_bf16_kernel(const __grid
             w.y = pack_bf16x2(v[8 * j + 2], v[8 * j + 3]);
             w.z = pack_bf16x2(v[8 * j + 4], v[8 * j + 5]);
             w.w = pack_bf16x2(v[8 * j + 6], v[8 * j + 7]);
-            *reinterpret_cast<uint4*>(rowp + ((j ^ (lane & 7)) << 4)) = w;
-            if (ep.rownorm2) {
+            if (write) *reinterpret_cast<uint4*>(rowp + ((j ^ (lane & 7)) << 4)) = w;
+            if (ep.rownorm2 || fused) {
               const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&w);
 #pragma unroll
-              for (int t = 0; t < 4; ++t) {
-                const float2 f = __bfloat1622float2(h[t]);
+              for (int t2 = 0; t2 < 4; ++t2) {
+                const float2 f = __bfloat1622float2(h[t2]);
                 ss = fmaf(f.x, f.x, fmaf(f.y, f.y, ss));
               }
             }
           }
         } else {
-          if (ep.mode == kOutCos || ep.mode == kOutRel) {
+          if (mode == kOutCos || mode == kOutRel) {
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              const int c = n0 + c0 + i;
-              const float cn = c < ep.N ? ep.colnorm[c] : 0.0f;
-              v[i] = (rinv == 0.0f || cn == 0.0f) ? 0.0f : v[i] * rinv / cn;
+            for (int c = 0; c < 32; ++c) {
+              const int col = n0 + c0 + c;
+              const float cn = col < nlim ? ep.colnorm[col] : 0.0f;
+              v[c] = (rinv == 0.0f || cn == 0.0f) ? 0.0f : v[c] * rinv / cn;
             }
           }
-          if (ep.mode == kOutRel) {
-            // Eq. 9 on the thread's whole row of similarities (N <= 32, one
-            // column tile): R_q = min_k 1 / (1 + e^{a (s_k - s_q)}) is the
-            // term of the largest canonical similarity; query q is column
-            // n_canon + q, staged at column q of the relevancy row
+          if (mode == kOutRel) {
+            // Eq. 9 on the thread's whole row of similarities (at most 32
+            // columns, one column tile): R_q = min_k 1 / (1 + e^{a (s_k - s_q)})
+            // is the term of the largest canonical similarity; query q is
+            // column n_canon + q, staged at column q of the relevancy row
             float smax = -INFINITY;
 #pragma unroll
-            for (int i = 0; i < 32; ++i)
-              if (i < ep.n_canon) smax = fmaxf(smax, v[i]);
+            for (int c = 0; c < 32; ++c)
+              if (c < ep.n_canon) smax = fmaxf(smax, v[c]);
             float* rowf = reinterpret_cast<float*>(rowp);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              const int q = i - ep.n_canon;
-              if (q >= 0 && i < ep.N) {
-                const float r = relevancy_term(ep.alpha, smax, v[i]);
-                rowf[(((q >> 2) ^ (lane & 7)) << 2) + (q & 3)] = r;
+            for (int c = 0; c < 32; ++c) {
+              const int qq = c - ep.n_canon;
+              if (qq >= 0 && c < nlim) {
+                const float r = relevancy_term(ep.alpha, smax, v[c]);
+                rowf[(((qq >> 2) ^ (lane & 7)) << 2) + (qq & 3)] = r;
               }
             }
           } else {
@@ -239,15 +293,21 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_bf16_kernel(const __grid
                   make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
           }
         }
+        if (!write) continue;
         ptx::fence_async_shared();
         __syncwarp();
         if (lane == 0) {
-          ptx::tma_store_2d(&tmO, buf, n0 + c0, m0 + q * 32);
+          ptx::tma_store_2d(mo, buf, n0 + c0, m0 + q * 32);
           ptx::bulk_commit();
         }
         sbuf ^= 1;
       }
-      if (!f32out && ep.rownorm2 && row < ep.M) atomicAdd(&ep.rownorm2[row], ss);
+      if (fused) {
+        if (!t.query) ss_row += ss;
+        else if (ep.rownorm2 && row < ep.M) ep.rownorm2[row] = ss_row;
+      } else if (!f32out && ep.rownorm2 && row < ep.M) {
+        atomicAdd(&ep.rownorm2[row], ss);
+      }
     }
     if (lane == 0) ptx::bulk_wait<0>();  // stores complete before the CTA leaves
     __syncwarp();
@@ -300,21 +360,36 @@ bool make_tmap(CUtensorMap* m, const void* ptr, CUtensorMapDataType dt, int esiz
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Gt (bf16 [sim_n, K]) is the fused query's operand; null without one.
 template <int BN>
-cudaError_t launch_bn(const void* A, const void* Bt, const GemmEpi& ep, cudaStream_t st) {
-  CUtensorMap ta, tb, to;
+cudaError_t launch_bn(const void* A, const void* Bt, const void* Gt, const GemmEpi& ep, cudaStream_t st) {
+  CUtensorMap ta, tb, to, tg, ts;
   const bool f32out = ep.mode != kOutBF16;
+  const bool fused = ep.sim_n > 0;
   if (!make_tmap(&ta, A, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ep.M, ep.K, BK, BM) ||
-      !make_tmap(&tb, Bt, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ep.N, ep.K, BK, BN) ||
-      !(f32out ? make_tmap(&to, ep.out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ep.M, ep.ldo, 32, 32)
-               : make_tmap(&to, ep.out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ep.M, ep.ldo, 64, 32)))
+      !make_tmap(&tb, Bt, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ep.N, ep.K, BK, BN))
     return cudaErrorInvalidValue;
+  // without stored rows (fused query, store = 0) the output map is never used:
+  // it is encoded on the operand Bt so that it is valid
+  if (!ep.store) to = tb;
+  else if (!(f32out ? make_tmap(&to, ep.out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ep.M, ep.ldo, 32, 32)
+                    : make_tmap(&to, ep.out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ep.M, ep.ldo, 64, 32)))
+    return cudaErrorInvalidValue;
+  if (fused) {
+    if (!make_tmap(&tg, Gt, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ep.sim_n, ep.K, BK, ep.sim_n) ||
+        !make_tmap(&ts, ep.sim_out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ep.M, ep.sim_ldo, 32, 32))
+      return cudaErrorInvalidValue;
+  } else {
+    tg = tb;  // unused
+    ts = to;
+  }
   const size_t smem = sizeof(GemmSmem<BN>) + 1024;
   cudaError_t e = cudaFuncSetAttribute(gemm_bf16_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int64_t units = ((int64_t)(ep.M + BM - 1) / BM) * ((ep.N + BN - 1) / BN);
+  const int64_t m_blocks = (ep.M + BM - 1) / BM;
+  const int64_t units = fused ? m_blocks : m_blocks * ((ep.N + BN - 1) / BN);
   const int grid = (int)(units < num_sms() ? units : num_sms());
-  gemm_bf16_kernel<BN><<<grid, kGemmThreads, smem, st>>>(ta, tb, to, ep);
+  gemm_bf16_kernel<BN><<<grid, kGemmThreads, smem, st>>>(ta, tb, to, tg, ts, ep);
   g_launches += 1;
   return cudaGetLastError();
 }
@@ -369,10 +444,47 @@ cudaError_t launch_gemm_bf16(const void* A, const void* Bt, const GemmEpi& ep, c
   if (ep.M <= 0 || ep.N <= 0) return cudaSuccess;
   // bf16 output is read back from TMEM 64 columns at a time: BN >= 64 (the
   // columns past N are the zero fill of the Bt tile)
-  if (ep.N <= 32 && ep.mode != kOutBF16) return launch_bn<32>(A, Bt, ep, st);
-  if (ep.N <= 64) return launch_bn<64>(A, Bt, ep, st);
-  if (ep.N <= 128) return launch_bn<128>(A, Bt, ep, st);
-  return launch_bn<256>(A, Bt, ep, st);
+  if (ep.sim_n) return cudaErrorInvalidValue;  // launch_gemm_bf16_query
+  if (ep.N <= 32 && ep.mode != kOutBF16) return launch_bn<32>(A, Bt, nullptr, ep, st);
+  if (ep.N <= 64) return launch_bn<64>(A, Bt, nullptr, ep, st);
+  if (ep.N <= 128) return launch_bn<128>(A, Bt, nullptr, ep, st);
+  return launch_bn<256>(A, Bt, nullptr, ep, st);
+}
+
+cudaError_t launch_gemm_bf16_query(const void* A, const void* Bt, const void* Gt, const GemmEpi& ep,
+                                   cudaStream_t st) {
+  if (ep.M <= 0 || ep.N <= 0) return cudaSuccess;
+  if (ep.mode != kOutBF16 || (ep.sim_n != 16 && ep.sim_n != 32) || !Gt || !ep.sim_out ||
+      (ep.sim_mode != kOutCos && ep.sim_mode != kOutRel) || (ep.store && !ep.out))
+    return cudaErrorInvalidValue;
+  if (ep.N <= 64) return launch_bn<64>(A, Bt, Gt, ep, st);
+  if (ep.N <= 128) return launch_bn<128>(A, Bt, Gt, ep, st);
+  return launch_bn<256>(A, Bt, Gt, ep, st);
+}
+
+// One warp per (q, c): Gt[q][c] = bf16(sum_d text[q][d] codebook[c][d]) with
+// FP32 sums; the warps of c = 0 also write |text_q|.
+__global__ void text_codebook_kernel(const float* __restrict__ text, const float* __restrict__ codebook, int Q,
+                                     int C, int D, __nv_bfloat16* __restrict__ Gt, float* __restrict__ tnorm) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; w < (int64_t)Q * C;
+       w += (int64_t)gridDim.x * blockDim.x / 32) {
+    const int qi = (int)(w / C), c = (int)(w - (int64_t)qi * C);
+    float dot = 0.0f, sq = 0.0f;
+    for (int d = lane; d < D; d += 32) {
+      const float t = text[(int64_t)qi * D + d];
+      dot = fmaf(t, codebook[(int64_t)c * D + d], dot);
+      sq = fmaf(t, t, sq);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      dot += __shfl_xor_sync(0xffffffffu, dot, off);
+      sq += __shfl_xor_sync(0xffffffffu, sq, off);
+    }
+    if (lane == 0) {
+      Gt[w] = __float2bfloat16_rn(dot);
+      if (c == 0) tnorm[qi] = sqrtf(sq);
+    }
+  }
 }
 
 cudaError_t launch_f32_to_bf16(const float* x, void* y, int64_t n, cudaStream_t st) {
@@ -384,6 +496,15 @@ cudaError_t launch_f32_to_bf16(const float* x, void* y, int64_t n, cudaStream_t 
 
 cudaError_t launch_transpose_bf16(const float* B, void* Bt, int Cdim, int D, cudaStream_t st) {
   transpose_bf16_kernel<<<blocks_for((int64_t)Cdim * D, 256), 256, 0, st>>>(B, (__nv_bfloat16*)Bt, Cdim, D);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_text_codebook(const float* text, const float* codebook, int Q, int C, int D, void* Gt,
+                                 float* tnorm, cudaStream_t st) {
+  if (Q <= 0 || C <= 0) return cudaSuccess;
+  text_codebook_kernel<<<blocks_for((int64_t)Q * C * 32, 256), 256, 0, st>>>(text, codebook, Q, C, D,
+                                                                             (__nv_bfloat16*)Gt, tnorm);
   g_launches += 1;
   return cudaGetLastError();
 }

@@ -305,8 +305,25 @@ struct GemmEpi {
   float alpha = 0.0f;    // kOutRel: softmax temperature of Eq. 9
   int* status;
   int stall_loads = 0;   // self-test only: the producer issues no loads, so the bounded waits run out
+  // Fused query (mode kOutBF16): every CTA takes whole row blocks and, after
+  // a block's N columns, one more unit of sim_n (16 or 32) columns against
+  // the operand Gt (bf16 [sim_n, K]); that unit's epilogue writes, with the
+  // row's squared norm summed over the block's rounded features, the cosine
+  // (sim_mode kOutCos, colnorm = the sim_n column norms) or the relevancy
+  // (kOutRel, with n_canon and alpha) to sim_out [M, sim_ldo] (f32).
+  int sim_n = 0;
+  int sim_mode = 0;
+  void* sim_out = nullptr;
+  int64_t sim_ldo = 0;
+  int store = 1;  // 0: the kOutBF16 rows are not written (their norms and the fused unit still are)
 };
 cudaError_t launch_gemm_bf16(const void* A, const void* Bt, const GemmEpi& ep, cudaStream_t st);
+// launch_gemm_bf16 with the fused query unit (ep.sim_n > 0; Gt bf16 [sim_n, K]).
+cudaError_t launch_gemm_bf16_query(const void* A, const void* Bt, const void* Gt, const GemmEpi& ep,
+                                   cudaStream_t st);
+// Gt[q][c] = bf16(sum_d text[q][d] codebook[c][d]) (FP32 sums) and tnorm[q] = |text_q| (FP32).
+cudaError_t launch_text_codebook(const float* text, const float* codebook, int Q, int C, int D, void* Gt,
+                                 float* tnorm, cudaStream_t st);
 cudaError_t launch_f32_to_bf16(const float* x, void* y, int64_t n, cudaStream_t st);
 cudaError_t launch_transpose_bf16(const float* B, void* Bt, int Cdim, int D, cudaStream_t st);
 cudaError_t launch_row_norm_bf16(const void* X, int64_t R, int D, float* out, int squared, cudaStream_t st);

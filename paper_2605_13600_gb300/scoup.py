@@ -400,6 +400,46 @@ def scoup_similarity_relevancy(features, text, n_canon: int, R, alpha: float = 1
     return workspace
 
 
+def scoup_decode_query_workspace_size(P: int, C: int, D: int, Q: int) -> int:
+    return int(load().scoup_decode_query_workspace_size(P, C, D, Q))
+
+
+def scoup_decode_query(codes, codebook, text, out, n_canon: int = 0, alpha: float = 10.0, features=None,
+                       feat_norm2=None, workspace=None, stream=None):
+    """Eq. 8 decode with the App. B query in the same GEMM: features = codes @
+    codebook (bf16 [P, D], or not written when None) and out = the cosine
+    similarity [P, Q] to the float32 text vectors [Q, D] (n_canon = 0) or the
+    relevancy [P, Q - n_canon] of Eq. 9 (n_canon canonical phrases first).
+    Q is 16 or 32.  Returns the workspace."""
+    import torch
+    if codes.dtype not in (torch.float32, torch.bfloat16):
+        raise TypeError("codes must be float32 or bfloat16")
+    _need(codes, codes.dtype, "codes")
+    _need(codebook, torch.float32, "codebook")
+    _need(text, torch.float32, "text")
+    _need(out, torch.float32, "out")
+    _need(features, torch.bfloat16, "features")
+    _need(feat_norm2, torch.float32, "feat_norm2")
+    P, C = codes.shape
+    D = codebook.shape[1]
+    Q = text.shape[0]
+    if codebook.shape[0] != C or text.shape[1] != D or tuple(out.shape) != (P, Q - int(n_canon)):
+        raise ValueError("shape mismatch")
+    if features is not None and tuple(features.shape) != (P, D):
+        raise ValueError("features shape mismatch")
+    if feat_norm2 is not None and feat_norm2.numel() < P:
+        raise ValueError("feat_norm2 too short")
+    if workspace is None:
+        workspace = torch.empty(scoup_decode_query_workspace_size(P, C, D, Q), dtype=torch.uint8,
+                                device=codes.device)
+    _need(workspace, torch.uint8, "workspace")
+    check(load().scoup_decode_query(_ptr(codes), 1 if codes.dtype == torch.bfloat16 else 0, P, C, _ptr(codebook),
+                                    D, _ptr(text), Q, int(n_canon), float(alpha), _ptr(features),
+                                    _ptr(feat_norm2), _ptr(out), _ptr(workspace), workspace.numel(),
+                                    _stream(stream)))
+    return workspace
+
+
 def scoup_decode_backward(dF, codebook, dcodes, workspace=None, stream=None):
     """dcodes [P, C] = dF [P, D] @ codebook[C, D]^T on the tensor cores (bf16
     operands, FP32 accumulation); dF float32 or bf16.  Returns the workspace."""
@@ -822,5 +862,5 @@ __all__ = ["ScoupError", "SCOUP_ACCUM_CONTINUE", "SCOUP_ACCUM_COMPENSATED", "sce
            "SCOUP_BATCH_EAGER", "LevelUplift", "scoup_selftest_gemm_timeout", "scoup_selftest_red_throughput", "scoup_topk_entropy", "scoup_entropy_filter", "scoup_entropy_filter_workspace_size", "scoup_relevancy",
            "scoup_render_decode_workspace_size", "scoup_render_decode_fused",
            "scoup_uplift_host_maps_workspace_size", "scoup_uplift_host_maps",
-           "scoup_similarity_relevancy", "scoup_decode_backward", "scoup_decode_backward_fp32",
+           "scoup_similarity_relevancy", "scoup_decode_query", "scoup_decode_query_workspace_size", "scoup_decode_backward", "scoup_decode_backward_fp32",
            "scoup_region_l2_grad"]
