@@ -73,6 +73,8 @@ struct RenderMmaSmem {
   unsigned long long cnt[2];
 };
 
+static_assert(sizeof(ChunkBuf) * 2 >= kMWarps * 16384, "the epilogue stages 16 KB per warp in the chunk buffers");
+
 // TMEM columns: a power of two holding two halves of Np columns, each half a
 // multiple of 32 columns (the width of one tcgen05.ld).
 __host__ __device__ inline uint32_t mma_tmem_cols(int Np) {
@@ -390,20 +392,65 @@ __global__ void __launch_bounds__(kMThreads, 1) render_mma_kernel(
   const bool bad = (__syncthreads_or(!fin_ok) != 0) || aborted;
   ptx::tc_fence_after();
 
-  // epilogue: each thread reads its own pixel's row (TMEM lane) and writes it once
+  // epilogue: each thread reads its own pixel's row (TMEM lane)
   const int q = warp & 3;
   const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)half * half_cols;
   const int64_t pix = (int64_t)py * cam.width + px;
   const bool have = ((acc_init >> half) & 1u) && !bad;  // uniform over the warp
-  for (int c0 = 0; c0 < Np; c0 += 32) {
-    float v[32];
-    if (have) {
-      ptx::tmem_ld32(tb + (uint32_t)c0, v);
-    } else {
+  // Rows that split into 512-byte pieces (bf16 with C a multiple of 256, FP32
+  // with C a multiple of 128) go through shared memory: the warp stages one
+  // piece of each of its 32 pixel rows (16-byte chunks XOR-swizzled by row,
+  // so neither the staging stores nor the reads conflict) in the chunk
+  // buffers, free once the last MMA has completed, and writes every row's
+  // piece with one coalesced warp store; other rows are stored per thread.
+  const int esz = out_bf16 ? 2 : 4;
+  const int piece_cols = 512 / esz;
+  if (!bad && C == Np && C % piece_cols == 0 && ((uintptr_t)out & 15u) == 0) {
+    unsigned char* stg = reinterpret_cast<unsigned char*>(&sm.buf[0]) + warp * 16384;
+    unsigned char* orow = reinterpret_cast<unsigned char*>(out) + pix * (int64_t)C * esz;
+    for (int p0 = 0; p0 < Np; p0 += piece_cols) {
+      for (int c0 = p0; c0 < p0 + piece_cols; c0 += 32) {
+        float v[32];
+        if (have) {
+          ptx::tmem_ld32(tb + (uint32_t)c0, v);
+        } else {
 #pragma unroll
-      for (int i = 0; i < 32; ++i) v[i] = 0.0f;
+          for (int i = 0; i < 32; ++i) v[i] = 0.0f;
+        }
+        const int k0 = (c0 - p0) * esz / 16;  // first 16-byte chunk of these columns in the piece
+        if (out_bf16) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            *reinterpret_cast<uint4*>(stg + lane * 512 + (((k0 + j) ^ lane) & 31) * 16) =
+                make_uint4(pack2_bf16(v[8 * j], v[8 * j + 1]), pack2_bf16(v[8 * j + 2], v[8 * j + 3]),
+                           pack2_bf16(v[8 * j + 4], v[8 * j + 5]), pack2_bf16(v[8 * j + 6], v[8 * j + 7]));
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            *reinterpret_cast<float4*>(stg + lane * 512 + (((k0 + j) ^ lane) & 31) * 16) =
+                make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        }
+      }
+      __syncwarp();
+      for (int r = 0; r < 32; ++r) {
+        const uint4 val = *reinterpret_cast<const uint4*>(stg + r * 512 + ((lane ^ r) & 31) * 16);
+        const unsigned long long ra = __shfl_sync(0xffffffffu, (unsigned long long)(uintptr_t)orow, r);
+        if (__shfl_sync(0xffffffffu, inside, r))
+          *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>((uintptr_t)ra) + p0 * esz + lane * 16) = val;
+      }
+      __syncwarp();
     }
-    if (inside && !bad) store_cols(out, pix, C, c0, out_bf16 != 0, v);
+  } else {
+    for (int c0 = 0; c0 < Np; c0 += 32) {
+      float v[32];
+      if (have) {
+        ptx::tmem_ld32(tb + (uint32_t)c0, v);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = 0.0f;
+      }
+      if (inside && !bad) store_cols(out, pix, C, c0, out_bf16 != 0, v);
+    }
   }
   if (inside) {
     if (out_T) out_T[pix] = T;
