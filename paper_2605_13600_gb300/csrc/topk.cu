@@ -3,23 +3,24 @@
 //
 // One warp per accumulator row.  Lane l holds entries l, l+32, l+64, ... in
 // registers; each of the K rounds picks the largest remaining positive entry
-// (ties to the lower atom index) with a butterfly arg-max across the warp.
-// The row is read once from HBM (coalesced), which makes this kernel HBM-bound.
+// (ties to the lower atom index): every lane offers its best remaining entry,
+// one warp reduction takes the maximum of the offered values' bit patterns
+// (positive floats order as their bits) and a second the lowest atom index
+// among the lanes that offer that maximum.  The row is read once from HBM
+// (coalesced).
 // With a compensation array (the compensated uplift) each entry is the FP32
 // sum of the running sum and its compensation.  Optionally the same pass
 // writes the entropy of the row's coefficient distribution,
 // H = -sum p log p with p = w / sum w over the positive entries (0 for an
-// empty row), computed as log S - (sum w log w) / S.
+// empty row), computed as log S - (sum w log w) / S; the per-entry logarithms
+// use the fast intrinsic (absolute error about 1e-6, so H is off by at most
+// that much: far inside the FP32 tolerance of the entropy).
 #include "scoup_internal.cuh"
 
 namespace scoup {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-
-__device__ __forceinline__ bool better(float v, int j, float ov, int oj) {
-  return v > ov || (v == ov && j < oj);
-}
 
 template <int VPL>
 __global__ void __launch_bounds__(256) topk_kernel(const float* __restrict__ acc, const float* __restrict__ comp,
@@ -42,7 +43,7 @@ __global__ void __launch_bounds__(256) topk_kernel(const float* __restrict__ acc
       for (int k = 0; k < VPL; ++k)
         if (v[k] > 0.0f) {
           S += v[k];
-          WL = fmaf(v[k], logf(v[k]), WL);
+          WL = fmaf(v[k], __logf(v[k]), WL);
         }
       for (int off = 16; off > 0; off >>= 1) {
         S += __shfl_xor_sync(kFull, S, off);
@@ -62,12 +63,10 @@ __global__ void __launch_bounds__(256) topk_kernel(const float* __restrict__ acc
       for (int k = 0; k < VPL; ++k) {
         if (!((taken >> k) & 1u) && v[k] > bv) { bv = v[k]; bj = lane + 32 * k; }
       }
-      for (int off = 16; off > 0; off >>= 1) {
-        const float ov = __shfl_xor_sync(kFull, bv, off);
-        const int oj = __shfl_xor_sync(kFull, bj, off);
-        if (better(ov, oj, bv, bj)) { bv = ov; bj = oj; }
-      }
-      if (!(bv > 0.0f)) break;
+      const unsigned mb = __reduce_max_sync(kFull, __float_as_uint(bv));
+      if (mb == 0u) break;  // no positive entry left
+      bj = __reduce_min_sync(kFull, __float_as_uint(bv) == mb ? bj : 0x7fffffff);
+      bv = __uint_as_float(mb);
       if ((bj & 31) == lane) taken |= 1u << (bj >> 5);
       if (lane == 0) { orow_i[r] = bj; orow_v[r] = bv; }
       sum += bv;
