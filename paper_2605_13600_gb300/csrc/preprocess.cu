@@ -112,15 +112,19 @@ __global__ void __launch_bounds__(256) preprocess_kernel(
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     ushort4 rect = make_ushort4(0, 0, 0, 0);
+    // every input of the Gaussian is loaded up front, so that all its loads
+    // are in flight together (one memory round trip instead of two)
     const float m0 = means[3 * i], m1 = means[3 * i + 1], m2 = means[3 * i + 2];
+    const float4 q = *reinterpret_cast<const float4*>(quats + 4 * i);
+    const float s0 = scales[3 * i], s1 = scales[3 * i + 1], s2 = scales[3 * i + 2];
+    const float op_i = opacity[i], tau_i = tau[i];
+    const int32_t orig_i = orig[i];
     const float* W = cam.vm;
     float t0 = W[0] * m0 + W[1] * m1 + W[2] * m2 + W[3];
     float t1 = W[4] * m0 + W[5] * m1 + W[6] * m2 + W[7];
     float t2 = W[8] * m0 + W[9] * m1 + W[10] * m2 + W[11];
     depth_bits[i] = __float_as_uint(t2);
     if (t2 > 0.2f) {
-      const float4 q = *reinterpret_cast<const float4*>(quats + 4 * i);
-      const float s0 = scales[3 * i], s1 = scales[3 * i + 1], s2 = scales[3 * i + 2];
       float qn = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
       float inv = 1.0f / sqrtf(qn);
       float w = q.x * inv, x = q.y * inv, y = q.z * inv, z = q.w * inv;
@@ -185,14 +189,13 @@ __global__ void __launch_bounds__(256) preprocess_kernel(
         if (xhi > xlo && yhi > ylo) {
           ProjRec pr;
           pr.a = make_float4(mx, my, -0.5f * con_a, -con_b);
-          pr.b = make_float4(-0.5f * con_c, opacity[i], tau[i], log2f(opacity[i]));
-          proj[orig[i]] = pr;
+          pr.b = make_float4(-0.5f * con_c, op_i, tau_i, log2f(op_i));
+          proj[orig_i] = pr;
           // Binning lists only the tiles of the rectangle that also meet the
           // bounding box of the alpha >= 1/255 ellipse {d : power(d) >= tau}:
           // half-widths sqrt(-2 tau (A^-1)_xx), sqrt(-2 tau (A^-1)_yy) with
           // A = [[-2qa, -qb], [-qb, -2qc]], widened by 0.1% + 0.5 px so no
           // pixel centre that passes the alpha test is left out.
-          const float tau_i = tau[i];
           int lx0 = xhi, lx1 = xlo, ly0 = yhi, ly1 = ylo;  // empty unless tau < 0
           if (tau_i < 0.0f) {
             const float A00 = con_a, A11 = con_c, A01 = con_b;  // = -2qa, -2qc, -qb
