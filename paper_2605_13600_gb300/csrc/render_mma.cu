@@ -34,13 +34,15 @@
 namespace scoup {
 namespace {
 
-constexpr int kMThreads = 256;  // one thread per pixel of the 16 x 16 tile
+constexpr int kMThreads = 256;  // walkers: one thread per pixel of the 16 x 16 tile
 constexpr int kMWarps = kMThreads / 32;
+constexpr int kMmaWarp = kMWarps;               // a ninth warp issues the tensor-core MMAs
+constexpr int kCtaThreads = kMThreads + 32;
 constexpr int kChunk = 32;      // Gaussians per chunk (contraction depth of one round of MMAs)
 constexpr int kMaxN = 256;      // widest code row: two 128-lane halves of N FP32 TMEM columns
 constexpr int kMaxK = 16;       // largest Top-K staged per window
 constexpr uint32_t kWaitIters = 1u << 22;
-using MOrder = OrderSmem<256, 10>;
+using MOrder = OrderSmem<256, 10, kMThreads>;  // the walkers order alone (named barrier 1)
 
 // Operand tiles are K-major without swizzle, built from 8-row x 16-byte core
 // matrices: the 4 core matrices of an 8-row group (32 bf16 along K) are
@@ -66,10 +68,12 @@ struct RenderMmaSmem {
   float4 rec_b[MOrder::kWin];
   float code_val[kMaxK * MOrder::kWin];  // entry-major: [k][window position]
   short code_idx[kMaxK * MOrder::kWin];
-  uint64_t mma_done[2];
+  uint64_t mma_done[2];  // per chunk buffer: the MMAs that read it have completed
+  uint64_t ready[2];     // per chunk buffer: the walkers have written E and W (and ctl)
   uint64_t fin;
   uint32_t tmem;
   int any_e[kMWarps];
+  int ctl[2][3];  // per chunk buffer: MMAs for pixel half 0, half 1; stop
   unsigned long long cnt[2];
 };
 
@@ -201,9 +205,22 @@ __device__ __forceinline__ void store_cols(void* __restrict__ out, int64_t pix, 
   }
 }
 
+// Barriers of the 256 walkers (named barrier 1; the MMA warp is not in it).
+__device__ __forceinline__ void walkers_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ bool walkers_or(bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\tbar.red.or.pred po, 1, 256, pi;\n\t"
+      "selp.u32 %0, 1, 0, po;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)p)
+      : "memory");
+  return r != 0u;
+}
+
 // One CTA per tile; one CTA per SM (the accumulator takes the SM's 512 TMEM
 // columns at C = 256, and the shared memory keeps a second CTA out).
-__global__ void __launch_bounds__(kMThreads, 1) render_mma_kernel(
+__global__ void __launch_bounds__(kCtaThreads, 1) render_mma_kernel(
     CamArgs cam, const ProjRec* __restrict__ proj, const unsigned long long* __restrict__ keys,
     const uint32_t* __restrict__ tile_start, int slot, const int32_t* __restrict__ topk_idx,
     const float* __restrict__ topk_val, int K, int C, void* __restrict__ out, int out_bf16,
@@ -224,6 +241,8 @@ __global__ void __launch_bounds__(kMThreads, 1) render_mma_kernel(
   if (tid == 0) {
     ptx::mbar_init(&sm.mma_done[0], 1);
     ptx::mbar_init(&sm.mma_done[1], 1);
+    ptx::mbar_init(&sm.ready[0], kMThreads);
+    ptx::mbar_init(&sm.ready[1], kMThreads);
     ptx::mbar_init(&sm.fin, 1);
     ptx::fence_mbar_init();
     sm.cnt[0] = sm.cnt[1] = 0ull;
@@ -232,6 +251,53 @@ __global__ void __launch_bounds__(kMThreads, 1) render_mma_kernel(
     ptx::tmem_alloc(&sm.tmem, cols);
     ptx::tmem_relinquish();
   }
+  ptx::tc_fence_before();
+  __syncthreads();  // the whole CTA: TMEM address and mbarriers are visible
+  ptx::tc_fence_after();
+  const uint32_t tmem = sm.tmem;
+
+  if (warp == kMmaWarp) {
+    // ---- MMA warp: one thread issues each chunk's MMAs once the walkers
+    // have written it, and commits every chunk (also one without MMAs) to its
+    // buffer's mma_done, so the walkers never run two chunks ahead of it ----
+    if (lane == 0) {
+      const uint32_t idesc = ptx::idesc_bf16_f32(128, Np);
+      unsigned acc_init = 0u;  // bit h: pixel half h has received an MMA
+      for (int chunk = 0;; ++chunk) {
+        const int b = chunk & 1;
+        if (!ptx::mbar_wait_bounded(&sm.ready[b], (uint32_t)(chunk >> 1) & 1u, kWaitIters)) {
+          atomicOr(&hdr->status, kStatTimeout);
+          break;
+        }
+        const int any0 = *(volatile int*)&sm.ctl[b][0], any1 = *(volatile int*)&sm.ctl[b][1];
+        const int stop = *(volatile int*)&sm.ctl[b][2];
+        if (stop) break;
+        ptx::tc_fence_after();
+        const ChunkBuf& cb = sm.buf[b];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (!(h ? any1 : any0)) continue;
+          const uint32_t d = tmem + (uint32_t)h * half_cols;
+#pragma unroll
+          for (int pass = 0; pass < 3; ++pass) {
+            const uint32_t ea = ptx::smem_u32(cb.e[pass == 2 ? 1 : 0][h]);
+            const uint32_t wb = ptx::smem_u32(cb.w[pass == 1 ? 1 : 0]);
+#pragma unroll
+            for (int ks = 0; ks < kChunk / 16; ++ks)
+              ptx::mma_f16(d, ptx::smem_desc_kmajor_none(ea + ks * 2 * kLBO, kLBO, kSBO),
+                           ptx::smem_desc_kmajor_none(wb + ks * 2 * kLBO, kLBO, kSBO), idesc,
+                           (((acc_init >> h) & 1u) || pass > 0 || ks > 0) ? 1u : 0u);
+          }
+        }
+        acc_init |= (any0 ? 1u : 0u) | (any1 ? 2u : 0u);
+        ptx::mma_commit(&sm.mma_done[b]);
+      }
+      // arrives once every MMA issued above has completed
+      ptx::mma_commit(&sm.fin);
+    }
+    __syncwarp();
+  } else {
+  // ---- walkers ----
   const int px = tx * kTile + (tid & (kTile - 1)), py = ty * kTile + (tid >> 4);
   const bool inside = px < cam.width && py < cam.height;
   const int half = tid >> 7, row = tid & 127;  // E row and TMEM lane of this pixel
@@ -239,15 +305,13 @@ __global__ void __launch_bounds__(kMThreads, 1) render_mma_kernel(
   int last = 0;
   bool done = !inside;
   const OrderBuckets bk = order_buckets<MOrder>(hdr, slot);
-  ptx::tc_fence_before();
-  order_init<MOrder, 16>(sm.ord, tkeys, n, bk);  // ends with a barrier: TMEM address and mbarriers are visible
-  ptx::tc_fence_after();
-  const uint32_t tmem = sm.tmem;
+  order_init<MOrder, 16>(sm.ord, tkeys, n, bk);
 
   unsigned n_eval = 0, n_contrib = 0;
   unsigned acc_init = 0u;  // bit h: pixel half h has received an MMA
-  // thread 0: per chunk buffer b, bit b of `pending` = a commit not yet
-  // waited for, bit b of `phase` = parity of that commit's completion
+  // thread 0: per chunk buffer b, bit b of `pending` = a chunk handed to the
+  // MMA warp whose commit has not been waited for, bit b of `phase` = parity
+  // of that commit's completion
   unsigned pending = 0u, phase = 0u;
   bool aborted = false, all_done = false;
   int chunk = 0, wbase = 0;
@@ -296,7 +360,7 @@ __global__ void __launch_bounds__(kMThreads, 1) render_mma_kernel(
           sm.code_val[k * MOrder::kWin + j] = av[k];
         }
     }
-    __syncthreads();
+    walkers_sync();
     for (int j0 = 0; j0 < m; j0 += kChunk, ++chunk) {
       const int b = chunk & 1;
       ChunkBuf& cb = sm.buf[b];
@@ -308,7 +372,7 @@ __global__ void __launch_bounds__(kMThreads, 1) render_mma_kernel(
         phase ^= 1u << b;
         if (timed_out) atomicOr(&hdr->status, kStatTimeout);
       }
-      if (__syncthreads_or(timed_out)) {
+      if (walkers_or(timed_out)) {
         aborted = true;
         break;
       }
@@ -324,7 +388,7 @@ __global__ void __launch_bounds__(kMThreads, 1) render_mma_kernel(
                                   cb.e[1][half], row);
       const unsigned wany = __ballot_sync(0xffffffffu, any);
       if (lane == 0) sm.any_e[warp] = wany != 0u;
-      __syncthreads();
+      walkers_sync();
       const bool any0 = (sm.any_e[0] | sm.any_e[1] | sm.any_e[2] | sm.any_e[3]) != 0;
       const bool any1 = (sm.any_e[4] | sm.any_e[5] | sm.any_e[6] | sm.any_e[7]) != 0;
       if (any0 || any1) {
@@ -349,47 +413,47 @@ __global__ void __launch_bounds__(kMThreads, 1) render_mma_kernel(
         }
       }
       ptx::fence_async_shared();  // E and W are read by the tensor core (async proxy)
-      const bool open = __syncthreads_or(!done) != 0;
-      if (tid == 0 && (any0 || any1)) {
-        ptx::tc_fence_after();
-        const uint32_t idesc = ptx::idesc_bf16_f32(128, Np);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (!(h ? any1 : any0)) continue;
-          const uint32_t d = tmem + (uint32_t)h * half_cols;
-#pragma unroll
-          for (int pass = 0; pass < 3; ++pass) {
-            const uint32_t ea = ptx::smem_u32(cb.e[pass == 2 ? 1 : 0][h]);
-            const uint32_t wb = ptx::smem_u32(cb.w[pass == 1 ? 1 : 0]);
-#pragma unroll
-            for (int ks = 0; ks < kChunk / 16; ++ks)
-              ptx::mma_f16(d, ptx::smem_desc_kmajor_none(ea + ks * 2 * kLBO, kLBO, kSBO),
-                           ptx::smem_desc_kmajor_none(wb + ks * 2 * kLBO, kLBO, kSBO), idesc,
-                           (((acc_init >> h) & 1u) || pass > 0 || ks > 0) ? 1u : 0u);
-          }
-        }
-        ptx::mma_commit(&sm.mma_done[b]);
+      const bool open = walkers_or(!done);
+      // hand the chunk to the MMA warp (thread 0's control words are
+      // published by its own arrival)
+      if (tid == 0) {
+        sm.ctl[b][0] = any0 ? 1 : 0;
+        sm.ctl[b][1] = any1 ? 1 : 0;
+        sm.ctl[b][2] = 0;
         pending |= 1u << b;
       }
+      ptx::mbar_arrive(&sm.ready[b]);
       acc_init |= (any0 ? 1u : 0u) | (any1 ? 2u : 0u);
       if (!open) {
         all_done = true;
+        ++chunk;  // the stop goes to the next chunk
         break;
       }
     }
     wbase += m;
   }
 
-  // every MMA has completed before the accumulator is read and TMEM freed
+  // stop the MMA warp: the stop travels on the next chunk's buffer, once the
+  // MMA warp has taken that buffer's previous chunk; then every MMA has
+  // completed before the accumulator is read and TMEM freed
   bool fin_ok = true;
+  {
+    const int b = chunk & 1;
+    if (tid == 0) {
+      if ((pending >> b) & 1u) {
+        fin_ok = ptx::mbar_wait_bounded(&sm.mma_done[b], (phase >> b) & 1u, kWaitIters);
+        pending &= ~(1u << b);
+        phase ^= 1u << b;
+      }
+      sm.ctl[b][2] = 1;
+    }
+    ptx::mbar_arrive(&sm.ready[b]);
+  }
   if (tid == 0) {
-    ptx::mma_commit(&sm.fin);
-    fin_ok = ptx::mbar_wait_bounded(&sm.fin, 0u, kWaitIters);
-    for (int b = 0; b < 2 && fin_ok; ++b)
-      if ((pending >> b) & 1u) fin_ok = ptx::mbar_wait_bounded(&sm.mma_done[b], (phase >> b) & 1u, kWaitIters);
+    fin_ok = ptx::mbar_wait_bounded(&sm.fin, 0u, kWaitIters) && fin_ok;
     if (!fin_ok) atomicOr(&hdr->status, kStatTimeout);
   }
-  const bool bad = (__syncthreads_or(!fin_ok) != 0) || aborted;
+  const bool bad = walkers_or(!fin_ok) || aborted;
   ptx::tc_fence_after();
 
   // epilogue: each thread reads its own pixel's row (TMEM lane)
@@ -462,6 +526,7 @@ __global__ void __launch_bounds__(kMThreads, 1) render_mma_kernel(
     atomicAdd(&sm.cnt[0], (unsigned long long)we);
     atomicAdd(&sm.cnt[1], (unsigned long long)wc);
   }
+  }  // walkers
   ptx::tc_fence_before();
   __syncthreads();
   if (warp == 0) ptx::tmem_dealloc(tmem, cols);
@@ -485,7 +550,7 @@ cudaError_t launch_render_mma(const CamArgs& cam, const UpliftWs& ws, int slot, 
   const size_t smem = render_mma_smem_bytes();
   cudaError_t err = cudaFuncSetAttribute(render_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  render_mma_kernel<<<ntiles, kMThreads, smem, st>>>(cam, ws.proj, ws.keys, ws.tile_start, slot, topk_idx, topk_val,
+  render_mma_kernel<<<ntiles, kCtaThreads, smem, st>>>(cam, ws.proj, ws.keys, ws.tile_start, slot, topk_idx, topk_val,
                                                       K, C, out, out_bf16, out_T, out_last, ws.hdr);
   g_launches += 1;
   return cudaGetLastError();

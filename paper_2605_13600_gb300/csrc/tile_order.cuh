@@ -18,11 +18,21 @@ namespace scoup {
 // registers allow.
 constexpr int kLoadBatch = 4;
 
-template <int kWin_, int kLogNB_>
+// kSync_: 0 when the whole CTA orders (the functions below synchronise with
+// __syncthreads and stride by blockDim.x); otherwise the number of threads,
+// the CTA's first kSync_, that order on named barrier 1 while the rest of the
+// CTA does other work.
+template <int kWin_, int kLogNB_, int kSync_ = 0>
 struct OrderSmem {
   static constexpr int kWin = kWin_;
   static constexpr int kNB = 1 << kLogNB_;
   static constexpr int kLogNB = kLogNB_;
+  static constexpr int kSync = kSync_;
+  __device__ static __forceinline__ int nthreads() { return kSync ? kSync : (int)blockDim.x; }
+  __device__ static __forceinline__ void sync() {
+    if constexpr (kSync > 0) asm volatile("bar.sync 1, %0;" ::"n"(kSync) : "memory");
+    else __syncthreads();
+  }
   uint32_t bstart[kNB + 1];
   uint32_t bcur[kNB];
   unsigned long long win[kWin];
@@ -62,13 +72,13 @@ __device__ OrderBuckets order_buckets(const WsHeader* hdr, int slot) {
   return bk;
 }
 
-// Histogram + exclusive scan into sm.bstart (block-wide; blockDim.x threads,
-// a multiple of 32 dividing kNB).
+// Histogram + exclusive scan into sm.bstart (S::nthreads() threads, a
+// multiple of 32 dividing kNB).
 template <class S, int kLB = kLoadBatch>
 __device__ void order_init(S& sm, const unsigned long long* __restrict__ keys, int n, const OrderBuckets& bk) {
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, nt = S::nthreads(), lane = tid & 31, warp = tid >> 5;
   for (int b = tid; b < S::kNB; b += nt) sm.bcur[b] = 0u;
-  __syncthreads();
+  S::sync();
   // kLB keys per thread are loaded before their atomics, so each
   // thread has that many global loads in flight at once
   for (int i0 = tid; i0 < n; i0 += kLB * nt) {
@@ -82,7 +92,7 @@ __device__ void order_init(S& sm, const unsigned long long* __restrict__ keys, i
     for (int u = 0; u < kLB; ++u)
       if (i0 + u * nt < n) atomicAdd(&sm.bcur[bk(kk[u])], 1u);
   }
-  __syncthreads();
+  S::sync();
   const int per = S::kNB / nt;
   uint32_t sum = 0;
   for (int q = 0; q < per; ++q) sum += sm.bcur[tid * per + q];
@@ -92,7 +102,7 @@ __device__ void order_init(S& sm, const unsigned long long* __restrict__ keys, i
     if (lane >= off) incl += y;
   }
   if (lane == 31) sm.hist[warp] = incl;
-  __syncthreads();
+  S::sync();
   uint32_t run = incl - sum;
   for (int w = 0; w < warp; ++w) run += sm.hist[w];
   for (int q = 0; q < per; ++q) {
@@ -101,7 +111,7 @@ __device__ void order_init(S& sm, const unsigned long long* __restrict__ keys, i
     run += c;
   }
   if (tid == nt - 1) sm.bstart[S::kNB] = run;
-  __syncthreads();
+  S::sync();
 }
 
 // The rank-th smallest (0-based) key in bucket b with (first || key > last).
@@ -109,9 +119,9 @@ template <class S>
 __device__ unsigned long long order_select(S& sm, const unsigned long long* __restrict__ keys, int n,
                                            const OrderBuckets& bk, int b, unsigned long long last,
                                            bool first, int rank) {
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x, nt = S::nthreads();
   if (tid == 0) { sm.red_min = ~0ull; sm.red_max = 0ull; }
-  __syncthreads();
+  S::sync();
   unsigned long long lmin = ~0ull, lmax = 0ull;
   for (int i = tid; i < n; i += nt) {
     const unsigned long long k = keys[i];
@@ -122,13 +132,13 @@ __device__ unsigned long long order_select(S& sm, const unsigned long long* __re
     lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, off));
   }
   if ((tid & 31) == 0) { atomicMin(&sm.red_min, lmin); atomicMax(&sm.red_max, lmax); }
-  __syncthreads();
+  S::sync();
   const unsigned long long base = sm.red_min, span = sm.red_max - sm.red_min;
   const int nbits = span ? 64 - __clzll((long long)span) : 1;
   unsigned long long prefix = 0ull, pmask = 0ull;
   for (int shift = ((nbits - 1) / 8) * 8; shift >= 0; shift -= 8) {
     for (int d = tid; d < 256; d += nt) sm.hist[d] = 0u;
-    __syncthreads();
+    S::sync();
     for (int i = tid; i < n; i += nt) {
       const unsigned long long k = keys[i];
       if (bk(k) == b && (first || k > last)) {
@@ -136,7 +146,7 @@ __device__ unsigned long long order_select(S& sm, const unsigned long long* __re
         if ((x & pmask) == prefix) atomicAdd(&sm.hist[(x >> shift) & 255u], 1u);
       }
     }
-    __syncthreads();
+    S::sync();
     if (tid < 32) {
       uint32_t c[8], sum = 0;
       for (int d = 0; d < 8; ++d) { c[d] = sm.hist[tid * 8 + d]; sum += c[d]; }
@@ -154,11 +164,11 @@ __device__ unsigned long long order_select(S& sm, const unsigned long long* __re
         }
       }
     }
-    __syncthreads();
+    S::sync();
     prefix |= (unsigned long long)sm.sel_digit << shift;
     pmask |= 0xffull << shift;
     rank = sm.sel_rank;
-    __syncthreads();
+    S::sync();
   }
   return base + prefix;
 }
@@ -169,7 +179,7 @@ __device__ unsigned long long order_select(S& sm, const unsigned long long* __re
 template <class S, int kLB = kLoadBatch>
 __device__ int order_next_window(S& sm, const unsigned long long* __restrict__ keys, int n,
                                  const OrderBuckets& bk, OrderState& st, WsHeader* hdr) {
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x, nt = S::nthreads();
   constexpr int kWin = S::kWin, kNB = S::kNB;
   // the in-place permutation below reads a whole window before writing it
   if (kWin > 4 * nt) {
@@ -187,9 +197,9 @@ __device__ int order_next_window(S& sm, const unsigned long long* __restrict__ k
       }
       sm.win_b1 = lo;
     }
-    __syncthreads();
+    S::sync();
     st.b0 = sm.win_b1;
-    __syncthreads();
+    S::sync();
   }
   if (st.b0 >= kNB) return 0;
   const uint32_t base = sm.bstart[st.b0];
@@ -207,14 +217,14 @@ __device__ int order_next_window(S& sm, const unsigned long long* __restrict__ k
         sm.win_b1 = lo;
       }
     }
-    __syncthreads();
+    S::sync();
   }
   const int b1 = sm.win_b1;
   int m;
   if (!st.in_split && b1 > st.b0) {
     m = (int)(sm.bstart[b1] - base);
     for (int b = st.b0 + tid; b < b1; b += nt) sm.bcur[b] = sm.bstart[b] - base;
-    __syncthreads();
+    S::sync();
     for (int i0 = tid; i0 < n; i0 += kLB * nt) {
       unsigned long long kk[kLB];
 #pragma unroll
@@ -231,7 +241,7 @@ __device__ int order_next_window(S& sm, const unsigned long long* __restrict__ k
         }
       }
     }
-    __syncthreads();
+    S::sync();
     // rank inside the bucket, then permute in place (m <= kWin <= 4 nt: one pass)
     for (int p0 = 0; p0 < m; p0 += nt * 4) {
       unsigned long long kk[4];
@@ -250,11 +260,11 @@ __device__ int order_next_window(S& sm, const unsigned long long* __restrict__ k
           dst[u] = lo + r;
         }
       }
-      __syncthreads();
+      S::sync();
 #pragma unroll
       for (int u = 0; u < 4; ++u)
         if (dst[u] >= 0) sm.win[dst[u]] = kk[u];
-      __syncthreads();
+      S::sync();
     }
   } else {
     if (!st.in_split) { st.in_split = true; st.split_first = true; st.consumed = 0; }
@@ -263,7 +273,7 @@ __device__ int order_next_window(S& sm, const unsigned long long* __restrict__ k
     unsigned long long hi_key = ~0ull;
     if (left > kWin) hi_key = order_select(sm, keys, n, bk, st.b0, st.split_last, st.split_first, kWin - 1);
     if (tid == 0) sm.cursor = 0u;
-    __syncthreads();
+    S::sync();
     for (int i = tid; i < n; i += nt) {
       const unsigned long long k = keys[i];
       if (bk(k) == st.b0 && (st.split_first || k > st.split_last) && k <= hi_key) {
@@ -271,7 +281,7 @@ __device__ int order_next_window(S& sm, const unsigned long long* __restrict__ k
         if (pos < (unsigned)kWin) sm.win[pos] = k;
       }
     }
-    __syncthreads();
+    S::sync();
     m = (int)min(sm.cursor, (unsigned)kWin);
     for (int p0 = 0; p0 < m; p0 += nt * 4) {
       unsigned long long kk[4];
@@ -288,14 +298,14 @@ __device__ int order_next_window(S& sm, const unsigned long long* __restrict__ k
           dst[u] = r;
         }
       }
-      __syncthreads();
+      S::sync();
 #pragma unroll
       for (int u = 0; u < 4; ++u)
         if (dst[u] >= 0) sm.win[dst[u]] = kk[u];
-      __syncthreads();
+      S::sync();
     }
   }
-  __syncthreads();
+  S::sync();
   if (m <= 0) {
     if (tid == 0) atomicOr(&hdr->status, kStatDeviceCheck);
     return -1;
