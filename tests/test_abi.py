@@ -163,3 +163,33 @@ def test_similarity_relevancy_rejects_bad_arguments(lib):
     assert f(buf, 10, 512, None, buf, 32, 3, 10.0, buf, buf, 1 << 20, None) == lib.SCOUP_ERR_INVALID_ARG
     assert f(buf, 10, 512, None, buf, 32, 0, 10.0, buf, buf, 1 << 20, None) == lib.SCOUP_ERR_INVALID_ARG
     assert f(buf, 10, 512, None, buf, 32, 4, 0.0, buf, buf, 1 << 20, None) == lib.SCOUP_ERR_INVALID_ARG
+
+
+def test_decode_query_rejects_bad_arguments(lib):
+    """Argument checks of the decode with the query unit, before any device work."""
+    f = lib.load().scoup_decode_query
+    buf = ct.c_void_p(256)
+    ws = 1 << 30
+    # scoup_decode_query(codes, codes_dtype, P, C, codebook, D, text, Q, n_canon, alpha,
+    #                    features, feat_norm2, out, workspace, ws_bytes, stream)
+    ok = dict(Q=32, n_canon=0, alpha=10.0, C=256, D=512, dt=1)
+
+    def call(**kw):
+        a = dict(ok, **kw)
+        return f(buf, a["dt"], 10, a["C"], buf, a["D"], buf, a["Q"], a["n_canon"], a["alpha"], None, None, buf,
+                 buf, ws, None)
+    assert call(Q=48) == lib.SCOUP_ERR_INVALID_ARG              # one 16- or 32-column unit
+    assert call(Q=24) == lib.SCOUP_ERR_INVALID_ARG
+    assert call(n_canon=3) == lib.SCOUP_ERR_INVALID_ARG         # Q - n_canon a multiple of 4
+    assert call(n_canon=32) == lib.SCOUP_ERR_INVALID_ARG        # at least one query
+    assert call(n_canon=4, alpha=0.0) == lib.SCOUP_ERR_INVALID_ARG
+    assert call(C=12) == lib.SCOUP_ERR_INVALID_ARG              # C a multiple of 8
+    assert call(D=40) == lib.SCOUP_ERR_INVALID_ARG              # D a multiple of 16
+    assert call(dt=2) == lib.SCOUP_ERR_INVALID_ARG
+    # misaligned output, and a workspace that is too small
+    assert f(buf, 1, 10, 256, buf, 512, buf, 32, 0, 10.0, None, None, ct.c_void_p(260), buf, ws, None) == \
+        lib.SCOUP_ERR_INVALID_ARG
+    need = lib.load().scoup_decode_query_workspace_size(10, 256, 512, 32)
+    assert need > 0
+    assert f(buf, 1, 10, 256, buf, 512, buf, 32, 0, 10.0, None, None, buf, buf, need - 1, None) == \
+        lib.SCOUP_ERR_OOM
