@@ -72,10 +72,10 @@ struct UnitPos {
   bool query, valid;
 };
 
-template <int BN>
-__device__ __forceinline__ UnitPos unit_at(int i, int n_tiles, int m_blocks, bool fused) {
+template <int BN, bool kQuery>
+__device__ __forceinline__ UnitPos unit_at(int i, int n_tiles, int m_blocks) {
   UnitPos p;
-  if (!fused) {
+  if constexpr (!kQuery) {
     const int u = blockIdx.x + i * (int)gridDim.x;
     p.m0 = (u / n_tiles) * BM;
     p.n0 = (u % n_tiles) * BN;
@@ -91,7 +91,8 @@ __device__ __forceinline__ UnitPos unit_at(int i, int n_tiles, int m_blocks, boo
   return p;
 }
 
-template <int BN>
+// kQuery: the fused query unit (compiled out of the plain launches).
+template <int BN, bool kQuery>
 __global__ void __launch_bounds__(kGemmThreads, 1) gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                     const __grid_constant__ CUtensorMap tmB,
                                                                     const __grid_constant__ CUtensorMap tmO,
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_bf16_kernel(const __grid
   const int kt = (ep.K + BK - 1) / BK;
   const int n_tiles = (ep.N + BN - 1) / BN;
   const int m_blocks = (ep.M + BM - 1) / BM;
-  const bool fused = ep.sim_n > 0;
+  constexpr bool fused = kQuery;
   constexpr uint32_t kBytesA = BM * BK * 2, kBytesB = BN * BK * 2;
   const uint32_t kBytesG = (uint32_t)ep.sim_n * BK * 2;
   constexpr uint32_t idesc = ptx::idesc_bf16_f32(BM, BN);
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_bf16_kernel(const __grid
     // ---- TMA producer ----
     int it = 0;
     for (int i = 0; !sm.abort && !ep.stall_loads; ++i) {
-      const UnitPos t = unit_at<BN>(i, n_tiles, m_blocks, fused);
+      const UnitPos t = unit_at<BN, kQuery>(i, n_tiles, m_blocks);
       if (!t.valid) break;
       const CUtensorMap* mb = t.query ? &tmG : &tmB;
       const int nb = t.query ? 0 : t.n0;
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_bf16_kernel(const __grid
     int it = 0, local = 0;
     bool ok = true;
     for (int i = 0; ok && !sm.abort; ++i, ++local) {
-      const UnitPos t = unit_at<BN>(i, n_tiles, m_blocks, fused);
+      const UnitPos t = unit_at<BN, kQuery>(i, n_tiles, m_blocks);
       if (!t.valid) break;
       const uint32_t id = t.query ? idesc_q : idesc;
       const int b = local & 1, use = local >> 1;
@@ -201,15 +202,15 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_bf16_kernel(const __grid
     int local = 0, sbuf = 0;
     float ss_row = 0.0f;  // fused query: squared norm of the row's rounded outputs over its row block
     for (int i = 0; !sm.abort; ++i, ++local) {
-      const UnitPos t = unit_at<BN>(i, n_tiles, m_blocks, fused);
+      const UnitPos t = unit_at<BN, kQuery>(i, n_tiles, m_blocks);
       if (!t.valid) break;
       const int m0 = t.m0, n0 = t.query ? 0 : t.n0;
-      const int mode = t.query ? ep.sim_mode : ep.mode;
+      const int mode = (kQuery && t.query) ? ep.sim_mode : ep.mode;
       const bool f32out = mode != kOutBF16;
       const int cw = f32out ? 32 : kCW;
-      const int ncols = t.query ? ep.sim_n : BN;  // accumulator columns of this unit (sim_n <= 32)
+      const int ncols = (kQuery && t.query) ? ep.sim_n : BN;  // accumulator columns of this unit (sim_n <= 32)
       const int nlim = t.query ? ep.sim_n : ep.N;
-      const bool write = t.query || ep.store;
+      const bool write = kQuery ? (t.query || ep.store) : true;
       const CUtensorMap* mo = t.query ? &tmS : &tmO;
       const int b = local & 1, use = local >> 1;
       if (!wait_or_abort(&sm.acc_full[b], use & 1, &sm.abort, ep.status)) break;
@@ -384,12 +385,13 @@ cudaError_t launch_bn(const void* A, const void* Bt, const void* Gt, const GemmE
     ts = to;
   }
   const size_t smem = sizeof(GemmSmem<BN>) + 1024;
-  cudaError_t e = cudaFuncSetAttribute(gemm_bf16_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = fused ? gemm_bf16_kernel<BN, true> : gemm_bf16_kernel<BN, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t m_blocks = (ep.M + BM - 1) / BM;
   const int64_t units = fused ? m_blocks : m_blocks * ((ep.N + BN - 1) / BN);
   const int grid = (int)(units < num_sms() ? units : num_sms());
-  gemm_bf16_kernel<BN><<<grid, kGemmThreads, smem, st>>>(ta, tb, to, tg, ts, ep);
+  kern<<<grid, kGemmThreads, smem, st>>>(ta, tb, to, tg, ts, ep);
   g_launches += 1;
   return cudaGetLastError();
 }
