@@ -15,7 +15,9 @@
 // counting pass reserves the CTA's run in each tile list right away (one
 // global atomic per (CTA, tile)) and keeps the run's offset, so the filling
 // pass expands the items only once and writes each CTA's keys of a tile into
-// one contiguous run.  Rectangles larger than kBigRect tiles go to separate
+// one contiguous run.  A warp whose rectangles overlap heavily walks their
+// union tile by tile instead, so that the keys of one tile leave in one
+// coalesced store.  Rectangles larger than kBigRect tiles go to separate
 // global counters and are placed after the reserved runs.
 //
 // Depth slabs.  Called for slab s of a view, both passes take only the

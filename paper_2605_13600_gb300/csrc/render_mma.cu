@@ -9,11 +9,15 @@
 // (two 128-pixel halves x C FP32 columns) and adds every chunk with
 // tcgen05.mma; the rows leave the SM once, at the end of the tile.
 //
-// One CTA per tile, one thread per pixel.  The list is ordered window by
-// window as in the uplift (tile_order.cuh).  Per chunk every thread walks its
-// pixel front to back over the chunk's Gaussians (the binary32 exponent,
-// alpha test and T-stop rule of the uplift) and writes its row of E; the CTA
-// expands the chunk's codes into W.  The bf16 operands are split, e = e_hi +
+// One CTA per tile: 256 walkers (one thread per pixel) and a ninth warp that
+// issues the MMAs.  The walkers order the list window by window as in the
+// uplift (tile_order.cuh, on a named barrier of their own).  Per chunk every
+// walker walks its pixel front to back over the chunk's Gaussians (the
+// binary32 exponent, alpha test and T-stop rule of the uplift) and writes its
+// row of E, the walkers expand the chunk's codes into W and arrive on the
+// chunk buffer's mbarrier; the MMA warp waits on it, issues the chunk's MMAs
+// and commits them to the buffer's completion barrier (every chunk, also one
+// without MMAs, so the walkers are never two chunks ahead on a buffer).  The bf16 operands are split, e = e_hi +
 // e_lo and w = w_hi + w_lo (each part rounded to bf16), and three MMAs add
 // E_hi W_hi + E_hi W_lo + E_lo W_hi.  With u = 2^-8 (bf16 unit roundoff)
 // each split leaves u^2 of its value and the dropped E_lo W_lo is below u^2
@@ -23,8 +27,11 @@
 // MMAs of the previous one.  A chunk in which a pixel half has no weight
 // issues no MMA for that half.
 //
-// Every wait on an MMA completion is bounded; a wait that gives up sets the
-// timeout status, the CTA stops walking, and TMEM is freed on every path.
+// Every wait (the MMA warp's on a chunk, the walkers' on a completion) is
+// bounded; a wait that gives up sets the timeout status, the walkers stop,
+// a stop still reaches the MMA warp, and TMEM is freed on every path.  The
+// tile's rows are written at the end through the free chunk buffers, in
+// coalesced 512-byte pieces.
 #include <cuda_bf16.h>
 #include <math.h>
 
