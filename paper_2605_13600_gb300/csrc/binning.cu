@@ -165,23 +165,13 @@ __device__ LocalBox chunk_box(const ushort4& r) {
 
 static_assert(kChunk == kBinThreads, "one Gaussian per binning thread");
 
-__device__ void scan_tiles(uint32_t* __restrict__ tile_count, uint32_t* __restrict__ tile_glob,
-                           uint32_t* __restrict__ tile_start, uint32_t* __restrict__ tile_fill, int ntiles,
-                           int64_t capacity, WsHeader* __restrict__ hdr, int slot);
-
-// The last counting CTA to finish (a fence, then a per-slot counter in the
-// header) scans the per-tile counts into the list offsets itself, so no
-// separate one-CTA launch sits between the counting and the filling pass.
 __global__ void __launch_bounds__(kBinThreads) count_kernel(const ushort4* __restrict__ rects,
                                                             const uint32_t* __restrict__ depth, int64_t n,
                                                             int gx, uint32_t* __restrict__ tile_count,
                                                             uint32_t* __restrict__ tile_glob,
                                                             uint32_t* __restrict__ run_base,
-                                                            WsHeader* __restrict__ hdr, int slot, int slab,
-                                                            int last, const uint8_t* __restrict__ done,
-                                                            uint32_t* __restrict__ tile_start,
-                                                            uint32_t* __restrict__ tile_fill, int ntiles,
-                                                            int64_t capacity) {
+                                                            const WsHeader* __restrict__ hdr, int slot, int slab,
+                                                            int last, const uint8_t* __restrict__ done) {
   __shared__ uint32_t s_cnt[kLocalMax];
   const SlabSel sel = slab_sel(hdr, slot, slab, last, done);
   const int64_t lo = blockIdx.x * kChunk, hi = min(n, lo + kChunk);
@@ -236,27 +226,17 @@ __global__ void __launch_bounds__(kBinThreads) count_kernel(const ushort4* __res
       base[t] = (c && !sel.skip_tile(g)) ? atomicAdd(&tile_count[g], c) : 0u;
     }
   }
-  __shared__ bool s_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(&hdr->bin_blocks[slot], 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  scan_tiles(tile_count, tile_glob, tile_start, tile_fill, ntiles, capacity, hdr, slot);
-  if (threadIdx.x == 0) hdr->bin_blocks[slot] = 0u;  // for the next view on this slot
 }
 
 // Exclusive scan of the tile counts (reserved runs + big-rectangle items; one
 // CTA), capacity check; the fill cursor of a tile starts after its reserved
 // runs; the counters are reset for the next view.
-// Exclusive scan of the per-tile counts (the chunk-local runs plus the
-// global-path items) into the tile list offsets, with the per-view resets;
-// run by one CTA (any multiple of 32 threads, at most 1024).  The counts were
-// accumulated by global atomics, so they are read through L2.
-__device__ void scan_tiles(uint32_t* __restrict__ tile_count, uint32_t* __restrict__ tile_glob,
-                           uint32_t* __restrict__ tile_start, uint32_t* __restrict__ tile_fill, int ntiles,
-                           int64_t capacity, WsHeader* __restrict__ hdr, int slot) {
+__global__ void __launch_bounds__(1024) scan_kernel(uint32_t* __restrict__ tile_count,
+                                                    uint32_t* __restrict__ tile_glob,
+                                                    uint32_t* __restrict__ tile_start,
+                                                    uint32_t* __restrict__ tile_fill, int ntiles,
+                                                    int64_t capacity, WsHeader* __restrict__ hdr,
+                                                    int slot) {
   __shared__ uint32_t s_warp[32];
   __shared__ unsigned long long s_carry;
   if (threadIdx.x == 0) s_carry = 0;
@@ -264,8 +244,8 @@ __device__ void scan_tiles(uint32_t* __restrict__ tile_count, uint32_t* __restri
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int base = 0; base < ntiles; base += blockDim.x) {
     const int t = base + threadIdx.x;
-    const uint32_t local = t < ntiles ? __ldcg(&tile_count[t]) : 0u;
-    uint32_t v = t < ntiles ? local + __ldcg(&tile_glob[t]) : 0u;
+    const uint32_t local = t < ntiles ? tile_count[t] : 0u;
+    uint32_t v = t < ntiles ? local + tile_glob[t] : 0u;
     uint32_t x = v;
     for (int off = 1; off < 32; off <<= 1) {
       uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
@@ -304,15 +284,6 @@ __device__ void scan_tiles(uint32_t* __restrict__ tile_count, uint32_t* __restri
     atomicAdd(&hdr->listed, total);
     atomicMax(&hdr->max_dups_view, (int)min(total, 0x7fffffffull));
   }
-}
-
-__global__ void __launch_bounds__(1024) scan_kernel(uint32_t* __restrict__ tile_count,
-                                                    uint32_t* __restrict__ tile_glob,
-                                                    uint32_t* __restrict__ tile_start,
-                                                    uint32_t* __restrict__ tile_fill, int ntiles,
-                                                    int64_t capacity, WsHeader* __restrict__ hdr,
-                                                    int slot) {
-  scan_tiles(tile_count, tile_glob, tile_start, tile_fill, ntiles, capacity, hdr, slot);
 }
 
 __global__ void __launch_bounds__(kBinThreads) fill_kernel(
@@ -430,16 +401,14 @@ cudaError_t launch_binning(const CamArgs& cam, int64_t n, const UpliftWs& ws, in
   const int last = last_slab ? 1 : 0;
   if (n > 0)
     count_kernel<<<blocks, kBinThreads, 0, st>>>(ws.rect, ws.depth, n, cam.gx, ws.tile_count, ws.tile_glob,
-                                                 ws.run_base, ws.hdr, slot, slab, last, done, ws.tile_start,
-                                                 ws.tile_fill, ntiles, ws.dup_capacity);
-  else
-    scan_kernel<<<1, 1024, 0, st>>>(ws.tile_count, ws.tile_glob, ws.tile_start, ws.tile_fill, ntiles,
-                                    ws.dup_capacity, ws.hdr, slot);
+                                                 ws.run_base, ws.hdr, slot, slab, last, done);
+  scan_kernel<<<1, 1024, 0, st>>>(ws.tile_count, ws.tile_glob, ws.tile_start, ws.tile_fill, ntiles,
+                                  ws.dup_capacity, ws.hdr, slot);
   if (n > 0)
     fill_kernel<<<blocks, kBinThreads, 0, st>>>(ws.rect, ws.depth, ws.sp.orig, n, cam.gx, ws.tile_start,
                                                 ws.tile_fill, ws.run_base, ws.keys, ws.hdr, slot, slab, last,
                                                 done);
-  g_launches += n > 0 ? 2 : 1;
+  g_launches += n > 0 ? 3 : 1;
   return cudaGetLastError();
 }
 

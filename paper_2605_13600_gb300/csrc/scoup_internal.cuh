@@ -54,7 +54,7 @@ struct WsHeader {
   uint32_t slab_lo[4][kMaxSlabs];  // [slot][s]: smallest depth bits of slab s (slab 0 starts at 0)
   uint32_t pp_blocks[4];           // projection CTAs finished in this slot's view (last one sets slab_lo)
   unsigned long long split_windows;  // windows cut out of a depth bucket holding more than a window
-  uint32_t bin_blocks[4];            // counting CTAs finished in this slot's view (the last one scans)
+  unsigned long long reserved[2];
 };
 static_assert(sizeof(WsHeader) == 256, "header size");
 
