@@ -398,10 +398,12 @@ typedef struct scoup_plan scoup_plan;  /* opaque */
 typedef struct scoup_tune_entry {
   int32_t lanes;
   int32_t warp_w;
-  float ms;  /* best of two timed runs on the view sample */
+  float ms;             /* best of two timed runs on the view sample */
+  int32_t chunk_views;  /* 0: scenes on lanes; > 0: the chunked form (scoup_plan_set_chunk) */
 } scoup_tune_entry;
 
-#define SCOUP_MAX_TUNE 16
+#define SCOUP_MAX_TUNE 24
+#define SCOUP_MAX_CHUNK_VIEWS 64
 typedef struct scoup_plan_info {
   int32_t lanes;            /* scenes run concurrently on this many streams */
   int32_t warp_w;           /* tile-kernel warp pixel block: warp_w x (32 / warp_w) */
@@ -410,6 +412,7 @@ typedef struct scoup_plan_info {
   int64_t workspace_bytes;  /* device memory held by the lane workspaces */
   int32_t n_tune;
   scoup_tune_entry tune[SCOUP_MAX_TUNE];  /* the autotuner's measurements */
+  int32_t chunk_views;      /* 0: scenes on lanes; > 0: views per chunk of the chunked form */
 } scoup_plan_info;
 
 #define SCOUP_BATCH_EAGER 1  /* scoup_uplift_batched flag: launch directly, no graph */
@@ -427,10 +430,26 @@ int scoup_plan_create(const scoup_batch_item* items, int32_t B, int32_t C, int32
  * 16) by hand; drops a captured graph. */
 int scoup_plan_set(scoup_plan* plan, int32_t lanes, int32_t warp_w);
 
+/* Selects the batch's execution form.  chunk_views = 0 (the default): each
+ * lane runs whole scenes one after another, every view with its own
+ * projection, binning and tile launch.  chunk_views in [1, 64]: the views of
+ * all scenes are interleaved (view r of every scene, then view r + 1, ...)
+ * and cut into chunks of chunk_views views; each view of a chunk is projected
+ * and binned into a view workspace of its own, then ONE persistent tile launch
+ * composites every (scene, view, tile) item of the chunk, its CTAs taking
+ * items from an atomic counter; `lanes` chunks are in flight on the lanes'
+ * streams.  Results are those of scoup_uplift per item (the order of FP32
+ * sums aside).  The chunked form's device memory (every scene's sorted copy
+ * and lanes x chunk_views view workspaces) is allocated at the next run, which
+ * then synchronises the device once.  Drops a captured graph. */
+int scoup_plan_set_chunk(scoup_plan* plan, int32_t chunk_views);
+
 /* Autotuner: runs the batch restricted to `sample_views` evenly spaced views
  * per scene for every lanes in {1, 2, 4, 8} (<= B) and warp block in
- * {8x4, 16x2, 4x8}, times each (CUDA events on `stream`, best of two after a
- * warm-up) and keeps the fastest (scoup_plan_info_get lists the timings).
+ * {8x4, 16x2, 4x8}, then the chunked form (chunk_views 4, 8 and 16 on 1, 2
+ * or 4 lanes (<= B), with the best warp block), times each (CUDA events on `stream`,
+ * best of two after a warm-up) and keeps the fastest (scoup_plan_info_get
+ * lists the timings).
  * Overwrites the items' accum and Top-K outputs; refused with
  * SCOUP_ACCUM_CONTINUE.  Synchronises `stream`. */
 int scoup_autotune(scoup_plan* plan, int32_t sample_views, void* stream);

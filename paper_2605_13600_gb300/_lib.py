@@ -64,17 +64,18 @@ class BatchItem(ct.Structure):
 
 
 class TuneEntry(ct.Structure):
-    _fields_ = [("lanes", ct.c_int32), ("warp_w", ct.c_int32), ("ms", ct.c_float)]
+    _fields_ = [("lanes", ct.c_int32), ("warp_w", ct.c_int32), ("ms", ct.c_float), ("chunk_views", ct.c_int32)]
 
 
-SCOUP_MAX_TUNE = 16
+SCOUP_MAX_TUNE = 24
+SCOUP_MAX_CHUNK_VIEWS = 64
 SCOUP_BATCH_EAGER = 1
 
 
 class PlanInfo(ct.Structure):
     _fields_ = [("lanes", ct.c_int32), ("warp_w", ct.c_int32), ("tuned", ct.c_int32),
                 ("graph_kernels", ct.c_int32), ("workspace_bytes", ct.c_int64), ("n_tune", ct.c_int32),
-                ("tune", TuneEntry * SCOUP_MAX_TUNE)]
+                ("tune", TuneEntry * SCOUP_MAX_TUNE), ("chunk_views", ct.c_int32)]
 
 
 _lib = None
@@ -121,6 +122,7 @@ PROTOS = {
                                         P, P, ct.POINTER(Stats), P]),
     "scoup_plan_create": (ct.c_int, [P, I32, I32, I32, I32, ct.POINTER(ct.c_void_p), P]),
     "scoup_plan_set": (ct.c_int, [P, I32, I32]),
+    "scoup_plan_set_chunk": (ct.c_int, [P, I32]),
     "scoup_autotune": (ct.c_int, [P, I32, P]),
     "scoup_uplift_batched": (ct.c_int, [P, I32, P]),
     "scoup_plan_stats": (ct.c_int, [P, P, P]),

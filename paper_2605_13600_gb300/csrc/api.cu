@@ -115,40 +115,60 @@ size_t uplift_fixed_bytes(int64_t n, int max_tiles, int64_t code_rows_k, int lan
   return shared_bytes(n, code_rows_k) + (size_t)lanes * lane_bytes(n, max_tiles);
 }
 
+}  // namespace
+
+size_t carve_scene_part(void* base, int64_t n, int64_t code_rows_k, UpliftWs* w, int32_t** codes_i,
+                        float** codes_v) {
+  char* p = (char*)base;
+  size_t off = 0;
+  const size_t un = (size_t)n;
+  auto take = [&](size_t sz) { char* q = p + off; off += align_up(sz); return (void*)q; };
+  w->hdr = (WsHeader*)take(sizeof(WsHeader));
+  w->sp.means = (float*)take(sizeof(float) * 3 * un);
+  w->sp.scales = (float*)take(sizeof(float) * 3 * un);
+  w->sp.quats = (float*)take(sizeof(float) * 4 * un);
+  w->sp.opacity = (float*)take(sizeof(float) * un);
+  w->sp.tau = (float*)take(sizeof(float) * un);
+  w->sp.orig = (int32_t*)take(sizeof(int32_t) * un);
+  w->cell = (uint32_t*)take(sizeof(uint32_t) * un);
+  w->cells_scratch = (uint32_t*)take(reorder_scratch_bytes());
+  *codes_i = (int32_t*)take((size_t)code_rows_k * 4);
+  *codes_v = (float*)take((size_t)code_rows_k * 4);
+  return off;
+}
+
+size_t carve_view_part(void* base, int64_t n, int max_tiles, UpliftWs* w) {
+  char* p = (char*)base;
+  size_t off = 0;
+  const size_t un = (size_t)n;
+  auto take = [&](size_t sz) { char* q = p + off; off += align_up(sz); return (void*)q; };
+  w->max_tiles = max_tiles;
+  w->proj = (ProjRec*)take(sizeof(ProjRec) * un);
+  w->depth = (uint32_t*)take(sizeof(uint32_t) * un);
+  w->rect = (ushort4*)take(sizeof(ushort4) * un);
+  w->tile_count = (uint32_t*)take(sizeof(uint32_t) * ((size_t)max_tiles + 1));
+  w->tile_glob = (uint32_t*)take(sizeof(uint32_t) * ((size_t)max_tiles + 1));
+  w->run_base = (uint32_t*)take(binning_run_base_bytes(n));
+  w->tile_start = (uint32_t*)take(sizeof(uint32_t) * ((size_t)max_tiles + 1));
+  w->tile_fill = (uint32_t*)take(sizeof(uint32_t) * ((size_t)max_tiles + 1));
+  w->pix_state = (float*)take(sizeof(float) * kTilePixels * (size_t)max_tiles);
+  w->tile_done = (uint8_t*)take((size_t)max_tiles);
+  w->dhist = (uint32_t*)take(sizeof(uint32_t) * kDepthBuckets);
+  return off;
+}
+
+namespace {
+
 // Carves `lanes` view pipelines out of the workspace; out[l] share the header
 // and the scene copy.
 void carve_lanes(void* ws, size_t bytes, int64_t n, int max_tiles, int64_t code_rows_k, int lanes,
                  int32_t** codes_i, float** codes_v, UpliftWs* out) {
   UpliftWs w;
   char* p = (char*)ws;
-  size_t off = 0;
-  const size_t un = (size_t)n;
-  auto take = [&](size_t sz) { char* q = p + off; off += align_up(sz); return (void*)q; };
-  w.hdr = (WsHeader*)take(sizeof(WsHeader));
-  w.sp.means = (float*)take(sizeof(float) * 3 * un);
-  w.sp.scales = (float*)take(sizeof(float) * 3 * un);
-  w.sp.quats = (float*)take(sizeof(float) * 4 * un);
-  w.sp.opacity = (float*)take(sizeof(float) * un);
-  w.sp.tau = (float*)take(sizeof(float) * un);
-  w.sp.orig = (int32_t*)take(sizeof(int32_t) * un);
-  w.cell = (uint32_t*)take(sizeof(uint32_t) * un);
-  w.cells_scratch = (uint32_t*)take(reorder_scratch_bytes());
-  *codes_i = (int32_t*)take((size_t)code_rows_k * 4);
-  *codes_v = (float*)take((size_t)code_rows_k * 4);
-  w.max_tiles = max_tiles;
+  size_t off = carve_scene_part(p, n, code_rows_k, &w, codes_i, codes_v);
   for (int l = 0; l < lanes; ++l) {
     out[l] = w;
-    out[l].proj = (ProjRec*)take(sizeof(ProjRec) * un);
-    out[l].depth = (uint32_t*)take(sizeof(uint32_t) * un);
-    out[l].rect = (ushort4*)take(sizeof(ushort4) * un);
-    out[l].tile_count = (uint32_t*)take(sizeof(uint32_t) * ((size_t)max_tiles + 1));
-    out[l].tile_glob = (uint32_t*)take(sizeof(uint32_t) * ((size_t)max_tiles + 1));
-    out[l].run_base = (uint32_t*)take(binning_run_base_bytes(n));
-    out[l].tile_start = (uint32_t*)take(sizeof(uint32_t) * ((size_t)max_tiles + 1));
-    out[l].tile_fill = (uint32_t*)take(sizeof(uint32_t) * ((size_t)max_tiles + 1));
-    out[l].pix_state = (float*)take(sizeof(float) * kTilePixels * (size_t)max_tiles);
-    out[l].tile_done = (uint8_t*)take((size_t)max_tiles);
-    out[l].dhist = (uint32_t*)take(sizeof(uint32_t) * kDepthBuckets);
+    off += carve_view_part(p + off, n, max_tiles, &out[l]);
   }
   const int64_t keys_each = bytes > off ? (int64_t)((bytes - off) / sizeof(unsigned long long) / lanes) : 0;
   for (int l = 0; l < lanes; ++l) {
@@ -532,6 +552,17 @@ size_t uplift_required_bytes(int64_t n, const scoup_camera* cams, int32_t V, int
   }
   const int64_t code_rows_k = s > K ? (int64_t)R_total * K : 0;
   return uplift_fixed_bytes(n, max_tiles, code_rows_k) + sizeof(unsigned long long) * (size_t)dup_capacity;
+}
+
+size_t uplift_scene_part_bytes(int64_t n, int64_t code_rows_k) { return shared_bytes(n, code_rows_k); }
+
+size_t uplift_view_part_bytes(int64_t n, int max_tiles) { return lane_bytes(n, max_tiles); }
+
+CamArgs camera_args(const scoup_camera& c) { return cam_args(c); }
+
+int check_scene_views(const scoup_scene* scene, const scoup_camera* cams, int32_t V, int* max_tiles) {
+  const int rc = check_scene(scene);
+  return rc ? rc : check_cams(cams, V, max_tiles);
 }
 
 int uplift_stats(const WsHeader* dev_hdr, scoup_stats* stats, cudaStream_t st) {

@@ -22,7 +22,7 @@
 #include <numeric>
 #include <vector>
 
-#include "scoup_internal.cuh"
+#include "drain.cuh"
 
 struct scoup_plan {
   std::vector<scoup_batch_item> items;
@@ -30,6 +30,7 @@ struct scoup_plan {
   int device = 0;
   int lanes = 1;
   int warp_w = 8;
+  int chunk = 0;                  // 0: scenes on lanes; > 0: chunks of this many views (drain.cu)
   bool tuned = false;
   std::vector<int64_t> max_dups;  // per scene
   std::vector<double> cost;       // per scene
@@ -43,6 +44,7 @@ struct scoup_plan {
   cudaGraphExec_t exec = nullptr;
   long long graph_kernels = 0;
   std::vector<scoup_tune_entry> tune;
+  scoup::DrainLayout drain;       // device memory and schedule of the chunked form
 };
 
 namespace scoup {
@@ -135,8 +137,16 @@ ItemView sample_views(const scoup_batch_item& it, int max_views) {
 // Enqueue the batch (or a view sample of it) on the lanes, forked from and
 // joined back into `st`.  copy_stats: append a device copy of each scene's
 // counters to stats_dev.
-int enqueue_batch(scoup_plan* p, int lanes, int warp_w, int sample, bool copy_stats, cudaStream_t st) {
+int enqueue_batch(scoup_plan* p, int lanes, int warp_w, int sample, bool copy_stats, cudaStream_t st,
+                  int chunk = 0) {
   cudaError_t e;
+  if (chunk > 0) {
+    const DrainLayout& d = p->drain;
+    if (!d.mem || d.chunk != chunk || d.lanes != lanes || d.sample != sample)
+      return err(SCOUP_ERR_INVALID_ARG, "chunked batch: layout not prepared for this configuration");
+    return drain_enqueue(&p->drain, p->items, p->C, p->K, p->accum_mode, warp_w, p->lane_st.data(), p->join_ev.data(),
+                         p->fork_ev, copy_stats ? p->stats_dev : nullptr, st);
+  }
   if ((e = cudaEventRecord(p->fork_ev, st)) != cudaSuccess) return cuda_err(e, "fork");
   const auto groups = assign(p, lanes);
   std::vector<ItemView> views(p->items.size());
@@ -170,16 +180,28 @@ int enqueue_batch(scoup_plan* p, int lanes, int warp_w, int sample, bool copy_st
   return SCOUP_OK;
 }
 
+// Lays out the chunked form for (chunk, lanes, sample) unless it already is;
+// synchronises the device, so never while capturing.
+int ensure_drain(scoup_plan* p, int chunk, int lanes, int sample) {
+  const DrainLayout& d = p->drain;
+  if (d.mem && d.chunk == chunk && d.lanes == lanes && d.sample == sample) return SCOUP_OK;
+  return drain_prepare(&p->drain, p->items, p->max_dups, p->C, p->K, p->accum_mode, chunk, lanes, sample);
+}
+
 // Captures the batch on the plan's own origin stream (the caller's stream may
 // be the legacy default stream, which cannot be captured).
 int capture(scoup_plan* p) {
   drop_graph(p);
   const cudaStream_t st = p->cap_st;
   cudaError_t e;
+  if (p->chunk > 0) {
+    const int rc = ensure_drain(p, p->chunk, p->lanes, 0);
+    if (rc != SCOUP_OK) return rc;
+  }
   if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
     return cuda_err(e, "begin capture");
   const long long l0 = g_launches.load();
-  const int rc = enqueue_batch(p, p->lanes, p->warp_w, 0, true, st);
+  const int rc = enqueue_batch(p, p->lanes, p->warp_w, 0, true, st, p->chunk);
   cudaGraph_t g = nullptr;
   e = cudaStreamEndCapture(st, &g);
   const long long nk = g_launches.load() - l0;
@@ -305,40 +327,50 @@ int scoup_autotune(scoup_plan* p, int32_t sample_views, void* stream) {
   }
   p->tune.clear();
   double best = 1e300;
-  int best_l = p->lanes, best_w = p->warp_w;
+  int best_l = p->lanes, best_w = p->warp_w, best_c = 0;
+  // one configuration: one warm-up, then the best of two timed runs
+  auto try_config = [&](int lanes, int w, int chunk) {
+    if (chunk > 0 && (rc = ensure_drain(p, chunk, lanes, sample_views)) != SCOUP_OK) return;
+    float ms_best = 1e30f;
+    for (int rep = 0; rep < 3 && rc == SCOUP_OK; ++rep) {
+      if ((e = cudaEventRecord(t0, st)) != cudaSuccess) { rc = cuda_err(e, "event"); break; }
+      rc = enqueue_batch(p, lanes, w, sample_views, true, st, chunk);
+      if (rc != SCOUP_OK) break;
+      if ((e = cudaEventRecord(t1, st)) != cudaSuccess || (e = cudaEventSynchronize(t1)) != cudaSuccess) {
+        rc = cuda_err(e, "autotune timing");
+        break;
+      }
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, t0, t1);
+      if (rep > 0) ms_best = std::min(ms_best, ms);
+    }
+    if (rc != SCOUP_OK) return;
+    scoup_tune_entry te;
+    te.lanes = lanes;
+    te.warp_w = w;
+    te.ms = ms_best;
+    te.chunk_views = chunk;
+    p->tune.push_back(te);
+    if (ms_best < best) {
+      best = ms_best;
+      best_l = lanes;
+      best_w = w;
+      best_c = chunk;
+    }
+  };
+  // scenes on lanes, every warp block; then the chunked form with the best warp block
   const int lane_opts[] = {1, 2, 4, 8};
   const int w_opts[] = {8, 16, 4};
   for (int lanes : lane_opts) {
     if (lanes > B) break;
-    for (int w : w_opts) {
-      // one warm-up, then the best of two timed runs
-      float ms_best = 1e30f;
-      for (int rep = 0; rep < 3 && rc == SCOUP_OK; ++rep) {
-        if ((e = cudaEventRecord(t0, st)) != cudaSuccess) { rc = cuda_err(e, "event"); break; }
-        rc = enqueue_batch(p, lanes, w, sample_views, true, st);
-        if (rc != SCOUP_OK) break;
-        if ((e = cudaEventRecord(t1, st)) != cudaSuccess || (e = cudaEventSynchronize(t1)) != cudaSuccess) {
-          rc = cuda_err(e, "autotune timing");
-          break;
-        }
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, t0, t1);
-        if (rep > 0) ms_best = std::min(ms_best, ms);
-      }
-      if (rc != SCOUP_OK) break;
-      scoup_tune_entry te;
-      te.lanes = lanes;
-      te.warp_w = w;
-      te.ms = ms_best;
-      p->tune.push_back(te);
-      if (ms_best < best) {
-        best = ms_best;
-        best_l = lanes;
-        best_w = w;
-      }
-    }
-    if (rc != SCOUP_OK) break;
+    for (int w : w_opts)
+      if (rc == SCOUP_OK) try_config(lanes, w, 0);
   }
+  const int w_lane = best_w;
+  const int chunk_opts[] = {4, 8, 16};
+  for (int chunk : chunk_opts)
+    for (int lanes : {1, 2, 4})
+      if (rc == SCOUP_OK && lanes <= (int)p->lane_st.size()) try_config(lanes, w_lane, chunk);
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
   if (rc != SCOUP_OK) return rc;
@@ -349,7 +381,18 @@ int scoup_autotune(scoup_plan* p, int32_t sample_views, void* stream) {
   for (int b = 0; b < B; ++b)
     if (h[b].status) return err(SCOUP_ERR_DEVICE_CHECK, "a scene reported a device error while tuning");
   p->tuned = true;
-  return scoup_plan_set(p, best_l, best_w);
+  rc = scoup_plan_set(p, best_l, best_w);
+  if (rc != SCOUP_OK) return rc;
+  return scoup_plan_set_chunk(p, best_c);
+}
+
+int scoup_plan_set_chunk(scoup_plan* p, int32_t chunk_views) {
+  if (!p) return err(SCOUP_ERR_INVALID_ARG, "plan is NULL");
+  if (chunk_views < 0 || chunk_views > SCOUP_MAX_CHUNK_VIEWS)
+    return err(SCOUP_ERR_INVALID_ARG, "chunk_views outside [0, 64]");
+  if (chunk_views != p->chunk) drop_graph(p);
+  p->chunk = chunk_views;
+  return SCOUP_OK;
 }
 
 int scoup_uplift_batched(scoup_plan* p, int32_t flags, void* stream) {
@@ -357,7 +400,13 @@ int scoup_uplift_batched(scoup_plan* p, int32_t flags, void* stream) {
   if (flags & ~SCOUP_BATCH_EAGER) return err(SCOUP_ERR_INVALID_ARG, "unknown flags");
   cudaStream_t st = (cudaStream_t)stream;
   if (p->items.empty()) return SCOUP_OK;
-  if (flags & SCOUP_BATCH_EAGER) return enqueue_batch(p, p->lanes, p->warp_w, 0, true, st);
+  if (flags & SCOUP_BATCH_EAGER) {
+    if (p->chunk > 0) {
+      const int rc = ensure_drain(p, p->chunk, p->lanes, 0);
+      if (rc != SCOUP_OK) return rc;
+    }
+    return enqueue_batch(p, p->lanes, p->warp_w, 0, true, st, p->chunk);
+  }
   if (!p->exec) {
     const int rc = capture(p);
     if (rc != SCOUP_OK) return rc;
@@ -392,7 +441,8 @@ int scoup_plan_info_get(const scoup_plan* p, scoup_plan_info* info) {
   info->warp_w = p->warp_w;
   info->tuned = p->tuned ? 1 : 0;
   info->graph_kernels = (int32_t)p->graph_kernels;
-  info->workspace_bytes = (int64_t)(p->lane_bytes * p->lane_ws.size());
+  info->workspace_bytes = (int64_t)(p->lane_bytes * p->lane_ws.size() + p->drain.bytes);
+  info->chunk_views = p->chunk;
   info->n_tune = (int32_t)std::min<size_t>(p->tune.size(), SCOUP_MAX_TUNE);
   for (int i = 0; i < info->n_tune; ++i) info->tune[i] = p->tune[i];
   return SCOUP_OK;
@@ -408,6 +458,7 @@ int scoup_plan_destroy(scoup_plan* p) {
   if (p->fork_ev) cudaEventDestroy(p->fork_ev);
   if (p->cap_st) cudaStreamDestroy(p->cap_st);
   if (p->stats_dev) cudaFree(p->stats_dev);
+  drain_release(&p->drain);
   delete p;
   return SCOUP_OK;
 }

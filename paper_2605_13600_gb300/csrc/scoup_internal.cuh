@@ -184,6 +184,24 @@ struct CamArgs {
   int gx, gy;  // tile grid
 };
 
+// One view of a batched chunk, as the drain kernel takes it: the arguments
+// of the per-view tile kernel (single level, one slab) and the view's tiles.
+struct TileJob {
+  CamArgs cam;
+  LevelCodes lc;
+  const ProjRec* proj;
+  const unsigned long long* keys;
+  const uint32_t* tile_start;
+  float* accum;
+  float* comp;                 // compensation array (compensated form) or null
+  WsHeader* hdr;        // the view's own header: depth range, counters, status
+  WsHeader* scene_hdr;  // the scene's header, into which the view's counters are merged
+  int slot;                    // depth-range slot of the view in its own header
+  int C;
+  int tiles;
+  int scene;
+};
+
 // Scene copy in spatial (Morton) order; orig[p] is the caller's index.
 struct SceneP {
   float* means;    // [n,3]
@@ -257,6 +275,17 @@ int uplift_call(const UpliftCall& c, void* workspace, size_t ws_bytes, int warp_
 size_t uplift_required_bytes(int64_t n, const scoup_camera* cams, int32_t V, int32_t s, int32_t K, int32_t R_total,
                              int64_t dup_capacity);
 int uplift_stats(const struct WsHeader* dev_hdr, scoup_stats* stats, cudaStream_t st);
+// Parts of an uplift workspace (api.cu): the scene part (header, Morton-ordered
+// scene copy, codes filtered to K entries) and one view part (records, depth,
+// rectangles, tile counters, slab state); the carve functions lay a part out
+// from a 256-byte aligned base and return its size.
+size_t uplift_scene_part_bytes(int64_t n, int64_t code_rows_k);
+size_t uplift_view_part_bytes(int64_t n, int max_tiles);
+size_t carve_scene_part(void* base, int64_t n, int64_t code_rows_k, UpliftWs* w, int32_t** codes_i,
+                        float** codes_v);
+size_t carve_view_part(void* base, int64_t n, int max_tiles, UpliftWs* w);
+CamArgs camera_args(const scoup_camera& c);
+int check_scene_views(const scoup_scene* scene, const scoup_camera* cams, int32_t V, int* max_tiles);
 void header_stats(const struct WsHeader& h, scoup_stats* stats);
 
 // Launchers (each defined in its own translation unit).
@@ -279,6 +308,14 @@ cudaError_t launch_binning(const CamArgs& cam, int64_t n, const UpliftWs& ws, in
 cudaError_t launch_uplift_tiles(const CamArgs& cam, const UpliftWs& ws, int slot, const LevelCodes& lc, int C,
                                 int Crow, float* accum, float* comp, int warp_w, cudaStream_t st,
                                 int slab = 0, int nslabs = 1);
+// Batched chunk: one persistent launch composites every tile of njobs <=
+// kMaxDrainJobs views (HOST jobs[njobs], copied into the launch's parameters).
+// tile0[j] is the index of view j's first tile in the chunk's item space
+// (tile0[0] = 0, each the sum of the tiles before it); CTAs take items from
+// *counter (DEVICE, zero before the launch).
+constexpr int kMaxDrainJobs = 64;
+cudaError_t launch_uplift_drain(const TileJob* jobs, const uint32_t* tile0, int njobs, unsigned* counter,
+                                bool compensated, int warp_w, cudaStream_t st);
 size_t render_smem_bytes(int C, int K);
 bool render_uses_mma(int C, int K);
 bool render_mma_supported(int C, int K);

@@ -51,6 +51,7 @@
 // next in pix_state, and a tile whose pixels have all stopped is marked done:
 // it returns at once in later slabs, and binning lists nothing for it.
 #include <math.h>
+#include <string.h>
 
 #include "scoup_internal.cuh"
 
@@ -254,21 +255,23 @@ __device__ __forceinline__ void acc_add(float* accum, float* comp, int64_t x, fl
   }
 }
 
+// The whole pass over one tile of one view: ordering, compositing, flush and
+// counters.  Called by the per-view kernel (one CTA per tile) and by the
+// batched drain kernel (a CTA takes tiles of several views in turn); every
+// early return is taken by the whole CTA.
 template <bool kComp, int kBW, int kL>
-__global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
-    CamArgs cam, const ProjRec* __restrict__ proj, const unsigned long long* __restrict__ keys,
-    const uint32_t* __restrict__ tile_start, int slot, LevelCodes lc, int C, int Crow,
-    float* __restrict__ accum, float* __restrict__ comp, WsHeader* __restrict__ hdr,
-    float* __restrict__ pix_state, uint8_t* __restrict__ tile_done, int slab, int nslabs) {
+__device__ __forceinline__ void tile_pass(
+    TileSmem<kComp, kL>& sm, const int tile, const CamArgs& cam, const ProjRec* __restrict__ proj,
+    const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ tile_start, int slot,
+    const LevelCodes& lc, int C, int Crow, float* __restrict__ accum, float* __restrict__ comp,
+    WsHeader* __restrict__ hdr, float* __restrict__ pix_state, uint8_t* __restrict__ tile_done, int slab,
+    int nslabs) {
   const bool first_slab = slab == 0, last_slab = slab == nslabs - 1;
   using RK = typename RegionKey<kL>::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  TileSmem<kComp, kL>& sm = *reinterpret_cast<TileSmem<kComp, kL>*>(smem_raw);
   // code entries per slot (the concatenated level codes with several levels)
   const int s = kL == 1 ? lc.s[0] : lc.s_tot;
   const int32_t* __restrict__ code_idx = lc.ci[0];
   const float* __restrict__ code_val = lc.cv[0];
-  const int tile = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (pix_state && !first_slab && tile_done[tile]) return;  // every pixel stopped in an earlier slab
   const uint32_t begin = tile_start[tile];
@@ -742,6 +745,62 @@ __global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
   }
 }
 
+template <bool kComp, int kBW, int kL>
+__global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_tile_kernel(
+    const __grid_constant__ CamArgs cam, const ProjRec* __restrict__ proj,
+    const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ tile_start, int slot,
+    const __grid_constant__ LevelCodes lc, int C, int Crow, float* __restrict__ accum, float* __restrict__ comp,
+    WsHeader* __restrict__ hdr, float* __restrict__ pix_state, uint8_t* __restrict__ tile_done, int slab,
+    int nslabs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  tile_pass<kComp, kBW, kL>(*reinterpret_cast<TileSmem<kComp, kL>*>(smem_raw), blockIdx.x, cam, proj, keys,
+                            tile_start, slot, lc, C, Crow, accum, comp, hdr, pix_state, tile_done, slab, nslabs);
+}
+
+// Batched chunk: a persistent CTA takes (view, tile) items from the chunk's
+// counter until none is left and runs the same per-tile pass on each.  The
+// chunk's views travel in the kernel's parameter space (like the per-view
+// kernel's arguments, read through the constant cache), which keeps them out
+// of the pass's registers.  No CTA waits on another.
+struct DrainArgs {
+  uint32_t tile0[kMaxDrainJobs];  // first item of each view (ascending, tile0[0] = 0)
+  int njobs;
+  uint32_t total;
+  TileJob jobs[kMaxDrainJobs];
+};
+static_assert(sizeof(DrainArgs) <= 32000, "kernel parameter space");
+
+template <bool kComp, int kBW>
+__global__ void __launch_bounds__(kThreads, kComp ? 3 : 4) uplift_drain_kernel(const __grid_constant__ DrainArgs a,
+                                                                             unsigned* __restrict__ counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TileSmem<kComp, 1>& sm = *reinterpret_cast<TileSmem<kComp, 1>*>(smem_raw);
+  __shared__ uint32_t s_item;
+  __shared__ int s_job;
+  for (;;) {
+    __syncthreads();  // the previous pass is done with the tile's shared memory
+    if (threadIdx.x == 0) {
+      const uint32_t t = atomicAdd(counter, 1u);
+      int lo = 0;
+      if (t < a.total) {
+        int hi = a.njobs - 1;  // last view whose first item is at or before t
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (a.tile0[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+      }
+      s_item = t;
+      s_job = lo;
+    }
+    __syncthreads();
+    const uint32_t t = s_item;
+    if (t >= a.total) return;
+    const TileJob& job = a.jobs[s_job];
+    tile_pass<kComp, kBW, 1>(sm, (int)(t - a.tile0[s_job]), job.cam, job.proj, job.keys, job.tile_start, job.slot,
+                             job.lc, job.C, job.C, job.accum, job.comp, job.hdr, nullptr, nullptr, 0, 1);
+  }
+}
+
 struct SlabLaunch {
   float* pix_state;  // null with a single slab
   uint8_t* tile_done;
@@ -774,7 +833,52 @@ cudaError_t launch_tiles_shape(int warp_w, const CamArgs& cam, const UpliftWs& w
   }
 }
 
+template <bool kComp, int kBW>
+cudaError_t launch_drain_t(const DrainArgs& args, unsigned* counter, cudaStream_t st) {
+  const size_t smem = sizeof(TileSmem<kComp, 1>);
+  auto kern = uplift_drain_kernel<kComp, kBW>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  // CTAs resident per SM by the launch bounds (the shared memory of four fits);
+  // a CTA beyond them would only start later and drain what is left
+  const long long resident = (long long)num_sms() * (kComp ? 3 : 4);
+  const int grid = (int)(args.total < (uint32_t)resident ? args.total : (uint32_t)resident);
+  kern<<<grid, kThreads, smem, st>>>(args, counter);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_uplift_drain(const TileJob* jobs, const uint32_t* tile0, int njobs, unsigned* counter,
+                                bool compensated, int warp_w, cudaStream_t st) {
+  if (njobs <= 0) return cudaSuccess;
+  if (njobs > kMaxDrainJobs) return cudaErrorInvalidValue;
+  DrainArgs args;
+  memset(&args, 0, sizeof(args));
+  args.njobs = njobs;
+  uint32_t total = 0;
+  for (int j = 0; j < njobs; ++j) {
+    if (tile0[j] != total) return cudaErrorInvalidValue;
+    args.tile0[j] = tile0[j];
+    args.jobs[j] = jobs[j];
+    total += (uint32_t)jobs[j].tiles;
+  }
+  args.total = total;
+  if (total == 0) return cudaSuccess;
+  if (compensated) {
+    switch (warp_w) {
+      case 16: return launch_drain_t<true, 16>(args, counter, st);
+      case 4: return launch_drain_t<true, 4>(args, counter, st);
+      default: return launch_drain_t<true, 8>(args, counter, st);
+    }
+  }
+  switch (warp_w) {
+    case 16: return launch_drain_t<false, 16>(args, counter, st);
+    case 4: return launch_drain_t<false, 4>(args, counter, st);
+    default: return launch_drain_t<false, 8>(args, counter, st);
+  }
+}
 
 cudaError_t launch_uplift_tiles(const CamArgs& cam, const UpliftWs& ws, int slot, const LevelCodes& lc, int C,
                                 int Crow, float* accum, float* comp, int warp_w, cudaStream_t st, int slab,

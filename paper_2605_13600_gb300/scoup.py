@@ -819,6 +819,11 @@ class BatchedUplift:
     def set(self, lanes: int, warp_w: int) -> None:
         check(load().scoup_plan_set(self.plan, int(lanes), int(warp_w)))
 
+    def set_chunk(self, chunk_views: int) -> None:
+        """0: scenes on lanes; > 0: chunks of this many views, each composited
+        by one persistent tile launch (scoup_plan_set_chunk)."""
+        check(load().scoup_plan_set_chunk(self.plan, int(chunk_views)))
+
     def run(self, eager: bool = False, stream=None) -> None:
         check(load().scoup_uplift_batched(self.plan, SCOUP_BATCH_EAGER if eager else 0, _stream(stream)))
 
@@ -831,9 +836,9 @@ class BatchedUplift:
         pi = PlanInfo()
         check(load().scoup_plan_info_get(self.plan, ct.byref(pi)))
         return {"lanes": pi.lanes, "warp_w": pi.warp_w, "tuned": bool(pi.tuned), "graph_kernels": pi.graph_kernels,
-                "workspace_bytes": int(pi.workspace_bytes),
-                "tune": [{"lanes": pi.tune[i].lanes, "warp_w": pi.tune[i].warp_w, "ms": float(pi.tune[i].ms)}
-                         for i in range(pi.n_tune)]}
+                "workspace_bytes": int(pi.workspace_bytes), "chunk_views": pi.chunk_views,
+                "tune": [{"lanes": pi.tune[i].lanes, "warp_w": pi.tune[i].warp_w, "ms": float(pi.tune[i].ms),
+                          "chunk_views": pi.tune[i].chunk_views} for i in range(pi.n_tune)]}
 
     def accum_value(self, b: int):
         if self.compensated:

@@ -72,7 +72,7 @@ def test_every_declared_entry_point_has_a_python_wrapper():
         if fn.endswith(".h"):
             src = re.sub(r"/\*.*?\*/", "", open(os.path.join(root, "include", fn)).read(), flags=re.S)
             names |= set(re.findall(r"\b(scoup_[a-z0-9_]+)\s*\(", src))
-    host_only = {"scoup_last_error", "scoup_plan_create", "scoup_plan_destroy", "scoup_plan_set",
+    host_only = {"scoup_last_error", "scoup_plan_create", "scoup_plan_destroy", "scoup_plan_set", "scoup_plan_set_chunk",
                  "scoup_plan_stats", "scoup_plan_info_get", "scoup_autotune", "scoup_uplift_batched",
                  "scoup_uplift_levels", "scoup_uplift_levels_workspace_size",
                  "scoup_region_l2_grad_workspace_size", "scoup_decode_backward_workspace_size",

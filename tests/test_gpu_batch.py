@@ -2,7 +2,9 @@
 
 Every scene of a batch must give the results of its own plain uplift: the
 batch only changes which streams the launches run on, the order of FP32
-sums and the tile kernel's warp block shape.
+sums and the tile kernel's warp block shape.  The chunked form (one
+persistent tile launch per chunk of views of several scenes) is held to the
+same oracle, and its per-scene counters to those of the per-scene form.
 """
 import numpy as np
 import pytest
@@ -88,9 +90,13 @@ def test_batch_autotune(gb, batch_oracle):
     wls, ora = batch_oracle
     bu = gb.BatchedUplift(wls)
     info = bu.autotune(sample_views=2)
-    assert info["tuned"] and len(info["tune"]) == 9  # lanes {1, 2, 4} x warp blocks {8, 16, 4}
+    # lanes {1, 2, 4} x warp blocks {8, 16, 4}, then chunks {4, 8, 16} x lanes {1, 2, 4}
+    assert info["tuned"] and len(info["tune"]) == 18
+    assert sorted((t["chunk_views"], t["lanes"]) for t in info["tune"][9:]) == [
+        (c, l) for c in (4, 8, 16) for l in (1, 2, 4)]
     best = min(info["tune"], key=lambda t: t["ms"])
-    assert (info["lanes"], info["warp_w"]) == (best["lanes"], best["warp_w"])
+    assert (info["lanes"], info["warp_w"], info["chunk_views"]) == (best["lanes"], best["warp_w"],
+                                                                    best["chunk_views"])
     bu.run()
     _check_batch(bu, wls, ora, "tuned")
     bu.close()
@@ -104,7 +110,78 @@ def test_batch_compensated(gb, batch_oracle):
     bu.close()
 
 
-def test_batch_with_empty_scenes(gb, oracle_lib):
+@pytest.mark.parametrize("chunk,lanes", [(1, 1), (3, 2), (4, 1), (16, 2), (64, 1)])
+def test_batch_chunked_parity(gb, batch_oracle, chunk, lanes):
+    """One persistent tile launch per chunk: chunks of one view, chunks that
+    mix scenes, a chunk holding the whole batch; a graph replay recomputes
+    everything from zero."""
+    wls, ora = batch_oracle
+    bu = gb.BatchedUplift(wls)
+    bu.set(lanes, 8)
+    bu.set_chunk(chunk)
+    bu.run()
+    _check_batch(bu, wls, ora, f"chunked {chunk}x{lanes}")
+    info = bu.info()
+    assert info["chunk_views"] == chunk and info["graph_kernels"] > 0
+    for acc in bu.accum:
+        acc.fill_(123.0)
+    bu.run()
+    _check_batch(bu, wls, ora, f"chunked replay {chunk}x{lanes}")
+    bu.close()
+
+
+def test_batch_chunked_counters_match_per_scene_form(gb, batch_oracle):
+    """Every per-scene counter (visible, listed, evaluated, contributions,
+    flushes, atomics, ...) is a count over the same per-view, per-tile work in
+    both forms: the merge of the views' headers must give them exactly."""
+    wls, _ = batch_oracle
+    a = gb.BatchedUplift(wls)
+    a.set(2, 8)
+    a.run(eager=True)
+    sa = a.stats()
+    b = gb.BatchedUplift(wls)
+    b.set(2, 8)
+    b.set_chunk(5)
+    b.run(eager=True)
+    sb = b.stats()
+    for k, (x, y) in enumerate(zip(sa, sb)):
+        assert x == y, (k, x, y)
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("warp_w", [4, 16])
+def test_batch_chunked_eager_warp_shapes(gb, batch_oracle, warp_w):
+    wls, ora = batch_oracle
+    bu = gb.BatchedUplift(wls)
+    bu.set(2, warp_w)
+    bu.set_chunk(4)
+    bu.run(eager=True)
+    _check_batch(bu, wls, ora, f"chunked eager warp_w={warp_w}")
+    bu.close()
+
+
+def test_batch_chunked_compensated(gb, batch_oracle):
+    wls, ora = batch_oracle
+    bu = gb.BatchedUplift(wls, compensated=True)
+    bu.set(2, 8)
+    bu.set_chunk(3)
+    bu.run()
+    _check_batch(bu, wls, ora, "chunked compensated")
+    bu.close()
+
+
+def test_batch_chunk_argument_checked(gb, batch_oracle):
+    wls, _ = batch_oracle
+    bu = gb.BatchedUplift(wls)
+    for bad in (-1, 65):
+        with pytest.raises(gb.ScoupError):
+            bu.set_chunk(bad)
+    bu.close()
+
+
+@pytest.mark.parametrize("chunk", [0, 2])
+def test_batch_with_empty_scenes(gb, oracle_lib, chunk):
     """A scene with no Gaussians and a scene with no views ride along."""
     full = synth.tiny_workload(311, n=500, width=48, height=40, V=2, R=5, C=16, s=3, K=3)
     empty_n = synth.tiny_workload(312, n=1, width=48, height=40, V=2, R=5, C=16, s=3, K=3)
@@ -114,6 +191,7 @@ def test_batch_with_empty_scenes(gb, oracle_lib):
     no_views.map_offsets = no_views.map_offsets[:1]
     wls = [full, empty_n, no_views]
     bu = gb.BatchedUplift(wls)
+    bu.set_chunk(chunk)
     bu.run()
     st = bu.stats()
     assert all(s["status"] == 0 for s in st)
@@ -124,14 +202,20 @@ def test_batch_with_empty_scenes(gb, oracle_lib):
     bu.close()
 
 
-def test_cfg3_full_size_scenes_sampled_rows(gb, oracle_lib):
+@pytest.mark.parametrize("chunk", [None, 8])
+def test_cfg3_full_size_scenes_sampled_rows(gb, oracle_lib, chunk):
     """Two scenes of the 16-scene batch at full size (342k Gaussians x 58
     views at 680 x 508 and 229k x 72 views at 832 x 622, C = 256, s = K = 8)
-    in one autotuned batched graph; 8 seeded rows per scene against the oracle."""
+    in one autotuned batched graph (or the chunked form, 8 views per chunk on
+    two lanes); 8 seeded rows per scene against the oracle."""
     import torch
     wls = [synth.uplift_cfg3_scene(b, device="cuda") for b in (9, 6)]
     bu = gb.BatchedUplift(wls)
-    bu.autotune(sample_views=2)
+    if chunk is None:
+        bu.autotune(sample_views=2)
+    else:
+        bu.set(2, 8)
+        bu.set_chunk(chunk)
     bu.run()
     stats = bu.stats()
     for b, wl in enumerate(wls):
