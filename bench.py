@@ -44,6 +44,10 @@ def parse_args():
     ap.add_argument("--views", type=int, default=200, help="views of the workload (default: all 200)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-form-compare", action="store_true",
+                    help="skip timing the other uplift form beside the headline")
+    ap.add_argument("--per-view", action="store_true",
+                    help="time the per-view form (one tile launch per view) instead of the chunked form")
     ap.add_argument("--no-entropy", action="store_true",
                     help="skip the Top-K + entropy and entropy-filter measurement")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU oracle sample budget")
@@ -269,7 +273,9 @@ def run_gb300(args, dist):
     dev = torch.device("cuda", dist.local if dist.world > 1 else 0)
     torch.cuda.set_device(dev)
     wl = synth.uplift_cfg2(device=str(dev), V=args.views)
-    up = gb.Uplift(wl, device=str(dev))
+    # the chunked form (SCOUP_UPLIFT_CHUNKED): chunks of 8 views on two lanes,
+    # one persistent tile launch per chunk
+    up = gb.Uplift(wl, device=str(dev), chunked=not args.per_view)
     st0 = up.run(stats=True)
     if st0["status"] != 0:
         raise RuntimeError(f"uplift status {st0['status']}")
@@ -323,9 +329,18 @@ def run_gb300(args, dist):
         d2h = out_i.numel() * 4 + out_v.numel() * 4
 
         def e2e_step():
+            # every input copied from pinned host memory, then one scoup_uplift
+            # in the headline's form (the chunked form reads the maps on the device)
+            for k, t in host.items():
+                getattr(up, k).copy_(t, non_blocking=True)
+            up.run(stats=False)
+            out_i.copy_(up.topk_idx, non_blocking=True)
+            out_v.copy_(up.topk_val, non_blocking=True)
+
+        def e2e_host_maps_step():
             # scene and code table copied up front; the region maps (93% of the
-            # input bytes) are staged view by view by the library while earlier
-            # views compute (scoup_uplift_host_maps)
+            # input bytes) staged view by view by the library while earlier
+            # views compute (scoup_uplift_host_maps, the per-view form)
             for k, t in host.items():
                 if k != "region_maps":
                     getattr(up, k).copy_(t, non_blocking=True)
@@ -333,19 +348,26 @@ def run_gb300(args, dist):
             out_i.copy_(up.topk_idx, non_blocking=True)
             out_v.copy_(up.topk_val, non_blocking=True)
 
-        for _ in range(args.warmup):
-            e2e_step()
-        torch.cuda.synchronize()
-        dist.barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            e2e_step()
-        torch.cuda.synchronize()
-        t_e2e = dist.max((time.perf_counter() - t0) / args.steps)
+        def timed_e2e(step):
+            for _ in range(args.warmup):
+                step()
+            torch.cuda.synchronize()
+            dist.barrier()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                step()
+            torch.cuda.synchronize()
+            return dist.max((time.perf_counter() - t0) / args.steps)
+
+        t_e2e = timed_e2e(e2e_step)
+        t_hm = timed_e2e(e2e_host_maps_step)
         e2e = {"value": dist.world * contrib / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": t_e2e * 1e3,
-               "form": "pinned host inputs; scene and codes copied, region maps staged per view by "
-                       "scoup_uplift_host_maps; Top-K read back"}
+               "form": "pinned host inputs (scene, codes, region maps) copied, then scoup_uplift in the "
+                       "headline's form; Top-K read back",
+               "host_maps_form": {"value": dist.world * contrib / t_hm, "ms_per_step": t_hm * 1e3,
+                                  "form": "region maps staged per view by scoup_uplift_host_maps (per-view "
+                                          "form) while earlier views compute"}}
 
 
     # per-phase kernel times (CUDA events on the launching stream)
@@ -359,11 +381,12 @@ def run_gb300(args, dist):
     tiles_ms, tiles_n = prof.get("uplift_tiles", (0.0, 1))
     per_launch_s = tiles_ms / tiles_n / 1e3
 
-    # roofline of the dominant kernel (per-tile composite + scatter, one launch per view)
+    # roofline of the dominant kernel (per-tile composite + scatter: one drain
+    # launch per chunk of views, or one launch per view in the per-view form)
     pk = peaks()
     V = len(up.cams)
-    contrib_per_launch = contrib / V
-    evaluated_per_launch = st0["evaluated_pairs"] / V
+    views_per_launch = V / (tiles_n / 2)
+    evaluated_per_launch = st0["evaluated_pairs"] / V * views_per_launch
     # FP32-pipe work of Eq. 2 for every evaluated Gaussian-pixel pair, accepted
     # or not (a lower bound for any implementation; the exp runs on the SFU and
     # is not counted, nor e = alpha T of the accepted pairs): exponent 2
@@ -377,9 +400,10 @@ def run_gb300(args, dist):
     npx = up.cams[0].width * up.cams[0].height
     # algorithmic HBM bytes of one view: region map + one FP32 read-modify-write per
     # accumulator update issued + one 32-byte record per visible Gaussian
-    bytes_launch = 4.0 * npx + 8.0 * st0["atomics"] / V + 32.0 * st0["visible"] / V
-    traffic = profiled_traffic("uplift_tile_kernel", "uplift_tile.cu")
-    roofline = {"kernel": "uplift_tile_kernel", "bound": "alu", "achieved": achieved / 1e12,
+    bytes_launch = (4.0 * npx + 8.0 * st0["atomics"] / V + 32.0 * st0["visible"] / V) * views_per_launch
+    kname = "uplift_tile_kernel" if args.per_view else "uplift_drain_kernel"
+    traffic = profiled_traffic(kname, "uplift_tile.cu")
+    roofline = {"kernel": kname, "views_per_launch": views_per_launch, "bound": "alu", "achieved": achieved / 1e12,
                 "peak": alu_peak / 1e12, "unit": "Tops/s (FP32 lane ops)",
                 "frac": achieved / alu_peak, "traffic": traffic,
                 "per_launch_ms": per_launch_s * 1e3,
@@ -390,6 +414,29 @@ def run_gb300(args, dist):
                 "ops_per_launch": ops, "op_count": "15 FP32 ops per evaluated pair (exp on the SFU not counted)",
                 "peak_source": pk["source"] + f" (HBM); FP32 lanes x max SM clock x {n_sms} SMs (ALU)"}
     roofline["step"] = step_roofline(gb, up, wl, st0, t_step, pk, alu_peak)
+
+    # the other form on the same workload, for comparison (not the headline)
+    other = None
+    if not args.no_form_compare:
+        upo = gb.Uplift(wl, device=str(dev), dup_capacity=up.dup_capacity, chunked=args.per_view)
+        so = upo.run(stats=True)
+        if so["status"] != 0 or so["contributions"] != contrib:
+            raise RuntimeError("the two uplift forms disagree on the contributions")
+        for _ in range(args.warmup):
+            upo.run(stats=False)
+        torch.cuda.synchronize()
+        dist.barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            upo.run(stats=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t_o = dist.max(ev0.elapsed_time(ev1) / 1e3 / args.steps)
+        other = {"value": dist.world * contrib / t_o, "ms_per_step": t_o * 1e3,
+                 "form": ("chunked: 8 views per chunk on two lanes, one persistent tile launch per chunk"
+                          if args.per_view else "per-view: one tile launch per view, two view pipelines")}
+        del upo
+        torch.cuda.empty_cache()
 
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
@@ -436,6 +483,10 @@ def run_gb300(args, dist):
                        "evaluated_pairs_per_step": st0["evaluated_pairs"],
                        "l2": "inputs larger than L2 (region maps 578 MB, accumulator 1.02 GB)",
                        "parallelism": f"replica x{dist.world}"},
+            "form": ("per-view: one tile launch per view, two view pipelines" if args.per_view else
+                     "chunked (SCOUP_UPLIFT_CHUNKED): 8 views per chunk on two lanes, one persistent tile "
+                     "launch per chunk"),
+            "other_form": other,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk, "phase_ms_per_step": step_ms,
             "stats": {k: st0[k] for k in ("visible", "duplicates", "flushes", "atomics")},

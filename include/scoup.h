@@ -102,6 +102,7 @@ int scoup_uplift_plan(const scoup_scene* scene, const scoup_camera* cams, int32_
 
 #define SCOUP_ACCUM_CONTINUE 1    /* accum_mode: add to the accumulator instead of zeroing it */
 #define SCOUP_ACCUM_COMPENSATED 2 /* accum_mode: compensated (TwoSum) FP32 accumulation */
+#define SCOUP_UPLIFT_CHUNKED 4    /* accum_mode: composite the views in chunks (see scoup_uplift) */
 
 /* Sparse coefficient uplift.  For every view v (cams[v], host array of V),
  * rasterizes the scene with standard 3DGS compositing (Sec. 3, Eq. 2) and
@@ -126,11 +127,20 @@ int scoup_uplift_plan(const scoup_scene* scene, const scoup_camera* cams, int32_
  *               followed by their compensation terms (value = sum + term).
  *  accum_mode   bit flags.  Without SCOUP_ACCUM_CONTINUE accum is zeroed
  *               first; with it the call adds to the current contents (resume
- *               a chunked uplift).  SCOUP_ACCUM_COMPENSATED: every FP32
+ *               an uplift whose views were split over several calls).
+ *               SCOUP_ACCUM_COMPENSATED: every FP32
  *               addition into the per-tile partials and into accum carries
  *               its exact rounding error (TwoSum) into a compensation term,
  *               as does the product code value x weight; Top-K ranks
  *               sum + term.  Slower (one more atomic per update).
+ *               SCOUP_UPLIFT_CHUNKED (the fast form; single level): the
+ *               views are cut into chunks of 8 on two lanes (streams); each
+ *               view of a chunk is projected and binned into a view part of
+ *               its own, then ONE persistent tile launch composites every
+ *               (view, tile) item of the chunk, its CTAs taking items from
+ *               an atomic counter.  Same results up to the order of FP32
+ *               atomic additions; same counters.  The workspace must then be
+ *               sized by scoup_uplift_chunked_workspace_size (16 view parts).
  *  topk_idx     int32 [n, K] or NULL (accumulate only); topk_val float32 [n, K].
  *  workspace    device scratch of ws_bytes >= scoup_uplift_workspace_size().
  *  stats        HOST scoup_stats* or NULL; when given, the call synchronises
@@ -147,6 +157,12 @@ int scoup_uplift(const scoup_scene* scene, const scoup_camera* cams, int32_t V,
                  const int32_t* code_idx, const float* code_val, int32_t s, int32_t C, int32_t K,
                  float* accum, int32_t accum_mode, int32_t* topk_idx, float* topk_val,
                  void* workspace, size_t ws_bytes, scoup_stats* stats, void* stream);
+
+/* Workspace bytes for scoup_uplift with SCOUP_UPLIFT_CHUNKED: the scene part
+ * and 2 x 8 view parts, each holding dup_capacity (Gaussian, tile) keys (the
+ * largest per-view pair count, scoup_uplift_plan).  0 on invalid arguments. */
+size_t scoup_uplift_chunked_workspace_size(int64_t n, int32_t max_width, int32_t max_height,
+                                           int64_t dup_capacity);
 
 /* Workspace bytes for scoup_uplift_host_maps: a staging ring of 4 view maps
  * of max_width x max_height int32 entries, then a scoup_uplift workspace

@@ -21,6 +21,7 @@ SCOUP_ERR_TIMEOUT = -6
 
 SCOUP_ACCUM_CONTINUE = 1
 SCOUP_ACCUM_COMPENSATED = 2
+SCOUP_UPLIFT_CHUNKED = 4
 
 
 class ScoupError(RuntimeError):
@@ -90,6 +91,7 @@ PROTOS = {
     "scoup_version": (ct.c_char_p, []),
     "scoup_last_error": (ct.c_char_p, []),
     "scoup_uplift_workspace_size": (SZ, [I64, I32, I32, I64]),
+    "scoup_uplift_chunked_workspace_size": (SZ, [I64, I32, I32, I64]),
     "scoup_uplift_plan": (ct.c_int, [ct.POINTER(Scene), P, I32, P, SZ, ct.POINTER(I64), P]),
     "scoup_uplift": (ct.c_int, [ct.POINTER(Scene), P, I32, P, P, I32, P, P, I32, I32, I32, P, I32,
                                 P, P, P, SZ, ct.POINTER(Stats), P]),

@@ -9,7 +9,7 @@
 #include <string>
 #include <vector>
 
-#include "scoup_internal.cuh"
+#include "drain.cuh"
 
 namespace scoup {
 
@@ -223,6 +223,31 @@ cudaStream_t map_copy_stream() {
   return streams[dev];
 }
 
+// The library's streams of the chunked form beyond the caller's and the view
+// lane stream: [0] the second chunk lane, [1], [2] the lanes' second
+// projection streams (one set per host thread and device).
+cudaStream_t chunk_stream(int i) {
+  thread_local cudaStream_t streams[64][3] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || i < 0 || i >= 3) return nullptr;
+  if (!streams[dev][i] && cudaStreamCreateWithFlags(&streams[dev][i], cudaStreamNonBlocking) != cudaSuccess)
+    streams[dev][i] = nullptr;
+  return streams[dev][i];
+}
+
+// Chunked form of one scene: kChunkLanes lanes of kChunkViews views per
+// chunk, i.e. kChunkLanes x kChunkViews view parts in the workspace.
+constexpr int kChunkLanes = 2, kChunkViews = 8;
+
+// Bytes of the chunked layout with `dup` keys per view part.
+size_t chunked_bytes(int64_t n, int max_tiles, int64_t code_rows_k, int64_t dup) {
+  const size_t part = align_up(sizeof(WsHeader)) + lane_bytes(n, max_tiles) +
+                      align_up(sizeof(unsigned long long) * (size_t)dup);
+  return shared_bytes(n, code_rows_k) + (size_t)(kChunkLanes * kChunkViews) * part +
+         align_up(sizeof(unsigned) * kChunkLanes);
+}
+
 // Depth slabs of the uplift.  Splitting a view into front-to-back slabs bins
 // far fewer (Gaussian, tile) pairs (3 slabs at the 5% and 20% depth quantiles
 // list 13% of the pairs of a 1M-Gaussian 988x731 view), but every slab pays a
@@ -309,6 +334,109 @@ int finish_with_stats(const WsHeader* dev_hdr, scoup_stats* stats, cudaStream_t 
 namespace scoup {
 int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
 
+// The views of one scene in chunks (SCOUP_UPLIFT_CHUNKED): view v goes to
+// chunk v / kChunkViews on lane chunk % kChunkLanes; each chunk is projected
+// and binned into the lane's view parts, composited by one drain launch and
+// merged into the scene header sw.hdr.  The scene part (header, Morton-ordered
+// copy) is set up; the view parts follow it in the workspace.
+static int uplift_views_chunked(const UpliftCall& c, const int32_t* region_maps, int32_t R_total, const UpliftWs& sw,
+                                void* workspace, size_t ws_bytes, int max_tiles, int64_t code_rows_k,
+                                const int32_t* ci, const float* cv, int s_eff, float* comp, int warp_w,
+                                cudaStream_t st) {
+  const int64_t n = c.scene->n;
+  const int V = c.V;
+  constexpr int kParts = kChunkLanes * kChunkViews;
+  // the layout: scene part, kParts x (header, view part, keys), lane counters
+  const size_t fixed = chunked_bytes(n, max_tiles, code_rows_k, 0);
+  if (ws_bytes < fixed + (size_t)kParts * 256)
+    return fail(SCOUP_ERR_OOM, "workspace too small for the chunked form: %zu < %zu bytes before tile lists", ws_bytes,
+                fixed + (size_t)kParts * 256);
+  const size_t keys_each = (ws_bytes - fixed) / kParts / 256 * 256;
+  char* p = (char*)workspace;
+  size_t off = shared_bytes(n, code_rows_k);
+  UpliftWs parts[kParts];
+  DrainViewInit init[kParts];
+  for (int q = 0; q < kParts; ++q) {
+    UpliftWs& w = parts[q];
+    w = sw;
+    w.hdr = (WsHeader*)(p + off);
+    off += align_up(sizeof(WsHeader));
+    off += carve_view_part(p + off, n, max_tiles, &w);
+    w.keys = (unsigned long long*)(p + off);
+    w.dup_capacity = (int64_t)(keys_each / sizeof(unsigned long long));
+    off += keys_each;
+    init[q] = DrainViewInit{w.hdr, w.tile_count, w.tile_glob, w.dhist};
+  }
+  unsigned* counters = (unsigned*)(p + off);
+  cudaError_t e;
+  if ((e = launch_view_init(init, kParts, max_tiles, st)) != cudaSuccess) return cuda_fail(e, "view parts");
+  // streams: lane 0 is `st`, lane 1 a library stream; each lane has a second projection stream
+  const cudaStream_t lane_st[kChunkLanes] = {st, chunk_stream(0)};
+  const cudaStream_t aux_st[kChunkLanes] = {chunk_stream(1), chunk_stream(2)};
+  if (!lane_st[1] || !aux_st[0] || !aux_st[1]) return fail(SCOUP_ERR_CUDA, "could not create the chunk streams");
+  cudaEvent_t ev[2 + 2 * kChunkLanes] = {};
+  for (cudaEvent_t& x : ev)
+    if ((e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming)) != cudaSuccess) {
+      for (cudaEvent_t y : ev)
+        if (y) cudaEventDestroy(y);
+      return cuda_fail(e, "chunk events");
+    }
+  const cudaEvent_t fork = ev[0], join = ev[1];
+  int rc = SCOUP_OK;
+  const int nchunks = (V + kChunkViews - 1) / kChunkViews;
+  const bool lane1 = nchunks > 1;
+  if (lane1 && ((e = cudaEventRecord(fork, st)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(lane_st[1], fork, 0)) != cudaSuccess))
+    rc = cuda_fail(e, "chunk lanes");
+  TileJob jobs[kChunkViews];
+  uint32_t tile0[kChunkViews];
+  UpliftWs views[kChunkViews];
+  const scoup_scene* scenes[kChunkViews];
+  for (int ch = 0; ch < nchunks && rc == SCOUP_OK; ++ch) {
+    const int lane = ch % kChunkLanes;
+    const int v0 = ch * kChunkViews, nv = std::min(kChunkViews, V - v0);
+    uint32_t items = 0;
+    for (int k = 0; k < nv; ++k) {
+      const int v = v0 + k;
+      const UpliftWs& w = parts[lane * kChunkViews + k];
+      TileJob& J = jobs[k];
+      J = TileJob();
+      J.cam = cam_args(c.cams[v]);
+      J.lc = LevelCodes();
+      J.lc.L = 1;
+      J.lc.s_tot = s_eff;
+      J.lc.rmap[0] = region_maps + c.map_offsets[v];
+      J.lc.ci[0] = ci;
+      J.lc.cv[0] = cv;
+      J.lc.s[0] = s_eff;
+      J.lc.R[0] = R_total;
+      J.proj = w.proj;
+      J.keys = w.keys;
+      J.tile_start = w.tile_start;
+      J.accum = c.accum;
+      J.comp = comp;
+      J.hdr = w.hdr;
+      J.scene_hdr = sw.hdr;
+      J.slot = (ch / kChunkLanes) & 1;
+      J.C = c.C;
+      J.tiles = J.cam.gx * J.cam.gy;
+      J.scene = 0;
+      tile0[k] = items;
+      items += (uint32_t)J.tiles;
+      views[k] = w;
+      scenes[k] = c.scene;
+    }
+    const ChunkStreams cs{lane_st[lane], aux_st[lane], ev[2 + 2 * lane], ev[3 + 2 * lane]};
+    rc = run_chunk(jobs, tile0, nv, views, scenes, counters + lane, comp != nullptr, warp_w, cs);
+  }
+  // join even on an error, so that a capture in progress stays well formed
+  if (lane1 && ((e = cudaEventRecord(join, lane_st[1])) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(st, join, 0)) != cudaSuccess) && rc == SCOUP_OK)
+    rc = cuda_fail(e, "chunk lanes");
+  for (cudaEvent_t y : ev) cudaEventDestroy(y);
+  return rc;
+}
+
 int uplift_call(const UpliftCall& c, void* workspace, size_t ws_bytes, int warp_w, const WsHeader** hdr_out,
                 cudaStream_t st, int view_lanes) {
   const scoup_scene* scene = c.scene;
@@ -354,8 +482,12 @@ int uplift_call(const UpliftCall& c, void* workspace, size_t ws_bytes, int warp_
   }
   if (L > 1 && s_tot > 64) return fail(SCOUP_ERR_INVALID_ARG, "levels: sum of s = %d above 64", s_tot);
   const int Crow = L * C;
-  if (accum_mode & ~(SCOUP_ACCUM_CONTINUE | SCOUP_ACCUM_COMPENSATED))
-    return fail(SCOUP_ERR_INVALID_ARG, "accum_mode=%d: only SCOUP_ACCUM_CONTINUE and SCOUP_ACCUM_COMPENSATED", accum_mode);
+  if (accum_mode & ~(SCOUP_ACCUM_CONTINUE | SCOUP_ACCUM_COMPENSATED | SCOUP_UPLIFT_CHUNKED))
+    return fail(SCOUP_ERR_INVALID_ARG,
+                "accum_mode=%d: only SCOUP_ACCUM_CONTINUE, SCOUP_ACCUM_COMPENSATED and SCOUP_UPLIFT_CHUNKED", accum_mode);
+  const bool chunked = (accum_mode & SCOUP_UPLIFT_CHUNKED) != 0;
+  if (chunked && (c.L > 0 || c.maps_on_host))
+    return fail(SCOUP_ERR_INVALID_ARG, "SCOUP_UPLIFT_CHUNKED is a mode of scoup_uplift (one level, device region maps)");
   if (scene->n > 0 && !accum) return fail(SCOUP_ERR_INVALID_ARG, "accum is NULL");
   if ((topk_idx == nullptr) != (topk_val == nullptr))
     return fail(SCOUP_ERR_INVALID_ARG, "topk_idx and topk_val must both be given or both be NULL");
@@ -377,7 +509,7 @@ int uplift_call(const UpliftCall& c, void* workspace, size_t ws_bytes, int warp_
 
   // two view pipelines (even / odd views on two streams) when the workspace holds them
   const int lanes =
-      (view_lanes >= 2 && V >= 2 && ws_bytes >= uplift_fixed_bytes(scene->n, max_tiles, code_rows_k, 2) + 64) ? 2 : 1;
+      (!chunked && view_lanes >= 2 && V >= 2 && ws_bytes >= uplift_fixed_bytes(scene->n, max_tiles, code_rows_k, 2) + 64) ? 2 : 1;
   int32_t* fci = nullptr;
   float* fcv = nullptr;
   UpliftWs wsl[2];
@@ -392,7 +524,7 @@ int uplift_call(const UpliftCall& c, void* workspace, size_t ws_bytes, int warp_
       (e = cudaMemsetAsync(accum, 0, sizeof(float) * (size_t)n * (size_t)Crow * (compensated ? 2 : 1), st)) !=
           cudaSuccess)
     return cuda_fail(e, "memset accum");
-  for (int l = 0; l < lanes; ++l)
+  for (int l = 0; l < (chunked ? 0 : lanes); ++l)
     if ((e = cudaMemsetAsync(wsl[l].tile_glob, 0, sizeof(uint32_t) * ((size_t)max_tiles + 1), st)) != cudaSuccess ||
         (e = cudaMemsetAsync(wsl[l].tile_count, 0, sizeof(uint32_t) * ((size_t)max_tiles + 1), st)) != cudaSuccess ||
         (e = cudaMemsetAsync(wsl[l].dhist, 0, sizeof(uint32_t) * kDepthBuckets, st)) != cudaSuccess)
@@ -409,7 +541,16 @@ int uplift_call(const UpliftCall& c, void* workspace, size_t ws_bytes, int warp_
     cv = fcv;
     s_eff = K;
   }
-  if (n > 0 && V > 0) {
+  if (n > 0 && V > 0 && chunked) {
+    {
+      PhaseScope ps(SCOUP_PHASE_TAU, st);
+      if ((e = launch_reorder(*scene, ws, st)) != cudaSuccess) return cuda_fail(e, "reorder");
+    }
+    const int rcc = uplift_views_chunked(c, region_maps, R_total, ws, workspace, ws_bytes, max_tiles, code_rows_k, ci,
+                                         cv, s_eff, comp, warp_w, st);
+    if (rcc != SCOUP_OK) return rcc;
+  }
+  if (n > 0 && V > 0 && !chunked) {
     {
       PhaseScope ps(SCOUP_PHASE_TAU, st);
       if ((e = launch_reorder(*scene, ws, st)) != cudaSuccess) return cuda_fail(e, "reorder");
@@ -554,6 +695,47 @@ size_t uplift_required_bytes(int64_t n, const scoup_camera* cams, int32_t V, int
   return uplift_fixed_bytes(n, max_tiles, code_rows_k) + sizeof(unsigned long long) * (size_t)dup_capacity;
 }
 
+int run_chunk(const TileJob* jobs, const uint32_t* tile0, int njobs, const UpliftWs* views,
+              const scoup_scene* const* scenes, unsigned* counter, bool compensated, int warp_w,
+              const ChunkStreams& cs) {
+  auto fail_cuda = [](cudaError_t e, const char* where) { return cuda_fail(e, where); };
+  if (njobs <= 0) return SCOUP_OK;
+  if (njobs > kMaxDrainJobs) return set_error(SCOUP_ERR_INVALID_ARG, "more views in a chunk than one drain takes");
+  cudaError_t e;
+  int rc = SCOUP_OK;
+  // the second stream starts after the lane's previous drain (the view parts are reused)
+  const bool split = njobs > 1 && cs.as != nullptr;
+  if (split && ((e = cudaEventRecord(cs.fork, cs.ls)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(cs.as, cs.fork, 0)) != cudaSuccess))
+    return fail_cuda(e, "fork");
+  for (int j = 0; j < njobs && rc == SCOUP_OK; ++j) {
+    const cudaStream_t vs = (split && (j & 1)) ? cs.as : cs.ls;
+    const TileJob& J = jobs[j];
+    {
+      PhaseScope ps(SCOUP_PHASE_PREPROCESS, vs);
+      if ((e = launch_preprocess(*scenes[j], J.cam, views[j], J.slot, vs)) != cudaSuccess) {
+        rc = fail_cuda(e, "preprocess");
+        break;
+      }
+    }
+    PhaseScope ps(SCOUP_PHASE_BINNING, vs);
+    if ((e = launch_binning(J.cam, scenes[j]->n, views[j], J.slot, vs)) != cudaSuccess) rc = fail_cuda(e, "binning");
+  }
+  // join even on an error, so that a capture in progress stays well formed
+  if (split && ((e = cudaEventRecord(cs.join, cs.as)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(cs.ls, cs.join, 0)) != cudaSuccess) && rc == SCOUP_OK)
+    rc = fail_cuda(e, "join");
+  if (rc != SCOUP_OK) return rc;
+  if ((e = cudaMemsetAsync(counter, 0, sizeof(unsigned), cs.ls)) != cudaSuccess) return fail_cuda(e, "counter");
+  {
+    PhaseScope ps(SCOUP_PHASE_UPLIFT_TILES, cs.ls);
+    if ((e = launch_uplift_drain(jobs, tile0, njobs, counter, compensated, warp_w, cs.ls)) != cudaSuccess)
+      return fail_cuda(e, "drain");
+  }
+  if ((e = launch_view_merge(jobs, njobs, cs.ls)) != cudaSuccess) return fail_cuda(e, "merge");
+  return SCOUP_OK;
+}
+
 size_t uplift_scene_part_bytes(int64_t n, int64_t code_rows_k) { return shared_bytes(n, code_rows_k); }
 
 size_t uplift_view_part_bytes(int64_t n, int max_tiles) { return lane_bytes(n, max_tiles); }
@@ -582,6 +764,12 @@ extern "C" {
 const char* scoup_version(void) { return "scoup-gb300 0.1.0 (sm_103a)"; }
 
 const char* scoup_last_error(void) { return g_err.c_str(); }
+
+size_t scoup_uplift_chunked_workspace_size(int64_t n, int32_t max_width, int32_t max_height,
+                                           int64_t dup_capacity) {
+  if (n < 0 || max_width <= 0 || max_height <= 0 || dup_capacity < 0) return 0;
+  return chunked_bytes(n, tiles_of(max_width, max_height), 0, dup_capacity);
+}
 
 size_t scoup_uplift_workspace_size(int64_t n, int32_t max_width, int32_t max_height,
                                    int64_t dup_capacity) {

@@ -15,6 +15,7 @@
 // the first chunk (header, accumulator, Morton-ordered copy, codes cut to K
 // entries) and gets its Top-K after the last.
 #include <stdio.h>
+#include <string.h>
 
 #include <algorithm>
 #include <vector>
@@ -27,10 +28,17 @@ namespace {
 constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-// Resets the view parts before a batch: headers (counters, status, the
+constexpr int kMaxParts = 64;
+
+struct InitArgs {
+  DrainViewInit part[kMaxParts];
+  int max_tiles;
+};
+
+// Resets view parts before their first use: headers (counters, status, the
 // depth range of every slot) and the binning counters.
-__global__ void drain_init_kernel(const DrainViewInit* __restrict__ parts, int max_tiles) {
-  const DrainViewInit v = parts[blockIdx.y];
+__global__ void view_init_kernel(const __grid_constant__ InitArgs a) {
+  const DrainViewInit& v = a.part[blockIdx.y];
   const int stride = gridDim.x * blockDim.x;
   const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
   if (t0 == 0) {
@@ -38,17 +46,23 @@ __global__ void drain_init_kernel(const DrainViewInit* __restrict__ parts, int m
     for (int q = 0; q < 4; ++q) { h.drange[q][0] = 0xffffffffu; h.drange[q][1] = 0u; }
     *v.hdr = h;
   }
-  for (int t = t0; t <= max_tiles; t += stride) { v.tile_count[t] = 0u; v.tile_glob[t] = 0u; }
+  for (int t = t0; t <= a.max_tiles; t += stride) { v.tile_count[t] = 0u; v.tile_glob[t] = 0u; }
   for (int t = t0; t < kDepthBuckets; t += stride) v.dhist[t] = 0u;
 }
 
+struct MergeArgs {
+  WsHeader* view[kMaxDrainJobs];
+  WsHeader* scene[kMaxDrainJobs];
+  int n;
+};
+
 // After a chunk's drain: adds each view's counters into its scene's header
 // and clears them for the view part's next use.
-__global__ void drain_merge_kernel(const TileJob* __restrict__ jobs, int njobs) {
+__global__ void view_merge_kernel(const __grid_constant__ MergeArgs a) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= njobs) return;
-  WsHeader* v = jobs[j].hdr;
-  WsHeader* s = jobs[j].scene_hdr;
+  if (j >= a.n) return;
+  WsHeader* v = a.view[j];
+  WsHeader* s = a.scene[j];
   atomicAdd(&s->visible, v->visible);
   atomicAdd(&s->duplicates, v->duplicates);
   atomicAdd(&s->evaluated, v->evaluated);
@@ -66,6 +80,37 @@ __global__ void drain_merge_kernel(const TileJob* __restrict__ jobs, int njobs) 
 }
 
 }  // namespace
+
+cudaError_t launch_view_init(const DrainViewInit* parts, int nparts, int max_tiles, cudaStream_t st) {
+  for (int q0 = 0; q0 < nparts; q0 += kMaxParts) {
+    InitArgs a;
+    memset(&a, 0, sizeof(a));
+    const int np = std::min(kMaxParts, nparts - q0);
+    for (int q = 0; q < np; ++q) a.part[q] = parts[q0 + q];
+    a.max_tiles = max_tiles;
+    const int gx = std::min(64, (max_tiles + 1 + 255) / 256);
+    view_init_kernel<<<dim3(gx, np), 256, 0, st>>>(a);
+    g_launches += 1;
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_view_merge(const TileJob* jobs, int njobs, cudaStream_t st) {
+  if (njobs <= 0) return cudaSuccess;
+  if (njobs > kMaxDrainJobs) return cudaErrorInvalidValue;
+  MergeArgs m;
+  memset(&m, 0, sizeof(m));
+  m.n = njobs;
+  for (int j = 0; j < njobs; ++j) {
+    m.view[j] = jobs[j].hdr;
+    m.scene[j] = jobs[j].scene_hdr;
+  }
+  view_merge_kernel<<<(njobs + 63) / 64, 64, 0, st>>>(m);
+  g_launches += 1;
+  return cudaGetLastError();
+}
 
 namespace {
 
@@ -137,12 +182,9 @@ int drain_prepare(DrainLayout* d, const std::vector<scoup_batch_item>& items, co
   const size_t part_bytes = align_up(uplift_view_part_bytes(n_max, max_tiles));
   const size_t keys_bytes = align_up(sizeof(unsigned long long) * (size_t)dups_max);
   const size_t hdr_bytes = align_up(sizeof(WsHeader));
-  const size_t sched_bytes = align_up(sizeof(TileJob) * (size_t)std::max(njobs, 1)) +
-                             align_up(sizeof(unsigned) * (size_t)std::max(nchunks, 1)) +
-                             align_up(sizeof(DrainViewInit) * (size_t)nparts);
-  const size_t need = scene_bytes + (size_t)nparts * (hdr_bytes + part_bytes + keys_bytes) + sched_bytes;
-  cudaError_t e = cudaDeviceSynchronize();  // a replay still running may read the old schedule
-  if (e != cudaSuccess) return set_error(SCOUP_ERR_CUDA, cudaGetErrorString(e));
+  const size_t need = scene_bytes + (size_t)nparts * (hdr_bytes + part_bytes + keys_bytes) +
+                      align_up(sizeof(unsigned) * (size_t)lanes);
+  cudaError_t e;
   if ((int)d->aux.size() != lanes) {
     release_aux(d);
     for (int l = 0; l < lanes; ++l) {
@@ -162,6 +204,8 @@ int drain_prepare(DrainLayout* d, const std::vector<scoup_batch_item>& items, co
     }
   }
   if (need > d->bytes) {
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess)  // a run still in flight may use the old memory
+      return set_error(SCOUP_ERR_CUDA, cudaGetErrorString(e));
     if (d->mem) cudaFree(d->mem);
     d->mem = nullptr;
     d->bytes = 0;
@@ -184,7 +228,7 @@ int drain_prepare(DrainLayout* d, const std::vector<scoup_batch_item>& items, co
     if (code_rows_k == 0) { d->fci[b] = nullptr; d->fcv[b] = nullptr; }
   }
   d->view.assign(nparts, UpliftWs());
-  std::vector<DrainViewInit> init(nparts);
+  d->init.assign(nparts, DrainViewInit());
   for (int q = 0; q < nparts; ++q) {
     UpliftWs& w = d->view[q];
     w.hdr = (WsHeader*)(p + off);
@@ -193,13 +237,9 @@ int drain_prepare(DrainLayout* d, const std::vector<scoup_batch_item>& items, co
     w.keys = (unsigned long long*)(p + off);
     w.dup_capacity = dups_max;
     off += keys_bytes;
-    init[q] = DrainViewInit{w.hdr, w.tile_count, w.tile_glob, w.dhist};
+    d->init[q] = DrainViewInit{w.hdr, w.tile_count, w.tile_glob, w.dhist};
   }
-  d->jobs_dev = (TileJob*)(p + off);
-  off += align_up(sizeof(TileJob) * (size_t)std::max(njobs, 1));
   d->counters_dev = (unsigned*)(p + off);
-  off += align_up(sizeof(unsigned) * (size_t)std::max(nchunks, 1));
-  d->init_dev = (DrainViewInit*)(p + off);
   // the schedule
   d->jobs.assign(njobs, TileJob());
   d->job_view_part.assign(njobs, 0);
@@ -242,12 +282,6 @@ int drain_prepare(DrainLayout* d, const std::vector<scoup_batch_item>& items, co
     }
     d->chunk_items[c] = items_c;
   }
-  if (njobs > 0 && (e = cudaMemcpy(d->jobs_dev, d->jobs.data(), sizeof(TileJob) * (size_t)njobs,
-                                   cudaMemcpyHostToDevice)) != cudaSuccess)
-    return set_error(SCOUP_ERR_CUDA, cudaGetErrorString(e));
-  if ((e = cudaMemcpy(d->init_dev, init.data(), sizeof(DrainViewInit) * (size_t)nparts, cudaMemcpyHostToDevice)) !=
-      cudaSuccess)
-    return set_error(SCOUP_ERR_CUDA, cudaGetErrorString(e));
   d->chunk = chunk;
   d->lanes = lanes;
   d->sample = sample;
@@ -283,56 +317,34 @@ int drain_enqueue(DrainLayout* d, const std::vector<scoup_batch_item>& items, in
       return fail_cuda(e, "code top-k");
     if (it.V > 0 && (e = launch_reorder(it.scene, sw, st)) != cudaSuccess) return fail_cuda(e, "reorder");
   }
-  // the view parts and the chunks' counters
-  if (nparts > 0) {
-    const int gx = std::min(64, (d->max_tiles + 1 + 255) / 256);
-    drain_init_kernel<<<dim3(gx, nparts), 256, 0, st>>>(d->init_dev, d->max_tiles);
-    g_launches += 1;
-    if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "init");
-  }
-  if (nchunks > 0 && (e = cudaMemsetAsync(d->counters_dev, 0, sizeof(unsigned) * (size_t)nchunks, st)) != cudaSuccess)
-    return fail_cuda(e, "counters");
-  // chunks on the lanes: project and bin each view, drain the chunk, merge its counters
+  // the view parts
+  if (nparts > 0 && (e = launch_view_init(d->init.data(), nparts, d->max_tiles, st)) != cudaSuccess)
+    return fail_cuda(e, "init");
+  // chunks on the lanes
   const int used = std::min(d->lanes, nchunks);
   if (used > 0 && (e = cudaEventRecord(fork_ev, st)) != cudaSuccess) return fail_cuda(e, "fork");
   for (int l = 0; l < used; ++l)
     if ((e = cudaStreamWaitEvent(lane_st[l], fork_ev, 0)) != cudaSuccess) return fail_cuda(e, "fork wait");
   int rc = SCOUP_OK;
+  std::vector<UpliftWs> vw;
+  std::vector<const scoup_scene*> vs;
   for (int c = 0; c < nchunks && rc == SCOUP_OK; ++c) {
     const int lane = c % d->lanes;
-    const cudaStream_t ls = lane_st[lane], as = d->aux[lane];
     const int j0 = d->chunk_begin[c], j1 = d->chunk_begin[c + 1];
-    // the aux stream starts after the lane's previous drain (the view parts are reused)
-    if (j1 - j0 > 1 && ((e = cudaEventRecord(d->aux_fork[lane], ls)) != cudaSuccess ||
-                        (e = cudaStreamWaitEvent(as, d->aux_fork[lane], 0)) != cudaSuccess)) {
-      rc = fail_cuda(e, "aux fork");
-      break;
-    }
-    for (int j = j0; j < j1 && rc == SCOUP_OK; ++j) {
-      const cudaStream_t vs = ((j - j0) & 1) ? as : ls;
+    vw.clear();
+    vs.clear();
+    for (int j = j0; j < j1; ++j) {
       const TileJob& J = d->jobs[j];
-      const scoup_batch_item& it = items[J.scene];
       UpliftWs w = d->view[d->job_view_part[j]];
       w.sp = d->scene[J.scene].sp;
       w.cell = d->scene[J.scene].cell;
       w.cells_scratch = d->scene[J.scene].cells_scratch;
-      if ((e = launch_preprocess(it.scene, J.cam, w, J.slot, vs)) != cudaSuccess) rc = fail_cuda(e, "preprocess");
-      else if ((e = launch_binning(J.cam, it.scene.n, w, J.slot, vs)) != cudaSuccess) rc = fail_cuda(e, "binning");
+      vw.push_back(w);
+      vs.push_back(&items[J.scene].scene);
     }
-    // join even on an error, so that a capture in progress stays well formed
-    if (j1 - j0 > 1 && ((e = cudaEventRecord(d->aux_join[lane], as)) != cudaSuccess ||
-                        (e = cudaStreamWaitEvent(ls, d->aux_join[lane], 0)) != cudaSuccess) &&
-        rc == SCOUP_OK)
-      rc = fail_cuda(e, "aux join");
-    if (rc != SCOUP_OK) break;
-    if ((e = launch_uplift_drain(d->jobs.data() + j0, d->tile0.data() + j0, j1 - j0, d->counters_dev + c, compensated,
-                                 warp_w, ls)) != cudaSuccess) {
-      rc = fail_cuda(e, "drain");
-      break;
-    }
-    drain_merge_kernel<<<(j1 - j0 + 63) / 64, 64, 0, ls>>>(d->jobs_dev + j0, j1 - j0);
-    g_launches += 1;
-    if ((e = cudaGetLastError()) != cudaSuccess) rc = fail_cuda(e, "merge");
+    const ChunkStreams cs{lane_st[lane], d->aux[lane], d->aux_fork[lane], d->aux_join[lane]};
+    rc = run_chunk(d->jobs.data() + j0, d->tile0.data() + j0, j1 - j0, vw.data(), vs.data(), d->counters_dev + lane,
+                   compensated, warp_w, cs);
   }
   // join even on an error, so that a capture in progress stays well formed
   for (int l = 0; l < used; ++l)

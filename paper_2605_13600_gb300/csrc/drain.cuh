@@ -15,6 +15,27 @@ struct DrainViewInit {
   uint32_t* dhist;
 };
 
+// Streams of one chunk lane: the lane's stream and a second one that
+// projects and bins the odd views of a chunk (null: all on the lane's stream),
+// with the events that fork it from and join it back into the lane's stream.
+struct ChunkStreams {
+  cudaStream_t ls, as;
+  cudaEvent_t fork, join;
+};
+
+// One chunk of njobs <= kMaxDrainJobs views (HOST arrays): projection and
+// binning of each view into views[j] (its view part, with the scene copy of
+// *scenes[j]), one drain launch over every (view, tile) item (tile0 as for
+// launch_uplift_drain; *counter is cleared first), then the merge of the
+// views' counters into their scenes' headers (api.cu).
+int run_chunk(const TileJob* jobs, const uint32_t* tile0, int njobs, const UpliftWs* views,
+              const scoup_scene* const* scenes, unsigned* counter, bool compensated, int warp_w,
+              const ChunkStreams& cs);
+// Resets view parts before their first use (headers, binning counters).
+cudaError_t launch_view_init(const DrainViewInit* parts, int nparts, int max_tiles, cudaStream_t st);
+// Adds each job's view counters into its scene header and clears them.
+cudaError_t launch_view_merge(const TileJob* jobs, int njobs, cudaStream_t st);
+
 // Device memory and the chunk schedule of the chunked form for one plan.
 struct DrainLayout {
   int chunk = 0, lanes = 0, sample = -1;  // the configuration the layout was built for
@@ -30,9 +51,8 @@ struct DrainLayout {
   std::vector<uint32_t> chunk_items;   // (view, tile) items of each chunk
   std::vector<int> job_view_part;      // view part of each job
   std::vector<uint32_t> tile0;        // per job: its first item within its chunk
-  TileJob* jobs_dev = nullptr;         // device copy of jobs (read by the merge kernel)
-  unsigned* counters_dev = nullptr;    // [nchunks]
-  DrainViewInit* init_dev = nullptr;   // [lanes * chunk]
+  unsigned* counters_dev = nullptr;    // [lanes]: the drain counter of each lane
+  std::vector<DrainViewInit> init;     // [lanes * chunk]
   // per lane: a second stream projecting and binning the odd views of the
   // lane's chunk, forked from and joined back into the lane's stream
   std::vector<cudaStream_t> aux;

@@ -13,8 +13,8 @@ from typing import Optional, Sequence
 import numpy as np
 
 from . import _lib
-from ._lib import (SCOUP_ACCUM_COMPENSATED, SCOUP_ACCUM_CONTINUE, SCOUP_BATCH_EAGER, BatchItem, Camera, Level,
-                   PlanInfo, Scene, ScoupError, Stats, check, load)
+from ._lib import (SCOUP_ACCUM_COMPENSATED, SCOUP_ACCUM_CONTINUE, SCOUP_BATCH_EAGER, SCOUP_UPLIFT_CHUNKED, BatchItem,
+                   Camera, Level, PlanInfo, Scene, ScoupError, Stats, check, load)
 
 
 def _ptr(t) -> Optional[int]:
@@ -72,6 +72,11 @@ def scoup_version() -> str:
 
 def scoup_uplift_workspace_size(n: int, max_width: int, max_height: int, dup_capacity: int) -> int:
     return int(load().scoup_uplift_workspace_size(n, max_width, max_height, dup_capacity))
+
+
+def scoup_uplift_chunked_workspace_size(n: int, max_width: int, max_height: int, dup_capacity: int) -> int:
+    """Workspace bytes of scoup_uplift with SCOUP_UPLIFT_CHUNKED."""
+    return int(load().scoup_uplift_chunked_workspace_size(n, max_width, max_height, dup_capacity))
 
 
 def scoup_uplift_plan(scene: Scene, cams: Sequence, workspace, stream=None) -> int:
@@ -634,7 +639,9 @@ class Uplift:
     """
 
     def __init__(self, wl, device: str = "cuda", dup_capacity: Optional[int] = None,
-                 headroom: float = 1.0, compensated: bool = False, topk: bool = True):
+                 headroom: float = 1.0, compensated: bool = False, topk: bool = True, chunked: bool = False):
+        """chunked=True: run() uses the chunked form (SCOUP_UPLIFT_CHUNKED) and
+        the workspace is sized for it."""
         import torch
         dev = torch.device(device)
         sc = wl.scene
@@ -661,8 +668,9 @@ class Uplift:
             dup_capacity = int(scoup_uplift_plan(self.scene, self.cams, probe) * headroom) + 1
             del probe
         self.dup_capacity = dup_capacity
-        self.workspace = torch.empty(scoup_uplift_workspace_size(n, maxw, maxh, dup_capacity) + extra,
-                                     dtype=torch.uint8, device=dev)
+        self.chunked = bool(chunked)
+        size = scoup_uplift_chunked_workspace_size if self.chunked else scoup_uplift_workspace_size
+        self.workspace = torch.empty(size(n, maxw, maxh, dup_capacity) + extra, dtype=torch.uint8, device=dev)
         self.maxw, self.maxh, self.extra, self.device = maxw, maxh, extra, dev
         self._host_ws = None
         self.compensated = bool(compensated)
@@ -678,6 +686,8 @@ class Uplift:
         offs = self.map_offsets if views is None else self.map_offsets[list(views)]
         if self.compensated:
             accum_mode |= SCOUP_ACCUM_COMPENSATED
+        if self.chunked:
+            accum_mode |= SCOUP_UPLIFT_CHUNKED
         return scoup_uplift(self.scene, cams, self.region_maps, offs, self.R_total, self.code_idx,
                             self.code_val, self.s, self.C, self.K, self.accum, accum_mode,
                             self.topk_idx if topk else None, self.topk_val if topk else None,
@@ -738,13 +748,13 @@ class LevelUplift:
         self.topk_idx = torch.empty((self.L, n, self.K), dtype=torch.int32, device=dev)
         self.topk_val = torch.empty((self.L, n, self.K), dtype=torch.float32, device=dev)
 
-    def run(self, stats: bool = True, topk: bool = True, views=None, stream=None):
+    def run(self, stats: bool = True, topk: bool = True, views=None, stream=None, accum_mode: int = 0):
         b = self.base
         cams = b.cams if views is None else [b.cams[v] for v in views]
         offs = np.ascontiguousarray((b.map_offsets if views is None else b.map_offsets[list(views)])[:max(1, len(cams))])
         ca = camera_array(cams)
         st = Stats()
-        mode = SCOUP_ACCUM_COMPENSATED if self.compensated else 0
+        mode = accum_mode | (SCOUP_ACCUM_COMPENSATED if self.compensated else 0)
         check(load().scoup_uplift_levels(ct.byref(b.scene), ct.cast(ca, ct.c_void_p), len(cams),
                                          offs.ctypes.data_as(ct.c_void_p), ct.cast(self.levels, ct.c_void_p),
                                          self.L, self.C, self.K, _ptr(self.accum), mode,
@@ -857,8 +867,8 @@ class BatchedUplift:
             pass
 
 
-__all__ = ["ScoupError", "SCOUP_ACCUM_CONTINUE", "SCOUP_ACCUM_COMPENSATED", "scene_struct", "camera_array", "scoup_version",
-           "scoup_uplift_workspace_size", "scoup_uplift_plan", "scoup_uplift", "scoup_topk",
+__all__ = ["ScoupError", "SCOUP_ACCUM_CONTINUE", "SCOUP_ACCUM_COMPENSATED", "SCOUP_UPLIFT_CHUNKED", "scene_struct", "camera_array", "scoup_version",
+           "scoup_uplift_workspace_size", "scoup_uplift_chunked_workspace_size", "scoup_uplift_plan", "scoup_uplift", "scoup_topk",
            "scoup_read_stats", "scoup_uplift_noalloc", "scoup_uplift_noalloc_max_bytes",
            "scoup_profile_enable", "scoup_profile_read", "scoup_launch_count",
            "scoup_render", "scoup_render_backward", "Render", "Uplift",

@@ -68,7 +68,7 @@ def _call_uplift(lib, **kw):
 
 @pytest.mark.parametrize("kw,frag", [
     ({"K": 0}, "K=0"), ({"K": 9}, "K=9"), ({"C": 2000, "K": 2}, "C=2000"), ({"s": 0}, "s=0"),
-    ({"s": 1025}, "s=1025"), ({"V": -1}, "V=-1"), ({"n": -5}, "n=-5"), ({"mode": 4}, "accum_mode"),
+    ({"s": 1025}, "s=1025"), ({"V": -1}, "V=-1"), ({"n": -5}, "n=-5"), ({"mode": 8}, "accum_mode"),
     ({"wh": (0, 10)}, "bad size"), ({"fx": 0.0}, "focal"), ({"accum": None}, "accum"),
     ({"ws": None}, "workspace"), ({"ws_bytes": 16}, "workspace too small"),
     ({"quats": ct.c_void_p(0x10004)}, "aligned"),

@@ -3,8 +3,10 @@
 Element-by-element parity on seeded inputs small enough for the oracle
 (cfg1: 10k Gaussians x 8 views; random scenes with ragged image sizes), edge
 cases (empty scene, no views, all culled, unlabelled pixels, s > K, tiles
-longer than one sort window), device-side error reporting, chunked resume,
-and sampled rows of the full 1M-Gaussian x 200-view workload.
+longer than one sort window), device-side error reporting, resume over
+several calls, the chunked form (SCOUP_UPLIFT_CHUNKED: one persistent tile
+launch per chunk of views) held to the same oracle with the counters of the
+per-view form, and sampled rows of the full 1M-Gaussian x 200-view workload.
 """
 import numpy as np
 import pytest
@@ -32,8 +34,8 @@ def _run(gb, wl, **kw):
     return up, st
 
 
-def _parity(gb, oracle_lib, wl, tag=""):
-    up, st = _run(gb, wl)
+def _parity(gb, oracle_lib, wl, tag="", **kw):
+    up, st = _run(gb, wl, **kw)
     acc, risk, cnt = oracle_lib.uplift(wl)
     ga = up.accum.cpu().numpy()
     info = check_accum(ga, acc, risk)
@@ -135,6 +137,65 @@ def test_single_gaussian_closed_form(gb):
     assert up.topk_idx[0].tolist() == [5, -1, -1, -1] and float(up.topk_val[0, 0]) == 1.0
 
 
+@pytest.mark.parametrize("seed,V,W,H,n", [
+    (41, 19, 120, 90, 3000),   # chunks of 8, 8 and 3 views on both lanes
+    (42, 8, 64, 48, 800),      # exactly one chunk
+    (43, 1, 50, 37, 300),      # one view, ragged tiles
+    (44, 33, 40, 30, 600),     # five chunks: each lane reuses its view parts
+])
+def test_chunked_form_parity(gb, oracle_lib, seed, V, W, H, n):
+    wl = synth.tiny_workload(seed, n=n, width=W, height=H, V=V, R=9, C=32, s=4, K=4, layout="blobs")
+    _parity(gb, oracle_lib, wl, f"chunked seed{seed}", chunked=True)
+
+
+def test_chunked_form_counters_equal_per_view_form(gb, cfg1):
+    """Every counter is a count over the same per-view, per-tile work: the
+    merge of the view parts' headers must reproduce the per-view form's."""
+    _, a = _run(gb, cfg1)
+    _, b = _run(gb, cfg1, chunked=True)
+    assert a == b, (a, b)
+    wl = synth.tiny_workload(45, n=2000, width=96, height=64, V=21, R=11, C=32, s=4, K=4, layout="blobs")
+    _, a = _run(gb, wl)
+    _, b = _run(gb, wl, chunked=True)
+    assert a == b, (a, b)
+
+
+def test_chunked_form_compensated_and_s_above_k(gb, oracle_lib):
+    wl = synth.tiny_workload(46, n=1500, width=80, height=60, V=11, R=9, C=32, s=6, K=3, layout="blobs")
+    up, st = _run(gb, wl, chunked=True, compensated=True)
+    acc, risk, cnt = oracle_lib.uplift(wl)
+    info = check_accum(up.accum_value().cpu().numpy(), acc, risk)
+    assert info["n_bad"] == 0, info
+    tk = check_topk(up.topk_idx.cpu().numpy(), up.topk_val.cpu().numpy(), acc, risk, wl.K)
+    assert tk["n_problems"] == 0, tk
+
+
+def test_chunked_form_resume_and_capacity(gb, cfg1):
+    up = gb.Uplift(cfg1, chunked=True)
+    up.run()
+    one = up.accum.clone()
+    up.run(views=range(0, 3))
+    up.run(views=range(3, 8), accum_mode=1)
+    np.testing.assert_allclose(up.accum.cpu().numpy(), one.cpu().numpy(), rtol=2e-6, atol=1e-7)
+    small = gb.Uplift(cfg1, dup_capacity=1000, chunked=True)
+    with pytest.raises(gb.ScoupError) as ei:
+        small.run()
+    assert ei.value.code == -4
+
+
+def test_chunked_form_refuses_levels_and_host_maps(gb, cfg1):
+    import torch
+    up = gb.Uplift(cfg1)
+    host = torch.as_tensor(cfg1.region_maps).pin_memory()
+    with pytest.raises(gb.ScoupError) as ei:
+        up.run_host_maps(host, accum_mode=gb.SCOUP_UPLIFT_CHUNKED)
+    assert ei.value.code == -1
+    lv = gb.LevelUplift([cfg1, cfg1])
+    with pytest.raises(gb.ScoupError) as ei:
+        lv.run(accum_mode=gb.SCOUP_UPLIFT_CHUNKED)
+    assert ei.value.code == -1
+
+
 def test_chunked_resume_matches_one_shot(gb, cfg1):
     up = gb.Uplift(cfg1)
     up.run()
@@ -214,13 +275,15 @@ def _cfg2_rows(wl, rng):
 
 
 @pytest.mark.slow
-def test_cfg2_full_size_sampled_rows(gb, oracle_lib):
+@pytest.mark.parametrize("chunked", [True, False])
+def test_cfg2_full_size_sampled_rows(gb, oracle_lib, chunked):
     """Full 1M-Gaussian x 200-view x 988x731 uplift in the benchmark's launch
-    configuration; 256 rows (random, from the densest tiles and from tiles of
-    more than 4 regions) checked against the oracle over all 200 views."""
+    configuration (the chunked form) and in the per-view form; 256 rows
+    (random, from the densest tiles and from tiles of more than 4 regions)
+    checked against the oracle over all 200 views."""
     import torch
     wl = synth.uplift_cfg2(device="cuda")
-    up = gb.Uplift(wl)
+    up = gb.Uplift(wl, chunked=chunked)
     st = up.run()
     assert st["status"] == 0 and st["contributions"] > 1e9
     acc_g = up.accum
