@@ -171,10 +171,20 @@ size_t scoup_uplift_chunked_workspace_size(int64_t n, int32_t max_width, int32_t
 size_t scoup_uplift_host_maps_workspace_size(int64_t n, int32_t max_width, int32_t max_height,
                                              int64_t dup_capacity);
 
+/* Workspace bytes for scoup_uplift_host_maps with SCOUP_UPLIFT_CHUNKED: a
+ * staging ring of 16 view maps (one per view part) of max_width x max_height
+ * int32 entries, then the chunked layout (scoup_uplift_chunked_workspace_size
+ * with the same arguments).  0 on invalid arguments. */
+size_t scoup_uplift_host_maps_chunked_workspace_size(int64_t n, int32_t max_width, int32_t max_height,
+                                                     int64_t dup_capacity);
+
 /* scoup_uplift with the region maps in HOST memory (pinned for the copies to
  * run asynchronously): view v's map is copied to a ring slot in the workspace
  * on a library copy stream while earlier views compute, and only view v's
  * tile pass waits for it (its projection and binning do not read the map).
+ * With SCOUP_UPLIFT_CHUNKED the maps of a chunk are copied while the lane's
+ * previous chunk composites, and the chunk's drain waits for them (workspace:
+ * scoup_uplift_host_maps_chunked_workspace_size).
  * Results equal scoup_uplift on the same maps up to the order of the FP32
  * atomic additions (as two scoup_uplift runs do); counters are equal.  The copies
  * follow the work already on `stream` and the call's work is joined back

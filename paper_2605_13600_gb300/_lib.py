@@ -92,6 +92,7 @@ PROTOS = {
     "scoup_last_error": (ct.c_char_p, []),
     "scoup_uplift_workspace_size": (SZ, [I64, I32, I32, I64]),
     "scoup_uplift_chunked_workspace_size": (SZ, [I64, I32, I32, I64]),
+    "scoup_uplift_host_maps_chunked_workspace_size": (SZ, [I64, I32, I32, I64]),
     "scoup_uplift_plan": (ct.c_int, [ct.POINTER(Scene), P, I32, P, SZ, ct.POINTER(I64), P]),
     "scoup_uplift": (ct.c_int, [ct.POINTER(Scene), P, I32, P, P, I32, P, P, I32, I32, I32, P, I32,
                                 P, P, P, SZ, ct.POINTER(Stats), P]),

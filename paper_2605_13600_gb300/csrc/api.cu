@@ -338,7 +338,11 @@ int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
 // chunk v / kChunkViews on lane chunk % kChunkLanes; each chunk is projected
 // and binned into the lane's view parts, composited by one drain launch and
 // merged into the scene header sw.hdr.  The scene part (header, Morton-ordered
-// copy) is set up; the view parts follow it in the workspace.
+// copy) is set up; the view parts follow it in the workspace.  With host
+// region maps (c.maps_on_host) view part q reads its map from ring slot q:
+// a lane's copies for a chunk wait for the lane's previous drain (the last
+// reader of its slots) and the chunk's drain waits for the copies; projection
+// and binning do not read the maps and run meanwhile.
 static int uplift_views_chunked(const UpliftCall& c, const int32_t* region_maps, int32_t R_total, const UpliftWs& sw,
                                 void* workspace, size_t ws_bytes, int max_tiles, int64_t code_rows_k,
                                 const int32_t* ci, const float* cv, int s_eff, float* comp, int warp_w,
@@ -382,6 +386,25 @@ static int uplift_views_chunked(const UpliftCall& c, const int32_t* region_maps,
       return cuda_fail(e, "chunk events");
     }
   const cudaEvent_t fork = ev[0], join = ev[1];
+  // host maps: copy stream forked from `st`; ready[l] = lane l's chunk maps are staged,
+  // used[l] = lane l's last drain has been enqueued after them
+  cudaStream_t cps = nullptr;
+  cudaEvent_t mev[2 + 2 * kChunkLanes] = {};
+  auto destroy_events = [&]() {
+    for (cudaEvent_t y : ev) cudaEventDestroy(y);
+    for (cudaEvent_t y : mev)
+      if (y) cudaEventDestroy(y);
+  };
+  if (c.maps_on_host) {
+    cps = map_copy_stream();
+    bool ok = cps != nullptr;
+    for (cudaEvent_t& x : mev) ok = ok && cudaEventCreateWithFlags(&x, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventRecord(mev[0], st) == cudaSuccess && cudaStreamWaitEvent(cps, mev[0], 0) == cudaSuccess;
+    if (!ok) {
+      destroy_events();
+      return fail(SCOUP_ERR_CUDA, "map copy stream");
+    }
+  }
   int rc = SCOUP_OK;
   const int nchunks = (V + kChunkViews - 1) / kChunkViews;
   const bool lane1 = nchunks > 1;
@@ -405,7 +428,8 @@ static int uplift_views_chunked(const UpliftCall& c, const int32_t* region_maps,
       J.lc = LevelCodes();
       J.lc.L = 1;
       J.lc.s_tot = s_eff;
-      J.lc.rmap[0] = region_maps + c.map_offsets[v];
+      J.lc.rmap[0] = c.maps_on_host ? c.map_stage + (size_t)(lane * kChunkViews + k) * c.map_stage_cap
+                                    : region_maps + c.map_offsets[v];
       J.lc.ci[0] = ci;
       J.lc.cv[0] = cv;
       J.lc.s[0] = s_eff;
@@ -426,14 +450,34 @@ static int uplift_views_chunked(const UpliftCall& c, const int32_t* region_maps,
       views[k] = w;
       scenes[k] = c.scene;
     }
-    const ChunkStreams cs{lane_st[lane], aux_st[lane], ev[2 + 2 * lane], ev[3 + 2 * lane]};
+    ChunkStreams cs{lane_st[lane], aux_st[lane], ev[2 + 2 * lane], ev[3 + 2 * lane]};
+    if (c.maps_on_host) {
+      // stage the chunk's maps into the lane's slots once the lane's previous drain has run
+      cudaEvent_t ready = mev[2 + 2 * lane], used = mev[3 + 2 * lane];
+      if (ch >= kChunkLanes && (e = cudaStreamWaitEvent(cps, used, 0)) != cudaSuccess) rc = cuda_fail(e, "map copy");
+      for (int k = 0; k < nv && rc == SCOUP_OK; ++k) {
+        const int v = v0 + k;
+        const size_t bytes = sizeof(int32_t) * (size_t)c.cams[v].width * (size_t)c.cams[v].height;
+        if ((e = cudaMemcpyAsync((void*)jobs[k].lc.rmap[0], region_maps + c.map_offsets[v], bytes,
+                                 cudaMemcpyHostToDevice, cps)) != cudaSuccess)
+          rc = cuda_fail(e, "region map copy");
+      }
+      if (rc == SCOUP_OK && (e = cudaEventRecord(ready, cps)) != cudaSuccess) rc = cuda_fail(e, "map copy");
+      if (rc != SCOUP_OK) break;
+      cs.before_drain = ready;
+      cs.after_drain = used;
+    }
     rc = run_chunk(jobs, tile0, nv, views, scenes, counters + lane, comp != nullptr, warp_w, cs);
   }
+  if (c.maps_on_host &&
+      ((e = cudaEventRecord(mev[1], cps)) != cudaSuccess || (e = cudaStreamWaitEvent(st, mev[1], 0)) != cudaSuccess) &&
+      rc == SCOUP_OK)
+    rc = cuda_fail(e, "map copy stream");
   // join even on an error, so that a capture in progress stays well formed
   if (lane1 && ((e = cudaEventRecord(join, lane_st[1])) != cudaSuccess ||
                 (e = cudaStreamWaitEvent(st, join, 0)) != cudaSuccess) && rc == SCOUP_OK)
     rc = cuda_fail(e, "chunk lanes");
-  for (cudaEvent_t y : ev) cudaEventDestroy(y);
+  destroy_events();
   return rc;
 }
 
@@ -486,8 +530,8 @@ int uplift_call(const UpliftCall& c, void* workspace, size_t ws_bytes, int warp_
     return fail(SCOUP_ERR_INVALID_ARG,
                 "accum_mode=%d: only SCOUP_ACCUM_CONTINUE, SCOUP_ACCUM_COMPENSATED and SCOUP_UPLIFT_CHUNKED", accum_mode);
   const bool chunked = (accum_mode & SCOUP_UPLIFT_CHUNKED) != 0;
-  if (chunked && (c.L > 0 || c.maps_on_host))
-    return fail(SCOUP_ERR_INVALID_ARG, "SCOUP_UPLIFT_CHUNKED is a mode of scoup_uplift (one level, device region maps)");
+  if (chunked && c.L > 0)
+    return fail(SCOUP_ERR_INVALID_ARG, "SCOUP_UPLIFT_CHUNKED is a mode of the single-level uplift calls");
   if (scene->n > 0 && !accum) return fail(SCOUP_ERR_INVALID_ARG, "accum is NULL");
   if ((topk_idx == nullptr) != (topk_val == nullptr))
     return fail(SCOUP_ERR_INVALID_ARG, "topk_idx and topk_val must both be given or both be NULL");
@@ -726,6 +770,8 @@ int run_chunk(const TileJob* jobs, const uint32_t* tile0, int njobs, const Uplif
                 (e = cudaStreamWaitEvent(cs.ls, cs.join, 0)) != cudaSuccess) && rc == SCOUP_OK)
     rc = fail_cuda(e, "join");
   if (rc != SCOUP_OK) return rc;
+  if (cs.before_drain && (e = cudaStreamWaitEvent(cs.ls, cs.before_drain, 0)) != cudaSuccess)
+    return fail_cuda(e, "region map copy");
   if ((e = cudaMemsetAsync(counter, 0, sizeof(unsigned), cs.ls)) != cudaSuccess) return fail_cuda(e, "counter");
   {
     PhaseScope ps(SCOUP_PHASE_UPLIFT_TILES, cs.ls);
@@ -733,6 +779,8 @@ int run_chunk(const TileJob* jobs, const uint32_t* tile0, int njobs, const Uplif
       return fail_cuda(e, "drain");
   }
   if ((e = launch_view_merge(jobs, njobs, cs.ls)) != cudaSuccess) return fail_cuda(e, "merge");
+  if (cs.after_drain && (e = cudaEventRecord(cs.after_drain, cs.ls)) != cudaSuccess)
+    return fail_cuda(e, "region map copy");
   return SCOUP_OK;
 }
 
@@ -769,6 +817,13 @@ size_t scoup_uplift_chunked_workspace_size(int64_t n, int32_t max_width, int32_t
                                            int64_t dup_capacity) {
   if (n < 0 || max_width <= 0 || max_height <= 0 || dup_capacity < 0) return 0;
   return chunked_bytes(n, tiles_of(max_width, max_height), 0, dup_capacity);
+}
+
+size_t scoup_uplift_host_maps_chunked_workspace_size(int64_t n, int32_t max_width, int32_t max_height,
+                                                     int64_t dup_capacity) {
+  if (n < 0 || max_width <= 0 || max_height <= 0 || dup_capacity < 0) return 0;
+  return align_up(sizeof(int32_t) * (size_t)(kChunkLanes * kChunkViews) * (size_t)max_width * (size_t)max_height) +
+         chunked_bytes(n, tiles_of(max_width, max_height), 0, dup_capacity);
 }
 
 size_t scoup_uplift_workspace_size(int64_t n, int32_t max_width, int32_t max_height,
@@ -849,7 +904,9 @@ int scoup_uplift_host_maps(const scoup_scene* scene, const scoup_camera* cams, i
       return fail(SCOUP_ERR_INVALID_ARG, "view %d: bad size %dx%d", v, cams[v].width, cams[v].height);
     cap = std::max(cap, (int64_t)cams[v].width * cams[v].height);
   }
-  const size_t ring = align_up(sizeof(int32_t) * kMapStageSlots * (size_t)cap);
+  // one ring slot per view in flight: kMapStageSlots, or one per view part of the chunked form
+  const int slots = (accum_mode & SCOUP_UPLIFT_CHUNKED) ? kChunkLanes * kChunkViews : kMapStageSlots;
+  const size_t ring = align_up(sizeof(int32_t) * (size_t)slots * (size_t)cap);
   if (ws_bytes < ring) return fail(SCOUP_ERR_OOM, "workspace too small: %zu < %zu bytes of staging ring", ws_bytes, ring);
   UpliftCall c{scene, cams, V, host_region_maps, map_offsets, R_total, code_idx, code_val, s, C, K,
                accum, accum_mode, topk_idx, topk_val};

@@ -21,6 +21,8 @@ struct DrainViewInit {
 struct ChunkStreams {
   cudaStream_t ls, as;
   cudaEvent_t fork, join;
+  cudaEvent_t before_drain = nullptr;  // if set: the drain waits for it (staged region maps)
+  cudaEvent_t after_drain = nullptr;   // if set: recorded once the drain and merge are enqueued
 };
 
 // One chunk of njobs <= kMaxDrainJobs views (HOST arrays): projection and

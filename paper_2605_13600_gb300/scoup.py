@@ -123,6 +123,11 @@ def scoup_uplift_host_maps_workspace_size(n: int, max_width: int, max_height: in
     return int(load().scoup_uplift_host_maps_workspace_size(n, max_width, max_height, dup_capacity))
 
 
+def scoup_uplift_host_maps_chunked_workspace_size(n: int, max_width: int, max_height: int, dup_capacity: int) -> int:
+    """Workspace bytes of scoup_uplift_host_maps with SCOUP_UPLIFT_CHUNKED."""
+    return int(load().scoup_uplift_host_maps_chunked_workspace_size(n, max_width, max_height, dup_capacity))
+
+
 def scoup_uplift_host_maps(scene: Scene, cams: Sequence, host_region_maps, map_offsets, R_total: int, code_idx,
                            code_val, s: int, C: int, K: int, accum, accum_mode: int, topk_idx, topk_val,
                            workspace, stats: bool = True, stream=None):
@@ -693,22 +698,30 @@ class Uplift:
                             self.topk_idx if topk else None, self.topk_val if topk else None,
                             self.workspace, stats=stats, stream=stream)
 
-    def run_host_maps(self, host_maps, stats: bool = True, accum_mode: int = 0, stream=None, topk: bool = True):
+    def run_host_maps(self, host_maps, stats: bool = True, accum_mode: int = 0, stream=None, topk: bool = True,
+                      chunked: Optional[bool] = None):
         """One uplift with the region maps read from host memory (host_maps:
         a pinned CPU int32 tensor laid out like region_maps): the copies of
-        the views' maps overlap the earlier views' compute."""
+        the views' maps overlap the earlier views' compute.  chunked: the
+        form (default: the Uplift's own)."""
         import torch
         topk = topk and self.topk_idx is not None
+        chunked = self.chunked if chunked is None else bool(chunked)
         if self._host_ws is None:
-            self._host_ws = torch.empty(scoup_uplift_host_maps_workspace_size(self.n, self.maxw, self.maxh,
-                                                                              self.dup_capacity) + self.extra,
-                                        dtype=torch.uint8, device=self.device)
+            self._host_ws = {}
+        if chunked not in self._host_ws:
+            size = (scoup_uplift_host_maps_chunked_workspace_size if chunked
+                    else scoup_uplift_host_maps_workspace_size)
+            self._host_ws[chunked] = torch.empty(size(self.n, self.maxw, self.maxh, self.dup_capacity) + self.extra,
+                                                 dtype=torch.uint8, device=self.device)
+        if chunked:
+            accum_mode |= SCOUP_UPLIFT_CHUNKED
         if self.compensated:
             accum_mode |= SCOUP_ACCUM_COMPENSATED
         return scoup_uplift_host_maps(self.scene, self.cams, host_maps, self.map_offsets, self.R_total,
                                       self.code_idx, self.code_val, self.s, self.C, self.K, self.accum, accum_mode,
                                       self.topk_idx if topk else None, self.topk_val if topk else None,
-                                      self._host_ws, stats=stats, stream=stream)
+                                      self._host_ws[chunked], stats=stats, stream=stream)
 
     def accum_value(self):
         """The accumulator [n, C] (sum + compensation in the compensated form)."""
@@ -868,7 +881,8 @@ class BatchedUplift:
 
 
 __all__ = ["ScoupError", "SCOUP_ACCUM_CONTINUE", "SCOUP_ACCUM_COMPENSATED", "SCOUP_UPLIFT_CHUNKED", "scene_struct", "camera_array", "scoup_version",
-           "scoup_uplift_workspace_size", "scoup_uplift_chunked_workspace_size", "scoup_uplift_plan", "scoup_uplift", "scoup_topk",
+           "scoup_uplift_workspace_size", "scoup_uplift_chunked_workspace_size",
+           "scoup_uplift_host_maps_chunked_workspace_size", "scoup_uplift_plan", "scoup_uplift", "scoup_topk",
            "scoup_read_stats", "scoup_uplift_noalloc", "scoup_uplift_noalloc_max_bytes",
            "scoup_profile_enable", "scoup_profile_read", "scoup_launch_count",
            "scoup_render", "scoup_render_backward", "Render", "Uplift",

@@ -183,13 +183,7 @@ def test_chunked_form_resume_and_capacity(gb, cfg1):
     assert ei.value.code == -4
 
 
-def test_chunked_form_refuses_levels_and_host_maps(gb, cfg1):
-    import torch
-    up = gb.Uplift(cfg1)
-    host = torch.as_tensor(cfg1.region_maps).pin_memory()
-    with pytest.raises(gb.ScoupError) as ei:
-        up.run_host_maps(host, accum_mode=gb.SCOUP_UPLIFT_CHUNKED)
-    assert ei.value.code == -1
+def test_chunked_form_refuses_levels(gb, cfg1):
     lv = gb.LevelUplift([cfg1, cfg1])
     with pytest.raises(gb.ScoupError) as ei:
         lv.run(accum_mode=gb.SCOUP_UPLIFT_CHUNKED)
@@ -299,13 +293,15 @@ def test_cfg2_full_size_sampled_rows(gb, oracle_lib, chunked):
 
 
 @pytest.mark.parametrize("pinned", [True, False])
-def test_host_region_maps(gb, oracle_lib, cfg1, cfg1_oracle, pinned):
+@pytest.mark.parametrize("chunked", [False, True])
+def test_host_region_maps(gb, oracle_lib, cfg1, cfg1_oracle, pinned, chunked):
     """scoup_uplift_host_maps: cfg1's 8 views staged from host memory through a
-    4-slot device ring (every slot reused) against the oracle, and against
-    scoup_uplift on device maps (equal counters and Top-K; accumulators equal
-    up to the order of FP32 atomic additions)."""
+    4-slot device ring (every slot reused; in the chunked form one slot per
+    view part) against the oracle, and against scoup_uplift on device maps
+    (equal counters and Top-K; accumulators equal up to the order of FP32
+    atomic additions)."""
     import torch
-    up = gb.Uplift(cfg1)
+    up = gb.Uplift(cfg1, chunked=chunked)
     st_dev = up.run()
     acc_dev = up.accum.clone()
     idx_dev = up.topk_idx.clone()
@@ -325,11 +321,15 @@ def test_host_region_maps(gb, oracle_lib, cfg1, cfg1_oracle, pinned):
     assert (up.topk_idx != idx_dev).sum().item() <= 4
 
 
-def test_host_region_maps_ragged_views(gb, oracle_lib):
-    """Nine views (the ring wraps twice) of a ragged-size scene, host maps."""
+@pytest.mark.parametrize("chunked,V", [(False, 9), (True, 9), (True, 37)])
+def test_host_region_maps_ragged_views(gb, oracle_lib, chunked, V):
+    """Views of a ragged-size scene staged from host maps: nine views (the
+    4-slot ring wraps twice; in the chunked form one chunk per lane), and 37
+    views in the chunked form (five chunks: every lane's 8 slots refilled
+    after the lane's previous drain)."""
     import torch
-    wl = synth.tiny_workload(36, n=1500, width=70, height=45, V=9, R=12, C=32, s=4, K=4, log_scale_mean=-2.7)
-    up = gb.Uplift(wl)
+    wl = synth.tiny_workload(36, n=1500, width=70, height=45, V=V, R=12, C=32, s=4, K=4, log_scale_mean=-2.7)
+    up = gb.Uplift(wl, chunked=chunked)
     st = up.run_host_maps(torch.as_tensor(np.asarray(wl.region_maps, np.int32)).contiguous().pin_memory())
     assert st["status"] == 0
     acc, risk, cnt = oracle_lib.uplift(wl)
