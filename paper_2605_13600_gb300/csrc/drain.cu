@@ -8,12 +8,15 @@
 // of its own (records, depth, rectangles, tile lists and a header holding the
 // view's depth range and counters); then one launch of the drain kernel
 // composites every (view, tile) item of the chunk, its CTAs taking items from
-// the chunk's atomic counter (no CTA waits on another); then a merge kernel
-// adds the views' counters into their scenes' headers.  Chunk c uses the view
-// parts of lane c % lanes, so the projection and binning of one lane's chunk
-// overlap the compositing of another's.  Every scene is set up once before
-// the first chunk (header, accumulator, Morton-ordered copy, codes cut to K
-// entries) and gets its Top-K after the last.
+// the lane's atomic counter (cleared before each drain; no CTA waits on
+// another); then a merge kernel adds the views' counters into their scenes'
+// headers (run_chunk, api.cu, shared with scoup_uplift's chunked form).
+// Chunk c uses the view parts of lane c % lanes, so the projection and
+// binning of one lane's chunk overlap the compositing of another's.  Every
+// scene is set up once before the first chunk (header, accumulator,
+// Morton-ordered copy, codes cut to K entries) and gets its Top-K after the
+// last.  The schedule stays on the host: the chunk's views reach the kernels
+// through their launch parameters.
 #include <stdio.h>
 #include <string.h>
 
@@ -244,7 +247,6 @@ int drain_prepare(DrainLayout* d, const std::vector<scoup_batch_item>& items, co
   d->jobs.assign(njobs, TileJob());
   d->job_view_part.assign(njobs, 0);
   d->chunk_begin.assign(nchunks + 1, njobs);
-  d->chunk_items.assign(nchunks, 0u);
   d->tile0.assign(std::max(njobs, 1), 0u);
   for (int c = 0; c < nchunks; ++c) {
     d->chunk_begin[c] = c * chunk;
@@ -280,7 +282,6 @@ int drain_prepare(DrainLayout* d, const std::vector<scoup_batch_item>& items, co
       d->tile0[j] = items_c;
       items_c += (uint32_t)J.tiles;
     }
-    d->chunk_items[c] = items_c;
   }
   d->chunk = chunk;
   d->lanes = lanes;
@@ -294,7 +295,7 @@ int drain_enqueue(DrainLayout* d, const std::vector<scoup_batch_item>& items, in
   const int B = (int)items.size();
   const bool compensated = (accum_mode & SCOUP_ACCUM_COMPENSATED) != 0;
   const int nparts = d->lanes * d->chunk;
-  const int nchunks = (int)d->chunk_items.size();
+  const int nchunks = std::max(0, (int)d->chunk_begin.size() - 1);
   auto fail_cuda = [](cudaError_t e, const char* where) {
     char buf[256];
     snprintf(buf, sizeof(buf), "chunked batch, %s: %s", where, cudaGetErrorString(e));

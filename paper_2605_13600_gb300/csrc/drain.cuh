@@ -50,7 +50,6 @@ struct DrainLayout {
   std::vector<UpliftWs> view;          // [lanes * chunk] view parts, each with its own header
   std::vector<TileJob> jobs;           // chunk-major: jobs[chunk_begin[c] .. chunk_begin[c + 1])
   std::vector<int> chunk_begin;        // [nchunks + 1]
-  std::vector<uint32_t> chunk_items;   // (view, tile) items of each chunk
   std::vector<int> job_view_part;      // view part of each job
   std::vector<uint32_t> tile0;        // per job: its first item within its chunk
   unsigned* counters_dev = nullptr;    // [lanes]: the drain counter of each lane
@@ -64,7 +63,9 @@ struct DrainLayout {
 // Builds (or rebuilds) the layout for `chunk` views per chunk on `lanes`
 // streams over the items (every view, or `sample` evenly spaced views per
 // scene when sample > 0); max_dups[b] is scene b's largest per-view pair
-// count.  Synchronises the device (the schedule is uploaded with plain copies).
+// count.  Creates the lanes' second streams and, when the layout outgrows the
+// memory it has, synchronises the device and reallocates: never while a
+// stream is capturing.
 int drain_prepare(DrainLayout* d, const std::vector<scoup_batch_item>& items, const std::vector<int64_t>& max_dups,
                   int C, int K, int accum_mode, int chunk, int lanes, int sample);
 
