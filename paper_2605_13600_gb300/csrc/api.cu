@@ -550,6 +550,9 @@ int uplift_call(const UpliftCall& c, void* workspace, size_t ws_bytes, int warp_
   const size_t fixed = uplift_fixed_bytes(scene->n, max_tiles, code_rows_k);
   if (ws_bytes < fixed)
     return fail(SCOUP_ERR_OOM, "workspace too small: %zu < %zu bytes before tile lists", ws_bytes, fixed);
+  if (chunked && ws_bytes < chunked_bytes(scene->n, max_tiles, code_rows_k, 0) + (size_t)kChunkLanes * kChunkViews * 256)
+    return fail(SCOUP_ERR_OOM, "workspace too small for the chunked form: %zu < %zu bytes before tile lists", ws_bytes,
+                chunked_bytes(scene->n, max_tiles, code_rows_k, 0) + (size_t)kChunkLanes * kChunkViews * 256);
 
   // two view pipelines (even / odd views on two streams) when the workspace holds them
   const int lanes =

@@ -113,6 +113,28 @@ def test_render_decode_fused_sizes_and_checks(lib):
         assert rc != 0 and frag in L.scoup_last_error().decode(), (kw, L.scoup_last_error())
 
 
+def test_chunked_form_sizes_and_checks(lib):
+    """Workspace layout of the chunked form (SCOUP_UPLIFT_CHUNKED): the scene
+    part, then 2 x 8 view parts each holding dup_capacity 8-byte keys; with
+    host maps a 16-slot staging ring in front.  A workspace below the chunked
+    layout is refused before any device work."""
+    L = lib.load()
+    n, W, H, dup = 1000, 160, 120, 100
+    al = lambda x: (x + 255) // 256 * 256
+    a = L.scoup_uplift_chunked_workspace_size(n, W, H, 0)
+    b = L.scoup_uplift_chunked_workspace_size(n, W, H, dup)
+    assert b - a == 16 * al(8 * dup)
+    assert a > L.scoup_uplift_workspace_size(n, W, H, 0)  # 16 view parts against 2
+    assert L.scoup_uplift_host_maps_chunked_workspace_size(n, W, H, dup) == al(16 * W * H * 4) + b
+    for bad in ((-1, W, H, dup), (n, 0, H, dup), (n, W, H, -1)):
+        assert L.scoup_uplift_chunked_workspace_size(*bad) == 0
+        assert L.scoup_uplift_host_maps_chunked_workspace_size(*bad) == 0
+    # a per-view sized workspace does not hold the chunked layout
+    ws_bytes = L.scoup_uplift_workspace_size(4, 32, 32, 10)
+    rc, msg = _call_uplift(lib, n=4, mode=4, wh=(32, 32), ws_bytes=ws_bytes)
+    assert rc == lib.SCOUP_ERR_OOM and "chunked form" in msg, msg
+
+
 def test_uplift_host_maps_sizes_and_checks(lib):
     """Workspace layout of scoup_uplift_host_maps (a 4-slot staging ring of
     view maps, then a scoup_uplift workspace) and its host-side checks."""
