@@ -142,7 +142,9 @@ int scoup_uplift_plan(const scoup_scene* scene, const scoup_camera* cams, int32_
  *               atomic additions; same counters.  The workspace must then be
  *               sized by scoup_uplift_chunked_workspace_size (16 view parts).
  *  topk_idx     int32 [n, K] or NULL (accumulate only); topk_val float32 [n, K].
- *  workspace    device scratch of ws_bytes >= scoup_uplift_workspace_size().
+ *  workspace    device scratch of ws_bytes >= scoup_uplift_workspace_size()
+ *               (scoup_uplift_chunked_workspace_size() with SCOUP_UPLIFT_CHUNKED;
+ *               a smaller one is refused with SCOUP_ERR_OOM before any work).
  *  stats        HOST scoup_stats* or NULL; when given, the call synchronises
  *               `stream` and returns the device status.
  * Limits: 1 <= K <= C <= 1024, 1 <= s <= 1024, V >= 0, n >= 0 (n = 0 and V = 0
