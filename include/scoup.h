@@ -437,7 +437,7 @@ typedef struct scoup_plan_info {
   int32_t warp_w;           /* tile-kernel warp pixel block: warp_w x (32 / warp_w) */
   int32_t tuned;            /* 1 once scoup_autotune has chosen lanes and warp_w */
   int32_t graph_kernels;    /* kernel launches in one replay of the captured graph (0 before) */
-  int64_t workspace_bytes;  /* device memory held by the lane workspaces */
+  int64_t workspace_bytes;  /* device memory held by the lane workspaces and the chunked form */
   int32_t n_tune;
   scoup_tune_entry tune[SCOUP_MAX_TUNE];  /* the autotuner's measurements */
   int32_t chunk_views;      /* 0: scenes on lanes; > 0: views per chunk of the chunked form */
