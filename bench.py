@@ -857,8 +857,8 @@ def dense_leg(args, dist, wl, up, dev):
 
 
 def backward_leg(args, dist, dev):
-    """Secondary measurement: the differentiable sparse render of BASELINE
-    configuration 5 (500k Gaussians, 32 views at 800x600, K = 8 of C = 256,
+    """Secondary measurement: the differentiable sparse render workload
+    (500k Gaussians, 32 views at 800x600, K = 8 of C = 256,
     a 256 x 512 codebook) with its own uplift: the scene's region codes are
     uplifted over its 32 views (scoup_uplift, outside the timed region), and
     per view the whole loss chain runs in the library -- render (Eq. 7) ->

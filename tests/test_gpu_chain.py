@@ -1,5 +1,5 @@
-"""The differentiable render's loss chain on the GPU (BASELINE configuration
-5): render (Eq. 7) -> decode (Eq. 8, bf16 tensor cores) -> L2 loss against
+"""The differentiable render's loss chain on the GPU (the 500k-Gaussian,
+800 x 600 differentiable-render workload): render (Eq. 7) -> decode (Eq. 8, bf16 tensor cores) -> L2 loss against
 the decoded region codes -> dL/dF -> dL/dWhat = dL/dF C^T (tensor cores) ->
 render backward.  Each new piece is checked against FP64 NumPy within the
 bound its roundings imply; the whole chain against the oracle's FP64 chain
